@@ -1,0 +1,801 @@
+/*
+ * npfem_oracle.c -- plain, slow, FP64 CPU oracle of the npFEM solid-solver
+ * time step (Kotsalos et al., as summarised in arXiv 1911.03062,
+ * Supplementary Sec. 2.1, Eqs. (vel), (Newton2nd), (genericOptimizationNewton)
+ * and the quasi-Newton update that follows them).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load this file's library.  It shares no
+ * code, header, table or helper with the CUDA path.
+ *
+ * The paper states the variational form and the quasi-Newton iteration but
+ * defers the element energies, their projections, the Hessian approximation
+ * and the line search to its npFEM reference.  This file follows the standard
+ * projective-dynamics reading of those (each E_i = w_i/2 |A_i x - p_i(x)|^2,
+ * p_i the closest point of a constraint set; the constant matrix
+ * P = M/h^2 + sum_i w_i A_i^T A_i as H_0), with these concrete choices:
+ *   strain  : per triangle, p = polar factor of the deformation gradient F
+ *   area    : per triangle, p = U diag(d1,d2) V^T, closest (d1,d2) with d1 d2 = 1
+ *   bending : per interior edge, cotangent hinge vector b, p = b |b_rest|/|b|
+ *   volume  : per cell, p = closest point with V(p) = V_rest (Gauss-Newton)
+ *   step    : L-BFGS (history m, H_0 = P^{-1}) + Armijo backtracking, fixed K.
+ * The global solve uses this file's own sparse (RCM + envelope) Cholesky.
+ *
+ * Public layout: positions, velocities, forces are [nV][3] doubles per cell.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ENOMEM -2
+#define ORC_ENOTSPD -3
+
+#define AREA_MAX_IT 30
+#define AREA_TOL 1e-15
+#define VOL_MAX_UPDATES 8
+#define VOL_TOL 1e-14
+#define DEGEN_TOL 1e-12
+#define BEND_TOL 1e-12
+#define CURV_TOL 1e-12
+
+typedef struct {
+    int nV, nT, nH;
+    int *tri;          /* nT*3 */
+    double *rest;      /* nV*3 */
+    double *mass;      /* nV */
+    double ks, ka, kb, kv, h;
+    double *Dinv;      /* nT*4, row-major 2x2 */
+    double *area;      /* nT rest areas */
+    int *hv;           /* nH*4 hinge vertices (x0,x1 hinge; x2 opp. in t1; x3 opp. in t2) */
+    double *hc;        /* nH*4 stencil coefficients */
+    double *hrest;     /* nH rest |b| */
+    double V0;
+    /* P in CSR (full symmetric pattern, sorted columns) */
+    int *Pp, *Pj;
+    double *Px;
+    /* envelope Cholesky of P in RCM order */
+    int *perm;         /* perm[new] = old */
+    int *first;        /* first column (new numbering) of row i */
+    long *rowstart;    /* offset of row i in env */
+    double *env;       /* row i holds L[i][first[i] .. i] */
+} orc_type;
+
+/* ---------------------------------------------------------------- helpers */
+static double dot3(const double *a, const double *b) { return a[0]*b[0] + a[1]*b[1] + a[2]*b[2]; }
+static void sub3(const double *a, const double *b, double *o) { o[0]=a[0]-b[0]; o[1]=a[1]-b[1]; o[2]=a[2]-b[2]; }
+static void cross3(const double *a, const double *b, double *o) {
+    o[0] = a[1]*b[2] - a[2]*b[1];
+    o[1] = a[2]*b[0] - a[0]*b[2];
+    o[2] = a[0]*b[1] - a[1]*b[0];
+}
+static double norm3(const double *a) { return sqrt(dot3(a, a)); }
+
+/* cot of the angle at vertex a of triangle (a, b, c) */
+static double cot_at(const double *a, const double *b, const double *c) {
+    double u[3], v[3], w[3];
+    sub3(b, a, u); sub3(c, a, v); cross3(u, v, w);
+    return dot3(u, v) / norm3(w);
+}
+
+/* ------------------------------------------------------ element geometry */
+/* Deformation gradient of triangle t: F = [x1-x0, x2-x0] Dinv, 3x2 row-major. */
+static void tri_F(const orc_type *T, const double *x, int t, double F[6]) {
+    const int *v = T->tri + 3*t;
+    const double *Di = T->Dinv + 4*t;
+    double e1[3], e2[3];
+    sub3(x + 3*v[1], x + 3*v[0], e1);
+    sub3(x + 3*v[2], x + 3*v[0], e2);
+    for (int r = 0; r < 3; ++r) {
+        F[2*r+0] = e1[r]*Di[0] + e2[r]*Di[2];
+        F[2*r+1] = e1[r]*Di[1] + e2[r]*Di[3];
+    }
+}
+
+/* Coefficients G[j][c] with F[:,c] = sum_j x_j G[j][c]. */
+static void tri_G(const orc_type *T, int t, double G[3][2]) {
+    const double *Di = T->Dinv + 4*t;
+    for (int c = 0; c < 2; ++c) {
+        G[1][c] = Di[0*2+c];
+        G[2][c] = Di[1*2+c];
+        G[0][c] = -G[1][c] - G[2][c];
+    }
+}
+
+/*
+ * Thin SVD of a 3x2 matrix through the closed-form eigen-decomposition of the
+ * 2x2 symmetric S = F^T F: S = V diag(l1,l2) V^T, sigma_i = sqrt(l_i),
+ * u_i = F v_i / sigma_i.  When sigma2 <= DEGEN_TOL * sigma1 the second left
+ * vector is completed to an orthonormal pair deterministically.
+ * Returns U (3x2 row-major), V (2x2, columns v1 v2, row-major), s[2].
+ */
+static void svd32(const double F[6], double U[6], double V[4], double s[2]) {
+    double a = 0, b = 0, c = 0;
+    for (int r = 0; r < 3; ++r) {
+        a += F[2*r]*F[2*r];
+        b += F[2*r]*F[2*r+1];
+        c += F[2*r+1]*F[2*r+1];
+    }
+    double half = 0.5*(a + c);
+    double dd = hypot(0.5*(a - c), b);
+    double l1 = half + dd;
+    double det = a*c - b*b;
+    double l2 = (l1 > 0) ? det / l1 : 0.0;
+    if (l2 < 0) l2 = 0;
+    double v1[2];
+    if (dd == 0.0) { v1[0] = 1; v1[1] = 0; }
+    else {
+        double w1x = l1 - c, w1y = b, w2x = b, w2y = l1 - a;
+        double n1 = w1x*w1x + w1y*w1y, n2 = w2x*w2x + w2y*w2y;
+        if (n1 >= n2) { double n = sqrt(n1); v1[0] = w1x/n; v1[1] = w1y/n; }
+        else          { double n = sqrt(n2); v1[0] = w2x/n; v1[1] = w2y/n; }
+    }
+    double v2[2] = { -v1[1], v1[0] };
+    V[0] = v1[0]; V[1] = v2[0];
+    V[2] = v1[1]; V[3] = v2[1];
+    s[0] = sqrt(l1); s[1] = sqrt(l2);
+    double u1[3], u2[3];
+    if (s[0] == 0.0) {
+        u1[0] = 1; u1[1] = 0; u1[2] = 0;
+        u2[0] = 0; u2[1] = 1; u2[2] = 0;
+    } else {
+        for (int r = 0; r < 3; ++r) u1[r] = (F[2*r]*v1[0] + F[2*r+1]*v1[1]) / s[0];
+        if (s[1] > DEGEN_TOL * s[0]) {
+            for (int r = 0; r < 3; ++r) u2[r] = (F[2*r]*v2[0] + F[2*r+1]*v2[1]) / s[1];
+        } else {
+            /* axis least aligned with u1, made orthogonal to it */
+            int ax = 0;
+            if (fabs(u1[1]) < fabs(u1[ax])) ax = 1;
+            if (fabs(u1[2]) < fabs(u1[ax])) ax = 2;
+            double e[3] = {0, 0, 0};
+            e[ax] = 1.0;
+            double pr = dot3(e, u1);
+            for (int r = 0; r < 3; ++r) u2[r] = e[r] - pr*u1[r];
+            double n = norm3(u2);
+            for (int r = 0; r < 3; ++r) u2[r] /= n;
+        }
+    }
+    for (int r = 0; r < 3; ++r) { U[2*r] = u1[r]; U[2*r+1] = u2[r]; }
+}
+
+/* U diag(d) V^T */
+static void usv(const double U[6], const double V[4], const double d[2], double P[6]) {
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 2; ++c)
+            P[2*r+c] = U[2*r]*d[0]*V[c*2+0] + U[2*r+1]*d[1]*V[c*2+1];
+}
+
+/*
+ * Closest (d1, d2) to (s1, s2) on d1 d2 = 1 (s1 >= s2 >= 0).  Stationarity
+ * gives d1 = (s1 + l s2)/(1 - l^2), d2 = (s2 + l s1)/(1 - l^2) with
+ * f(l) = (s1 + l s2)(s2 + l s1) - (1 - l^2)^2 = 0.  The root is bracketed by
+ * [-s2/s1, 0] when s1 s2 > 1 and by [0, 1] otherwise; Newton from l = 0,
+ * falling back to bisection when a step leaves the bracket, until
+ * |dl| <= AREA_TOL or AREA_MAX_IT iterations.
+ */
+static void area_target(double s1, double s2, double d[2]) {
+    double f0 = s1*s2 - 1.0;
+    double lam = 0.0;
+    if (f0 != 0.0 && s1 > 0.0) {
+        double lo, hi;
+        if (f0 > 0) { lo = -s2/s1; hi = 0.0; } else { lo = 0.0; hi = 1.0; }
+        for (int it = 0; it < AREA_MAX_IT; ++it) {
+            double A = s1 + lam*s2, B = s2 + lam*s1, q = 1.0 - lam*lam;
+            double f = A*B - q*q;
+            if (f == 0.0) break;
+            if (f < 0) lo = lam; else hi = lam;
+            double fp = s2*B + s1*A + 4.0*lam*q;
+            double ln = (fp > 0) ? lam - f/fp : 0.5*(lo + hi);
+            if (!(ln >= lo && ln <= hi)) ln = 0.5*(lo + hi);
+            double step = fabs(ln - lam);
+            lam = ln;
+            if (step <= AREA_TOL) break;
+        }
+    }
+    double q = 1.0 - lam*lam;
+    d[0] = (s1 + lam*s2)/q;
+    d[1] = (s2 + lam*s1)/q;
+}
+
+/* ------------------------------------------------------------------ volume */
+/* V(p) = sum_t (p_a - o).((p_b - o) x (p_c - o)) / 6 with o = p_0 (same value in
+ * exact arithmetic as the origin-based sum; the shift avoids cancellation). */
+static double volume(const orc_type *T, const double *p) {
+    const double *o = p;
+    double V = 0;
+    for (int t = 0; t < T->nT; ++t) {
+        const int *v = T->tri + 3*t;
+        double a[3], b[3], c[3], bc[3];
+        sub3(p + 3*v[0], o, a); sub3(p + 3*v[1], o, b); sub3(p + 3*v[2], o, c);
+        cross3(b, c, bc);
+        V += dot3(a, bc) / 6.0;
+    }
+    return V;
+}
+
+/* dV/dp_v = sum over triangles (v, b, c) containing v (CCW from v) of (p_b x p_c)/6 */
+static void volume_grad(const orc_type *T, const double *p, double *gV) {
+    const double *o = p;
+    memset(gV, 0, sizeof(double)*3*T->nV);
+    for (int t = 0; t < T->nT; ++t) {
+        const int *v = T->tri + 3*t;
+        for (int k = 0; k < 3; ++k) {
+            int a = v[k], b = v[(k+1)%3], c = v[(k+2)%3];
+            double pb[3], pc[3], w[3];
+            sub3(p + 3*b, o, pb); sub3(p + 3*c, o, pc);
+            cross3(pb, pc, w);
+            for (int r = 0; r < 3; ++r) gV[3*a+r] += w[r] / 6.0;
+        }
+    }
+}
+
+/*
+ * Closest point p to x with V(p) = V0, by Gauss-Newton on the linearised
+ * constraint: p_0 = x, lambda_j = (V0 - V(p_j) - gV(p_j).(x - p_j)) / |gV(p_j)|^2,
+ * p_{j+1} = x + lambda_j gV(p_j); stop once |V(p_j) - V0| <= VOL_TOL |V0| or
+ * after VOL_MAX_UPDATES updates.  Returns the number of updates.
+ */
+static int volume_project(const orc_type *T, const double *x, double *p, double *gV) {
+    int n3 = 3*T->nV;
+    memcpy(p, x, sizeof(double)*n3);
+    int j = 0;
+    for (;; ++j) {
+        double V = volume(T, p);
+        if (fabs(V - T->V0) <= VOL_TOL*fabs(T->V0) || j == VOL_MAX_UPDATES) break;
+        volume_grad(T, p, gV);
+        double G2 = 0, r = 0;
+        for (int i = 0; i < n3; ++i) { G2 += gV[i]*gV[i]; r += gV[i]*(x[i] - p[i]); }
+        double lam = (T->V0 - V - r) / G2;
+        for (int i = 0; i < n3; ++i) p[i] = x[i] + lam*gV[i];
+    }
+    return j;
+}
+
+/* ------------------------------------------------------------------ energy */
+#define TERM_INERTIA 1
+#define TERM_STRAIN 2
+#define TERM_AREA 4
+#define TERM_BEND 8
+#define TERM_VOLUME 16
+#define TERM_ALL 31
+
+/*
+ * g(x) = 1/(2h^2) sum_v m_v |x_v - y_v|^2 + sum_i E_i(x)   (Eq. genericOptimizationNewton, C = 0)
+ * and its gradient M/h^2 (x - y) + sum_i w_i A_i^T (A_i x - p_i).
+ * terms[0..4] receive the inertia/strain/area/bending/volume parts.
+ */
+double orc_energy(const orc_type *T, const double *x, const double *y, int mask,
+                  double *grad, double *terms) {
+    int nV = T->nV;
+    double e[5] = {0, 0, 0, 0, 0};
+    if (grad) memset(grad, 0, sizeof(double)*3*nV);
+    double ih2 = 1.0/(T->h*T->h);
+    if (mask & TERM_INERTIA) {
+        for (int v = 0; v < nV; ++v) {
+            double dx[3];
+            sub3(x + 3*v, y + 3*v, dx);
+            e[0] += 0.5*ih2*T->mass[v]*dot3(dx, dx);
+            if (grad) for (int r = 0; r < 3; ++r) grad[3*v+r] += ih2*T->mass[v]*dx[r];
+        }
+    }
+    if (mask & (TERM_STRAIN | TERM_AREA)) {
+        for (int t = 0; t < T->nT; ++t) {
+            double F[6], U[6], V[4], s[2], G[3][2], R[6] = {0, 0, 0, 0, 0, 0};
+            tri_F(T, x, t, F);
+            svd32(F, U, V, s);
+            tri_G(T, t, G);
+            if (mask & TERM_STRAIN) {
+                double one[2] = {1, 1}, Ps[6];
+                usv(U, V, one, Ps);
+                double w = T->ks*T->area[t], n2 = 0;
+                for (int i = 0; i < 6; ++i) { n2 += (F[i]-Ps[i])*(F[i]-Ps[i]); R[i] += w*(F[i]-Ps[i]); }
+                e[1] += 0.5*w*n2;
+            }
+            if (mask & TERM_AREA) {
+                double d[2], Pa[6];
+                area_target(s[0], s[1], d);
+                usv(U, V, d, Pa);
+                double w = T->ka*T->area[t], n2 = 0;
+                for (int i = 0; i < 6; ++i) { n2 += (F[i]-Pa[i])*(F[i]-Pa[i]); R[i] += w*(F[i]-Pa[i]); }
+                e[2] += 0.5*w*n2;
+            }
+            if (grad) {
+                const int *v = T->tri + 3*t;
+                for (int j = 0; j < 3; ++j)
+                    for (int r = 0; r < 3; ++r)
+                        grad[3*v[j]+r] += R[2*r]*G[j][0] + R[2*r+1]*G[j][1];
+            }
+        }
+    }
+    if (mask & TERM_BEND) {
+        for (int hh = 0; hh < T->nH; ++hh) {
+            const int *hv = T->hv + 4*hh;
+            const double *c = T->hc + 4*hh;
+            double b[3] = {0, 0, 0};
+            for (int j = 0; j < 4; ++j)
+                for (int r = 0; r < 3; ++r) b[r] += c[j]*x[3*hv[j]+r];
+            double nb = norm3(b), p[3];
+            if (nb > BEND_TOL*T->hrest[hh] && nb > 0) {
+                for (int r = 0; r < 3; ++r) p[r] = b[r]*T->hrest[hh]/nb;
+            } else {
+                for (int r = 0; r < 3; ++r) p[r] = b[r];
+            }
+            double rr[3];
+            sub3(b, p, rr);
+            e[3] += 0.5*T->kb*dot3(rr, rr);
+            if (grad)
+                for (int j = 0; j < 4; ++j)
+                    for (int r = 0; r < 3; ++r) grad[3*hv[j]+r] += T->kb*c[j]*rr[r];
+        }
+    }
+    if (mask & TERM_VOLUME) {
+        double *p = (double *)malloc(sizeof(double)*6*nV);
+        double *gV = p + 3*nV;
+        volume_project(T, x, p, gV);
+        for (int i = 0; i < 3*nV; ++i) {
+            double r = x[i] - p[i];
+            e[4] += 0.5*T->kv*r*r;
+            if (grad) grad[i] += T->kv*r;
+        }
+        free(p);
+    }
+    if (terms) for (int i = 0; i < 5; ++i) terms[i] = e[i];
+    return e[0] + e[1] + e[2] + e[3] + e[4];
+}
+
+/* ----------------------------------------------------------- sparse matrix */
+typedef struct { int i, j; double v; } trip;
+
+static int trip_cmp(const void *a, const void *b) {
+    const trip *x = (const trip *)a, *y = (const trip *)b;
+    if (x->i != y->i) return x->i < y->i ? -1 : 1;
+    if (x->j != y->j) return x->j < y->j ? -1 : 1;
+    return 0;
+}
+
+/*
+ * P = M/h^2 + sum_t (w_strain + w_area) A_t^T A_t + sum_e w_bend A_e^T A_e + w_vol I.
+ * A_t maps the triangle's vertices to F (F[:,c] = sum_j G[j][c] x_j), A_e to
+ * b = sum_j c_j x_j; the block for xyz is the same nV x nV matrix.
+ */
+static int assemble_P(orc_type *T) {
+    int nV = T->nV;
+    long cap = (long)nV + 9L*T->nT + 16L*T->nH;
+    trip *tr = (trip *)malloc(sizeof(trip)*cap);
+    if (!tr) return ORC_ENOMEM;
+    long n = 0;
+    double ih2 = 1.0/(T->h*T->h);
+    for (int v = 0; v < nV; ++v) { tr[n].i = v; tr[n].j = v; tr[n].v = T->mass[v]*ih2 + T->kv; ++n; }
+    for (int t = 0; t < T->nT; ++t) {
+        double G[3][2];
+        tri_G(T, t, G);
+        double w = (T->ks + T->ka)*T->area[t];
+        const int *v = T->tri + 3*t;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                tr[n].i = v[a]; tr[n].j = v[b];
+                tr[n].v = w*(G[a][0]*G[b][0] + G[a][1]*G[b][1]);
+                ++n;
+            }
+    }
+    for (int hh = 0; hh < T->nH; ++hh) {
+        const int *hv = T->hv + 4*hh;
+        const double *c = T->hc + 4*hh;
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                tr[n].i = hv[a]; tr[n].j = hv[b]; tr[n].v = T->kb*c[a]*c[b]; ++n;
+            }
+    }
+    qsort(tr, n, sizeof(trip), trip_cmp);
+    T->Pp = (int *)calloc(nV + 1, sizeof(int));
+    T->Pj = (int *)malloc(sizeof(int)*n);
+    T->Px = (double *)malloc(sizeof(double)*n);
+    if (!T->Pp || !T->Pj || !T->Px) { free(tr); return ORC_ENOMEM; }
+    long m = 0;
+    for (long k = 0; k < n; ++k) {
+        if (m > 0 && T->Pj[m-1] == tr[k].j && k > 0 && tr[k-1].i == tr[k].i) {
+            T->Px[m-1] += tr[k].v;
+        } else {
+            T->Pj[m] = tr[k].j; T->Px[m] = tr[k].v; T->Pp[tr[k].i + 1]++; ++m;
+        }
+    }
+    for (int i = 0; i < nV; ++i) T->Pp[i+1] += T->Pp[i];
+    free(tr);
+    return ORC_OK;
+}
+
+/* Reverse Cuthill-McKee ordering of P's graph (start: lowest-degree unvisited
+ * vertex; neighbours queued by increasing degree, then index). */
+static void rcm(const orc_type *T, int *perm) {
+    int n = T->nV;
+    int *deg = (int *)malloc(sizeof(int)*n);
+    char *seen = (char *)calloc(n, 1);
+    int *order = (int *)malloc(sizeof(int)*n);
+    int *nb = (int *)malloc(sizeof(int)*n);
+    for (int i = 0; i < n; ++i) deg[i] = T->Pp[i+1] - T->Pp[i] - 1;
+    int head = 0, tail = 0;
+    while (tail < n) {
+        int s = -1;
+        for (int i = 0; i < n; ++i)
+            if (!seen[i] && (s < 0 || deg[i] < deg[s])) s = i;
+        seen[s] = 1; order[tail++] = s;
+        while (head < tail) {
+            int u = order[head++], k = 0;
+            for (int p = T->Pp[u]; p < T->Pp[u+1]; ++p) {
+                int w = T->Pj[p];
+                if (!seen[w]) { seen[w] = 1; nb[k++] = w; }
+            }
+            for (int a = 1; a < k; ++a) {          /* insertion sort by (deg, idx) */
+                int w = nb[a], b = a - 1;
+                while (b >= 0 && (deg[nb[b]] > deg[w] || (deg[nb[b]] == deg[w] && nb[b] > w))) {
+                    nb[b+1] = nb[b]; --b;
+                }
+                nb[b+1] = w;
+            }
+            for (int a = 0; a < k; ++a) order[tail++] = nb[a];
+        }
+    }
+    for (int i = 0; i < n; ++i) perm[i] = order[n - 1 - i];
+    free(deg); free(seen); free(order); free(nb);
+}
+
+/* Envelope (profile) Cholesky of the RCM-permuted P, row by row. */
+static int factor_P(orc_type *T) {
+    int n = T->nV;
+    T->perm = (int *)malloc(sizeof(int)*n);
+    int *iperm = (int *)malloc(sizeof(int)*n);
+    T->first = (int *)malloc(sizeof(int)*n);
+    T->rowstart = (long *)malloc(sizeof(long)*(n + 1));
+    rcm(T, T->perm);
+    for (int i = 0; i < n; ++i) iperm[T->perm[i]] = i;
+    for (int i = 0; i < n; ++i) {
+        int old = T->perm[i], f = i;
+        for (int p = T->Pp[old]; p < T->Pp[old+1]; ++p) {
+            int j = iperm[T->Pj[p]];
+            if (j < f) f = j;
+        }
+        T->first[i] = f;
+    }
+    T->rowstart[0] = 0;
+    for (int i = 0; i < n; ++i) T->rowstart[i+1] = T->rowstart[i] + (i - T->first[i] + 1);
+    T->env = (double *)calloc(T->rowstart[n], sizeof(double));
+    if (!T->env) { free(iperm); return ORC_ENOMEM; }
+#define L(i, j) T->env[T->rowstart[i] + ((j) - T->first[i])]
+    for (int i = 0; i < n; ++i) {
+        int old = T->perm[i];
+        for (int p = T->Pp[old]; p < T->Pp[old+1]; ++p) {
+            int j = iperm[T->Pj[p]];
+            if (j <= i) L(i, j) = T->Px[p];
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        int fi = T->first[i];
+        for (int j = fi; j < i; ++j) {
+            double s = L(i, j);
+            int k0 = fi > T->first[j] ? fi : T->first[j];
+            for (int k = k0; k < j; ++k) s -= L(i, k)*L(j, k);
+            L(i, j) = s / L(j, j);
+        }
+        double s = L(i, i);
+        for (int k = fi; k < i; ++k) s -= L(i, k)*L(i, k);
+        if (!(s > 0)) { free(iperm); return ORC_ENOTSPD; }
+        L(i, i) = sqrt(s);
+    }
+    free(iperm);
+    return ORC_OK;
+}
+
+/* x = P^{-1} b for each of the 3 components (b, x: [nV][3]). */
+void orc_solve(const orc_type *T, const double *b, double *x) {
+    int n = T->nV;
+    double *z = (double *)malloc(sizeof(double)*n);
+    for (int c = 0; c < 3; ++c) {
+        for (int i = 0; i < n; ++i) z[i] = b[3*T->perm[i] + c];
+        for (int i = 0; i < n; ++i) {                 /* L z = b */
+            double s = z[i];
+            for (int k = T->first[i]; k < i; ++k) s -= L(i, k)*z[k];
+            z[i] = s / L(i, i);
+        }
+        for (int i = n - 1; i >= 0; --i) {            /* L^T w = z */
+            z[i] /= L(i, i);
+            for (int k = T->first[i]; k < i; ++k) z[k] -= L(i, k)*z[i];
+        }
+        for (int i = 0; i < n; ++i) x[3*T->perm[i] + c] = z[i];
+    }
+    free(z);
+}
+#undef L
+
+/* ------------------------------------------------------------ type set-up */
+void orc_type_destroy(orc_type *T) {
+    if (!T) return;
+    free(T->tri); free(T->rest); free(T->mass); free(T->Dinv); free(T->area);
+    free(T->hv); free(T->hc); free(T->hrest); free(T->Pp); free(T->Pj); free(T->Px);
+    free(T->perm); free(T->first); free(T->rowstart); free(T->env);
+    free(T);
+}
+
+/*
+ * Hinges: every undirected edge of a closed, consistently oriented mesh is
+ * seen once as a->b (triangle t1 = (a, b, c)) and once as b->a (t2 = (b, a, d)).
+ * Stencil (cotangent hinge vector, scaled by sqrt(3/(A1+A2))) with
+ * alpha_{t,v} = rest angle of triangle t at hinge vertex v:
+ *   c0 = cot a_{1,1} + cot a_{2,1},  c1 = cot a_{1,0} + cot a_{2,0},
+ *   c2 = -(cot a_{1,0} + cot a_{1,1}),  c3 = -(cot a_{2,0} + cot a_{2,1}).
+ */
+static int build_hinges(orc_type *T) {
+    int nT = T->nT, nV = T->nV;
+    int ne = 3*nT;
+    /* directed half-edges (a, b, opposite, triangle) sorted by (min, max) key */
+    long *key = (long *)malloc(sizeof(long)*ne);
+    int *idx = (int *)malloc(sizeof(int)*ne);
+    for (int t = 0; t < nT; ++t)
+        for (int k = 0; k < 3; ++k) {
+            int a = T->tri[3*t+k], b = T->tri[3*t+(k+1)%3];
+            int lo = a < b ? a : b, hi = a < b ? b : a;
+            key[3*t+k] = (long)lo*nV + hi;
+            idx[3*t+k] = 3*t + k;
+        }
+    /* pair each half-edge with its twin through an open-addressing table on the key */
+    long hsz = 1;
+    while (hsz < 4L*ne) hsz <<= 1;
+    int *tab = (int *)malloc(sizeof(int)*hsz);
+    for (long i = 0; i < hsz; ++i) tab[i] = -1;
+    int *twin = (int *)malloc(sizeof(int)*ne);
+    int ok = 1;
+    for (int e = 0; e < ne; ++e) {
+        twin[e] = -1;
+        long hpos = (long)((unsigned long)(key[e]*2654435761UL) & (hsz - 1));
+        while (tab[hpos] >= 0 && key[tab[hpos]] != key[e]) hpos = (hpos + 1) & (hsz - 1);
+        if (tab[hpos] < 0) tab[hpos] = e;
+        else {
+            int o = tab[hpos];
+            if (twin[o] >= 0) { ok = 0; break; }       /* edge in > 2 triangles */
+            int a = T->tri[e], b = T->tri[3*(e/3) + (e%3+1)%3];
+            int oa = T->tri[o], ob = T->tri[3*(o/3) + (o%3+1)%3];
+            if (!(a == ob && b == oa)) { ok = 0; break; } /* inconsistent orientation */
+            twin[o] = e; twin[e] = o;
+        }
+    }
+    if (ok) for (int e = 0; e < ne; ++e) if (twin[e] < 0) { ok = 0; break; }  /* open mesh */
+    if (!ok) { free(key); free(idx); free(tab); free(twin); return ORC_EINVAL; }
+    T->nH = ne/2;
+    T->hv = (int *)malloc(sizeof(int)*4*T->nH);
+    T->hc = (double *)malloc(sizeof(double)*4*T->nH);
+    T->hrest = (double *)malloc(sizeof(double)*T->nH);
+    int h = 0;
+    for (int e = 0; e < ne; ++e) {
+        int o = twin[e];
+        if (o < e) continue;                  /* first appearance defines the hinge */
+        int t1 = e/3, k1 = e%3, t2 = o/3, k2 = o%3;
+        int x0 = T->tri[3*t1+k1], x1 = T->tri[3*t1+(k1+1)%3], x2 = T->tri[3*t1+(k1+2)%3];
+        int x3 = T->tri[3*t2+(k2+2)%3];
+        const double *X0 = T->rest + 3*x0, *X1 = T->rest + 3*x1, *X2 = T->rest + 3*x2, *X3 = T->rest + 3*x3;
+        double c10 = cot_at(X0, X1, X2), c11 = cot_at(X1, X2, X0);
+        double c20 = cot_at(X0, X3, X1), c21 = cot_at(X1, X0, X3);
+        double A1 = T->area[t1], A2 = T->area[t2];
+        double sc = sqrt(3.0/(A1 + A2));
+        int *hv = T->hv + 4*h;
+        double *c = T->hc + 4*h;
+        hv[0] = x0; hv[1] = x1; hv[2] = x2; hv[3] = x3;
+        c[0] = sc*(c11 + c21);
+        c[1] = sc*(c10 + c20);
+        c[2] = -sc*(c10 + c11);
+        c[3] = -sc*(c20 + c21);
+        double b[3] = {0, 0, 0};
+        for (int j = 0; j < 4; ++j)
+            for (int r = 0; r < 3; ++r) b[r] += c[j]*T->rest[3*hv[j]+r];
+        T->hrest[h] = norm3(b);
+        ++h;
+    }
+    free(key); free(idx); free(tab); free(twin);
+    return ORC_OK;
+}
+
+int orc_type_create(int nV, const double *rest, int nT, const int *tris, const double *mass,
+                    double ks, double ka, double kb, double kv, double dt, orc_type **out) {
+    *out = NULL;
+    if (nV < 4 || nT < 4 || !(dt > 0)) return ORC_EINVAL;
+    for (int i = 0; i < 3*nT; ++i) if (tris[i] < 0 || tris[i] >= nV) return ORC_EINVAL;
+    orc_type *T = (orc_type *)calloc(1, sizeof(orc_type));
+    if (!T) return ORC_ENOMEM;
+    T->nV = nV; T->nT = nT;
+    T->ks = ks; T->ka = ka; T->kb = kb; T->kv = kv; T->h = dt;
+    T->tri = (int *)malloc(sizeof(int)*3*nT);
+    T->rest = (double *)malloc(sizeof(double)*3*nV);
+    T->mass = (double *)malloc(sizeof(double)*nV);
+    T->Dinv = (double *)malloc(sizeof(double)*4*nT);
+    T->area = (double *)malloc(sizeof(double)*nT);
+    memcpy(T->tri, tris, sizeof(int)*3*nT);
+    memcpy(T->rest, rest, sizeof(double)*3*nV);
+    for (int v = 0; v < nV; ++v) T->mass[v] = mass ? mass[v] : 1.0/nV;
+    for (int t = 0; t < nT; ++t) {
+        const int *v = T->tri + 3*t;
+        double E1[3], E2[3], n[3];
+        sub3(T->rest + 3*v[1], T->rest + 3*v[0], E1);
+        sub3(T->rest + 3*v[2], T->rest + 3*v[0], E2);
+        cross3(E1, E2, n);
+        double nn = norm3(n), l1 = norm3(E1);
+        if (!(nn > 0) || !(l1 > 0)) { orc_type_destroy(T); return ORC_EINVAL; }
+        double u[3] = {E1[0]/l1, E1[1]/l1, E1[2]/l1};
+        double nh[3] = {n[0]/nn, n[1]/nn, n[2]/nn}, w[3];
+        cross3(nh, u, w);
+        /* D_m = [[E1.u, E2.u], [E1.w, E2.w]] */
+        double a = dot3(E1, u), b = dot3(E2, u), c = dot3(E1, w), d = dot3(E2, w);
+        double det = a*d - b*c;
+        double *Di = T->Dinv + 4*t;
+        Di[0] = d/det; Di[1] = -b/det; Di[2] = -c/det; Di[3] = a/det;
+        T->area[t] = 0.5*nn;
+    }
+    int rc = build_hinges(T);
+    if (rc) { orc_type_destroy(T); return rc; }
+    T->V0 = volume(T, T->rest);
+    rc = assemble_P(T);
+    if (!rc) rc = factor_P(T);
+    if (rc) { orc_type_destroy(T); return rc; }
+    *out = T;
+    return ORC_OK;
+}
+
+void orc_type_info(const orc_type *T, int *nH, double *V0, int *nnzP, long *nnzL) {
+    if (nH) *nH = T->nH;
+    if (V0) *V0 = T->V0;
+    if (nnzP) *nnzP = T->Pp[T->nV];
+    if (nnzL) *nnzL = T->rowstart[T->nV];
+}
+
+void orc_P_dense(const orc_type *T, double *P) {
+    int n = T->nV;
+    memset(P, 0, sizeof(double)*n*n);
+    for (int i = 0; i < n; ++i)
+        for (int p = T->Pp[i]; p < T->Pp[i+1]; ++p) P[(long)i*n + T->Pj[p]] = T->Px[p];
+}
+
+void orc_hinges(const orc_type *T, int *hv, double *hc, double *hrest) {
+    memcpy(hv, T->hv, sizeof(int)*4*T->nH);
+    memcpy(hc, T->hc, sizeof(double)*4*T->nH);
+    memcpy(hrest, T->hrest, sizeof(double)*T->nH);
+}
+
+/* ------------------------------------------------- single-element entries */
+void orc_polar(const double F[6], double T[6], double s[2]) {
+    double U[6], V[4], one[2] = {1, 1};
+    svd32(F, U, V, s);
+    usv(U, V, one, T);
+}
+
+void orc_area_project(const double F[6], double Pa[6], double d[2]) {
+    double U[6], V[4], s[2];
+    svd32(F, U, V, s);
+    area_target(s[0], s[1], d);
+    usv(U, V, d, Pa);
+}
+
+void orc_area_target(double s1, double s2, double d[2]) { area_target(s1, s2, d); }
+
+int orc_volume_project(const orc_type *T, const double *x, double *p) {
+    double *gV = (double *)malloc(sizeof(double)*3*T->nV);
+    int j = volume_project(T, x, p, gV);
+    free(gV);
+    return j;
+}
+
+double orc_volume(const orc_type *T, const double *p) { return volume(T, p); }
+void orc_volume_grad(const orc_type *T, const double *p, double *g) { volume_grad(T, p, g); }
+
+/* ------------------------------------------------------------- time step */
+static double vdot(const double *a, const double *b, int n) {
+    double s = 0;
+    for (int i = 0; i < n; ++i) s += a[i]*b[i];
+    return s;
+}
+
+/*
+ * One implicit-Euler step of one cell (Eqs. vel, Newton2nd via the
+ * minimisation of g):
+ *   y = x_n + h v_n + h^2 M^{-1} F_ext,  x^0 = y
+ *   for k < K:  d = -H grad g(x^k)  (L-BFGS two-loop, H_0 = P^{-1}, history m;
+ *                                    plain -P^{-1} grad when the history is empty)
+ *               if grad.d >= 0: clear history, d = -P^{-1} grad
+ *               Armijo backtracking from alpha = 1 (c1, halving, <= max_bt halvings,
+ *               the last trial is taken when the cap is hit)
+ *               store (s, dgrad) when s.dgrad > CURV_TOL |s||dgrad|
+ *   x_{n+1} = x^K,  v_{n+1} = (x_{n+1} - x_n)/h.
+ * Traces (nullable): g_tr[K+1] energies, a_tr[K] accepted alphas,
+ * bt_tr[K] halvings, fb_tr[K] 1 where the descent fallback ran.
+ * Returns the number of iterations whose line search hit the cap.
+ */
+int orc_step(const orc_type *T, const double *xn, const double *vn, const double *f,
+             int K, int m, double c1, int max_bt,
+             double *x_out, double *v_out,
+             double *g_tr, double *a_tr, int *bt_tr, int *fb_tr) {
+    int nV = T->nV, n3 = 3*nV;
+    double h = T->h;
+    int mm = m > 0 ? m : 1;
+    double *buf = (double *)malloc(sizeof(double)*n3*(8 + 2*mm));
+    double *y = buf, *x = y + n3, *gr = x + n3, *d = gr + n3, *xt = d + n3, *gt = xt + n3;
+    double *q = gt + n3, *r = q + n3;
+    double *S = r + n3, *Y = S + n3*mm;
+    double *rho = (double *)malloc(sizeof(double)*mm), *al = (double *)malloc(sizeof(double)*mm);
+    for (int v = 0; v < nV; ++v)
+        for (int c = 0; c < 3; ++c)
+            y[3*v+c] = xn[3*v+c] + h*vn[3*v+c] + h*h/T->mass[v]*f[3*v+c];
+    memcpy(x, y, sizeof(double)*n3);
+    double g = orc_energy(T, x, y, TERM_ALL, gr, NULL);
+    if (g_tr) g_tr[0] = g;
+    int cnt = 0, head = 0, caps = 0;    /* ring: newest at (head-1) mod m */
+    for (int k = 0; k < K; ++k) {
+        int fb = 0;
+        if (cnt == 0) {
+            orc_solve(T, gr, d);
+            for (int i = 0; i < n3; ++i) d[i] = -d[i];
+        } else {
+            memcpy(q, gr, sizeof(double)*n3);
+            for (int l = 0; l < cnt; ++l) {             /* newest -> oldest */
+                int i = ((head - 1 - l) % mm + mm) % mm;
+                al[i] = rho[i]*vdot(S + (long)i*n3, q, n3);
+                for (int e = 0; e < n3; ++e) q[e] -= al[i]*Y[(long)i*n3 + e];
+            }
+            orc_solve(T, q, r);
+            for (int l = cnt - 1; l >= 0; --l) {        /* oldest -> newest */
+                int i = ((head - 1 - l) % mm + mm) % mm;
+                double be = rho[i]*vdot(Y + (long)i*n3, r, n3);
+                for (int e = 0; e < n3; ++e) r[e] += S[(long)i*n3 + e]*(al[i] - be);
+            }
+            for (int i = 0; i < n3; ++i) d[i] = -r[i];
+        }
+        double gd = vdot(gr, d, n3);
+        if (gd >= 0 && cnt > 0) {
+            cnt = 0; fb = 1;
+            orc_solve(T, gr, d);
+            for (int i = 0; i < n3; ++i) d[i] = -d[i];
+            gd = vdot(gr, d, n3);
+        }
+        double alpha = 1.0, gtv;
+        int bt = 0;
+        for (;;) {
+            for (int i = 0; i < n3; ++i) xt[i] = x[i] + alpha*d[i];
+            gtv = orc_energy(T, xt, y, TERM_ALL, gt, NULL);
+            if (gtv <= g + c1*alpha*gd) break;
+            if (bt == max_bt) { ++caps; break; }
+            alpha *= 0.5; ++bt;
+        }
+        double *s_new = q, *y_new = r;          /* free here: the pair enters the ring only if kept */
+        for (int i = 0; i < n3; ++i) { s_new[i] = xt[i] - x[i]; y_new[i] = gt[i] - gr[i]; }
+        double sy = vdot(s_new, y_new, n3);
+        double ns = sqrt(vdot(s_new, s_new, n3)), ny = sqrt(vdot(y_new, y_new, n3));
+        memcpy(x, xt, sizeof(double)*n3);
+        memcpy(gr, gt, sizeof(double)*n3);
+        g = gtv;
+        if (m > 0 && sy > CURV_TOL*ns*ny) {
+            memcpy(S + (long)head*n3, s_new, sizeof(double)*n3);
+            memcpy(Y + (long)head*n3, y_new, sizeof(double)*n3);
+            rho[head] = 1.0/sy;
+            head = (head + 1) % mm;
+            if (cnt < m) ++cnt;
+        }
+        if (g_tr) g_tr[k+1] = g;
+        if (a_tr) a_tr[k] = alpha;
+        if (bt_tr) bt_tr[k] = bt;
+        if (fb_tr) fb_tr[k] = fb;
+    }
+    for (int i = 0; i < n3; ++i) {
+        x_out[i] = x[i];
+        v_out[i] = (x[i] - xn[i]) / h;
+    }
+    free(buf); free(rho); free(al);
+    return caps;
+}
+
+/* n cells of one type, one after another (arrays: [n][nV][3]). */
+int orc_step_cells(const orc_type *T, int n, const double *xn, const double *vn, const double *f,
+                   int K, int m, double c1, int max_bt, double *x_out, double *v_out) {
+    long n3 = 3L*T->nV;
+    int caps = 0;
+    for (int c = 0; c < n; ++c)
+        caps += orc_step(T, xn + c*n3, vn + c*n3, f + c*n3, K, m, c1, max_bt,
+                         x_out + c*n3, v_out + c*n3, NULL, NULL, NULL, NULL);
+    return caps;
+}

@@ -1,0 +1,218 @@
+"""ctypes binding of the FP64 CPU oracle (npfem_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the CPU
+baseline of bench.py are the only users.  Nothing in the product package
+imports this module.
+
+Layout of every per-cell array: [nV, 3] float64 (vertex major, xyz inner).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "npfem_oracle.c")
+LIB = os.path.join(HERE, "liboracle.so")
+
+TERM_INERTIA, TERM_STRAIN, TERM_AREA, TERM_BEND, TERM_VOLUME = 1, 2, 4, 8, 16
+TERM_ALL = 31
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, -O2, no vector intrinsics)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(LIB)
+            dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+            ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+            vp = C.c_void_p
+            L.orc_type_create.argtypes = [C.c_int, dp, C.c_int, ip, vp, C.c_double, C.c_double,
+                                          C.c_double, C.c_double, C.c_double, C.POINTER(vp)]
+            L.orc_type_create.restype = C.c_int
+            L.orc_type_destroy.argtypes = [vp]
+            L.orc_type_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_int), C.POINTER(C.c_long)]
+            L.orc_P_dense.argtypes = [vp, dp]
+            L.orc_hinges.argtypes = [vp, ip, dp, dp]
+            L.orc_solve.argtypes = [vp, dp, dp]
+            L.orc_energy.argtypes = [vp, dp, dp, C.c_int, vp, vp]
+            L.orc_energy.restype = C.c_double
+            L.orc_polar.argtypes = [dp, dp, dp]
+            L.orc_area_project.argtypes = [dp, dp, dp]
+            L.orc_area_target.argtypes = [C.c_double, C.c_double, dp]
+            L.orc_volume_project.argtypes = [vp, dp, dp]
+            L.orc_volume_project.restype = C.c_int
+            L.orc_volume.argtypes = [vp, dp]
+            L.orc_volume.restype = C.c_double
+            L.orc_volume_grad.argtypes = [vp, dp, dp]
+            L.orc_step.argtypes = [vp, dp, dp, dp, C.c_int, C.c_int, C.c_double, C.c_int,
+                                   dp, dp, vp, vp, vp, vp]
+            L.orc_step.restype = C.c_int
+            L.orc_step_cells.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, C.c_int, C.c_double,
+                                         C.c_int, vp, vp]
+            L.orc_step_cells.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _c(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class OracleType:
+    """One mesh type: rest shape, topology, material, time step; owns P and its factor."""
+
+    def __init__(self, rest, tris, k_strain, k_area, k_bend, k_vol, dt, mass=None):
+        L = lib()
+        self.rest = _c(rest).reshape(-1, 3)
+        self.tris = _c(tris, np.int32).reshape(-1, 3)
+        self.nV, self.nT = self.rest.shape[0], self.tris.shape[0]
+        self.dt = float(dt)
+        self.mass = None if mass is None else _c(mass)
+        h = C.c_void_p()
+        rc = L.orc_type_create(self.nV, self.rest, self.nT, self.tris, _ptr(self.mass),
+                               k_strain, k_area, k_bend, k_vol, dt, C.byref(h))
+        if rc != 0:
+            raise ValueError(f"oracle type creation failed ({rc})")
+        self._h = h
+        nH, V0, nnz, nnzL = C.c_int(), C.c_double(), C.c_int(), C.c_long()
+        L.orc_type_info(h, C.byref(nH), C.byref(V0), C.byref(nnz), C.byref(nnzL))
+        self.nH, self.V0, self.nnzP, self.nnzL = nH.value, V0.value, nnz.value, nnzL.value
+
+    @classmethod
+    def from_mesh_type(cls, mt):
+        m = mt.material
+        return cls(mt.rest, mt.tris, m.k_strain, m.k_area, m.k_bend, m.k_vol, m.dt, mt.mass)
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) is not None:
+                lib().orc_type_destroy(self._h)
+        except Exception:
+            pass
+
+    # -- pieces -------------------------------------------------------------
+    def P_dense(self):
+        P = np.empty((self.nV, self.nV))
+        lib().orc_P_dense(self._h, P)
+        return P
+
+    def hinges(self):
+        hv = np.empty((self.nH, 4), np.int32)
+        hc = np.empty((self.nH, 4))
+        hr = np.empty(self.nH)
+        lib().orc_hinges(self._h, hv, hc, hr)
+        return hv, hc, hr
+
+    def solve(self, b):
+        b = _c(b).reshape(self.nV, 3)
+        x = np.empty_like(b)
+        lib().orc_solve(self._h, b, x)
+        return x
+
+    def energy(self, x, y, mask=TERM_ALL, grad=True):
+        x = _c(x).reshape(self.nV, 3)
+        y = _c(y).reshape(self.nV, 3)
+        g = np.empty_like(x) if grad else None
+        terms = np.empty(5)
+        e = lib().orc_energy(self._h, x, y, mask, _ptr(g), _ptr(terms))
+        return e, g, terms
+
+    def volume(self, p):
+        return lib().orc_volume(self._h, _c(p).reshape(self.nV, 3))
+
+    def volume_grad(self, p):
+        g = np.empty((self.nV, 3))
+        lib().orc_volume_grad(self._h, _c(p).reshape(self.nV, 3), g)
+        return g
+
+    def volume_project(self, x):
+        x = _c(x).reshape(self.nV, 3)
+        p = np.empty_like(x)
+        it = lib().orc_volume_project(self._h, x, p)
+        return p, it
+
+    # -- time step ----------------------------------------------------------
+    def step(self, xn, vn, f, K=10, m=5, c1=1e-4, max_bt=8, trace=False):
+        xn, vn, f = (_c(a).reshape(self.nV, 3) for a in (xn, vn, f))
+        xo, vo = np.empty_like(xn), np.empty_like(xn)
+        if trace:
+            gt, at = np.empty(K + 1), np.empty(K)
+            bt, fb = np.empty(K, np.int32), np.empty(K, np.int32)
+            caps = lib().orc_step(self._h, xn, vn, f, K, m, c1, max_bt, xo, vo,
+                                  _ptr(gt), _ptr(at), _ptr(bt), _ptr(fb))
+            return xo, vo, dict(g=gt, alpha=at, backtracks=bt, fallback=fb, caps=caps)
+        lib().orc_step(self._h, xn, vn, f, K, m, c1, max_bt, xo, vo, None, None, None, None)
+        return xo, vo
+
+    def step_cells(self, xn, vn, f, K=10, m=5, c1=1e-4, max_bt=8, threads=1):
+        """Step n cells ([n, nV, 3]); ``threads`` host threads split the cells."""
+        xn, vn, f = (_c(a).reshape(-1, self.nV, 3) for a in (xn, vn, f))
+        n = xn.shape[0]
+        xo, vo = np.empty_like(xn), np.empty_like(xn)
+        L = lib()
+        threads = max(1, min(threads, n))
+        bounds = np.linspace(0, n, threads + 1).astype(int)
+
+        def run(a, b):
+            if b > a:
+                L.orc_step_cells(self._h, b - a, _ptr(xn[a:b]), _ptr(vn[a:b]), _ptr(f[a:b]),
+                                 K, m, c1, max_bt, _ptr(xo[a:b]), _ptr(vo[a:b]))
+
+        if threads == 1:
+            run(0, n)
+        else:
+            ts = [threading.Thread(target=run, args=(bounds[i], bounds[i + 1])) for i in range(threads)]
+            for t in ts:
+                t.start()
+            for t in ts:
+                t.join()
+        return xo, vo
+
+
+def polar(F):
+    F = _c(F).reshape(3, 2)
+    T, s = np.empty((3, 2)), np.empty(2)
+    lib().orc_polar(F, T, s)
+    return T, s
+
+
+def area_project(F):
+    F = _c(F).reshape(3, 2)
+    P, d = np.empty((3, 2)), np.empty(2)
+    lib().orc_area_project(F, P, d)
+    return P, d
+
+
+def area_target(s1, s2):
+    d = np.empty(2)
+    lib().orc_area_target(float(s1), float(s2), d)
+    return d
+
+
+def predictor(xn, vn, f, dt, nV, mass=None):
+    """y = x_n + h v_n + h^2 M^{-1} F_ext (Eq. genericOptimizationNewton, C = 0)."""
+    m = (1.0 / nV) if mass is None else np.asarray(mass)[:, None]
+    return xn + dt * vn + dt * dt / m * f

@@ -1,0 +1,409 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test checks a closed form,
+an invariant of Eq. (genericOptimizationNewton) (Supplementary Sec. 2.1), a
+library routine (numpy SVD / Cholesky, scipy minimisers), finite
+differences, or a brute-force computation on a tiny mesh.
+"""
+import numpy as np
+import pytest
+
+from paper_1911_03062_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module")
+def O(oracle_lib):
+    return oracle_lib
+
+
+@pytest.fixture(scope="module")
+def rbc(O):
+    return I.rbc_type(), O.OracleType.from_mesh_type(I.rbc_type())
+
+
+@pytest.fixture(scope="module")
+def plt(O):
+    return I.plt_type(), O.OracleType.from_mesh_type(I.plt_type())
+
+
+def small_rbc(O, level=1, **kw):
+    unit, tris = I.icosphere(level)
+    mat = dict(k_strain=1.0, k_area=5.0, k_bend=0.05, k_vol=10.0, dt=1e-3)
+    mat.update(kw)
+    return I.rbc_shape(unit), tris, O.OracleType(I.rbc_shape(unit), tris, **mat)
+
+
+def rot(seed):
+    return I.random_rotations(np.random.default_rng(seed), 1)[0]
+
+
+# ------------------------------------------------------------------ meshes
+@pytest.mark.parametrize("level", [0, 1, 2, 3, 4])
+def test_icosphere_topology(level):
+    v, f = I.icosphere(level)
+    nV = 10 * 4 ** level + 2
+    assert v.shape == (nV, 3) and f.shape == (2 * nV - 4, 3)
+    assert np.allclose(np.linalg.norm(v, axis=1), 1.0)
+    # closed 2-manifold, consistently oriented: each directed edge once, its twin once
+    de = {}
+    for a, b, c in f:
+        for e in ((a, b), (b, c), (c, a)):
+            assert e not in de
+            de[e] = 1
+    assert all((b, a) in de for (a, b) in de)
+    # outward: every face normal points away from the origin
+    n = np.cross(v[f[:, 1]] - v[f[:, 0]], v[f[:, 2]] - v[f[:, 0]])
+    assert np.all(np.einsum("ij,ij->i", n, v[f].mean(axis=1)) > 0)
+
+
+def test_evans_fung_profile():
+    # centre thickness R0*C0, maximum thickness of the published profile
+    r2 = np.linspace(0, 1, 200001)
+    t = I.RBC_R0 * np.sqrt(1 - r2) * (I.RBC_C0 + I.RBC_C1 * r2 + I.RBC_C2 * r2 ** 2)
+    assert t[0] == pytest.approx(0.810, abs=5e-4)
+    assert t.max() == pytest.approx(2.566, abs=5e-4)
+    assert r2[np.argmax(t)] == pytest.approx(0.490, abs=5e-3)
+    rest = I.rbc_type().rest
+    assert np.ptp(rest[:, 0]) == pytest.approx(2 * I.RBC_R0, rel=1e-12)
+
+
+# ------------------------------------------------------------- projections
+def test_polar_matches_library_svd(O):
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        F = rng.standard_normal((3, 2))
+        T, s = O.polar(F)
+        U, S, Vt = np.linalg.svd(F, full_matrices=False)
+        assert np.allclose(s, S, rtol=1e-12, atol=1e-14)
+        assert np.allclose(T, U @ Vt, atol=1e-11)
+        assert np.allclose(T.T @ T, np.eye(2), atol=1e-12)
+
+
+def test_polar_special_cases(O):
+    Q = np.linalg.qr(np.random.default_rng(1).standard_normal((3, 3)))[0][:, :2]
+    T, s = O.polar(Q)                        # already a rotation: fixed point
+    assert np.allclose(T, Q, atol=1e-14) and np.allclose(s, 1)
+    T, s = O.polar(3.0 * Q)                  # uniform scale: same polar factor
+    assert np.allclose(T, Q, atol=1e-14) and np.allclose(s, 3)
+    F = np.outer([0.0, 0.0, 2.0], [1.0, 0.0])   # rank-1: degenerate triangle branch
+    T, s = O.polar(F)
+    assert s[1] == 0 and np.allclose(T.T @ T, np.eye(2), atol=1e-14)
+
+
+def brute_area(s1, s2):
+    """Global minimiser of (d1-s1)^2 + (1/d1-s2)^2 over d1 > 0 by grid + golden section."""
+    from scipy.optimize import minimize_scalar
+    phi = lambda d: (d - s1) ** 2 + (1.0 / d - s2) ** 2
+    grid = np.exp(np.linspace(np.log(1e-3), np.log(1e3), 200001))
+    i = int(np.argmin(phi(grid)))
+    r = minimize_scalar(phi, bounds=(grid[max(i - 1, 0)], grid[min(i + 1, len(grid) - 1)]),
+                        method="bounded", options=dict(xatol=1e-14))
+    return np.array([r.x, 1.0 / r.x])
+
+
+def test_area_target_brute_force(O):
+    rng = np.random.default_rng(2)
+    cases = [(1.0, 1.0), (1.3, 1.3), (0.7, 0.7), (1.5, 0.9), (1.2, 0.3), (3.0, 2.0), (0.2, 0.1),
+             (1.0, 1e-9)]
+    cases += [tuple(sorted(rng.uniform(0.2, 2.5, 2), reverse=True)) for _ in range(40)]
+    for s1, s2 in cases:
+        d = O.area_target(s1, s2)
+        assert d[0] * d[1] == pytest.approx(1.0, rel=1e-12)
+        db = brute_area(s1, s2)
+        f = lambda dd: (dd[0] - s1) ** 2 + (dd[1] - s2) ** 2
+        assert f(d) <= f(db) + 1e-12, (s1, s2, d, db)
+        assert np.allclose(d, db, rtol=1e-6), (s1, s2, d, db)
+
+
+def test_area_target_equal_singular_values(O):
+    for s in (0.3, 0.9, 1.0, 1.1, 1.9):
+        assert np.allclose(O.area_target(s, s), [1.0, 1.0], atol=1e-14)
+
+
+def test_area_projection_keeps_singular_vectors(O):
+    rng = np.random.default_rng(3)
+    for _ in range(100):
+        F = rng.standard_normal((3, 2))
+        Pa, d = O.area_project(F)
+        U, S, Vt = np.linalg.svd(F, full_matrices=False)
+        assert np.allclose(Pa, U @ np.diag(d) @ Vt, atol=1e-10)
+        assert np.prod(np.linalg.svd(Pa, compute_uv=False)) == pytest.approx(1.0, rel=1e-12)
+
+
+# ------------------------------------------------------------ volume, hinges
+def test_volume_closed_forms(O):
+    v, f = I.tetrahedron()
+    T = O.OracleType(v, f, 1, 1, 1, 1, 1e-3)
+    assert T.V0 == pytest.approx(8.0 / 3.0, rel=1e-14)          # regular tet of edge 2*sqrt(2)
+    assert T.volume(v * 2.0 + 7.0) == pytest.approx(8.0 * 8.0 / 3.0, rel=1e-13)
+    u, t = I.icosphere(4)
+    S = O.OracleType(u, t, 1, 1, 1, 1, 1e-3)
+    assert S.V0 == pytest.approx(4.0 / 3.0 * np.pi, rel=5e-3)
+    assert S.V0 < 4.0 / 3.0 * np.pi                               # inscribed polyhedron
+
+
+def test_volume_gradient_fd(O):
+    rest, tris, T = small_rbc(O, 2)
+    x = rest + 0.05 * np.random.default_rng(4).standard_normal(rest.shape)
+    g = T.volume_grad(x)
+    h = 1e-6
+    fd = np.zeros_like(x)
+    for i in range(x.shape[0]):
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, c] += h
+            xm[i, c] -= h
+            fd[i, c] = (T.volume(xp) - T.volume(xm)) / (2 * h)
+    assert np.allclose(g, fd, atol=1e-8 * np.abs(g).max())
+    assert np.allclose(g.sum(axis=0), 0, atol=1e-12)               # translation invariance
+
+
+def test_volume_projection_kkt(O, rbc):
+    # The projection is the Gauss-Newton closest-point iteration stopped once
+    # the constraint holds; for a small violation that is also (to first
+    # order) the KKT point: x - p parallel to grad V(p).
+    mt, T = rbc
+    rng = np.random.default_rng(5)
+    x = mt.rest * np.array([1.001, 1.0, 1.0]) + 0.02 * rng.standard_normal(mt.rest.shape)
+    p, it = T.volume_project(x)
+    assert 1 <= it <= 8
+    assert T.volume(p) == pytest.approx(T.V0, rel=1e-14)
+    gV = T.volume_grad(p).ravel()
+    r = (x - p).ravel()
+    lam = r @ gV / (gV @ gV)
+    assert np.linalg.norm(r - lam * gV) <= 1e-7 * np.linalg.norm(r)
+    # p is no farther from x than other points of the constraint surface nearby
+    for k in range(20):
+        w = rng.standard_normal(r.shape)
+        w -= (w @ gV) / (gV @ gV) * gV                 # tangent direction
+        q = p.ravel() + 1e-3 * w / np.linalg.norm(w)
+        gq = T.volume_grad(q.reshape(-1, 3)).ravel()
+        q = q + (T.V0 - T.volume(q.reshape(-1, 3))) / (gq @ gq) * gq   # back onto V = V0
+        assert np.linalg.norm(x.ravel() - q) >= np.linalg.norm(r) - 1e-12
+    # a large violation: the iteration stops at its cap, close to the surface
+    x2 = mt.rest * np.array([1.05, 0.97, 1.1])
+    p2, it2 = T.volume_project(x2)
+    assert it2 == 8 and T.volume(p2) == pytest.approx(T.V0, rel=1e-11)
+
+
+def test_hinge_stencil_properties(O, rbc):
+    mt, T = rbc
+    hv, hc, hr = T.hinges()
+    assert T.nH == 3 * mt.tris.shape[0] // 2
+    assert np.allclose(hc.sum(axis=1), 0, atol=1e-12)              # kills translations
+    # on the sphere the hinge vector is normal to the surface
+    u, tris = I.icosphere(3)
+    S = O.OracleType(u, tris, 1, 1, 1, 1, 1e-3)
+    hv, hc, hr = S.hinges()
+    b = np.einsum("hj,hjd->hd", hc, u[hv])
+    nrm = u[hv[:, 0]] + u[hv[:, 1]]
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    cosang = np.abs(np.einsum("hd,hd->h", b, nrm)) / np.linalg.norm(b, axis=1)
+    assert cosang.min() > 0.99
+    # rotation + translation leave |b| unchanged
+    R = rot(6)
+    X2 = u @ R.T + 3.0
+    b2 = np.einsum("hj,hjd->hd", hc, X2[hv])
+    assert np.allclose(np.linalg.norm(b2, axis=1), hr, rtol=1e-12)
+
+
+def test_flat_hinges_have_zero_rest_vector(O):
+    # one 4-way split of the tetrahedron without projection: the edges inside
+    # each original face are flat hinges
+    v, f = I.tetrahedron()
+    verts = [tuple(p) for p in v]
+    cache, faces = {}, []
+
+    def mid(a, b):
+        k = (min(a, b), max(a, b))
+        if k not in cache:
+            verts.append(tuple((np.array(verts[a]) + verts[b]) / 2))
+            cache[k] = len(verts) - 1
+        return cache[k]
+
+    for a, b, c in f:
+        ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+        faces += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+    V, F = np.array(verts), np.array(faces, np.int32)
+    T = O.OracleType(V, F, 1, 1, 1, 1, 1e-3)
+    hv, hc, hr = T.hinges()
+    flat = np.isclose(hr, 0, atol=1e-12)
+    assert flat.sum() == 12                      # 3 inner edges per original face
+    assert np.all(hr[~flat] > 0.1)
+
+
+# --------------------------------------------------------------- matrix P
+def test_P_structure_and_solve(O, rbc):
+    mt, T = rbc
+    P = T.P_dense()
+    nV = mt.nV
+    m = 1.0 / nV
+    assert np.allclose(P, P.T, atol=0)
+    # elastic parts annihilate constants: P 1 = (m/h^2 + k_vol) 1
+    assert np.allclose(P.sum(axis=1), m / mt.material.dt ** 2 + mt.material.k_vol, rtol=1e-12)
+    # library Cholesky + solve of the same matrix
+    L = np.linalg.cholesky(P)
+    b = np.random.default_rng(7).standard_normal((nV, 3))
+    ref = np.linalg.solve(L.T, np.linalg.solve(L, b))
+    x = T.solve(b)
+    assert np.allclose(x, ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
+    assert np.linalg.norm(P @ x - b) <= 1e-12 * np.linalg.norm(b)
+    assert T.nnzL < nV * nV / 4                  # the RCM envelope is sparse
+
+
+def test_P_quadratic_form_at_rest(O, rbc):
+    # F(rest) has orthonormal columns, so x^T A_t^T A_t x summed over xyz = 2 per
+    # triangle: sum_c X_c^T P X_c = sum_t 2 (ks+ka) A_t + kb sum_e |b_rest|^2 + (m/h^2 + kv)|X|^2
+    mt, T = rbc
+    P = T.P_dense()
+    X = mt.rest
+    mat = mt.material
+    e = X[mt.tris[:, 1]] - X[mt.tris[:, 0]]
+    f = X[mt.tris[:, 2]] - X[mt.tris[:, 0]]
+    area = 0.5 * np.linalg.norm(np.cross(e, f), axis=1)
+    hv, hc, hr = T.hinges()
+    expect = (2 * (mat.k_strain + mat.k_area) * area.sum() + mat.k_bend * (hr ** 2).sum()
+              + (1.0 / mt.nV / mat.dt ** 2 + mat.k_vol) * (X ** 2).sum())
+    got = np.einsum("vc,vw,wc->", X, P, X)
+    assert got == pytest.approx(expect, rel=1e-12)
+
+
+# ------------------------------------------------------------------ energy
+def test_rest_state_is_stationary(O, rbc):
+    mt, T = rbc
+    R, t = rot(8), np.array([50.0, 120.0, 7.0])
+    x = mt.rest @ R.T + t
+    e, g, terms = T.energy(x, x)
+    assert e < 1e-24 and np.abs(g).max() < 1e-12
+    xo, vo = T.step(x, np.zeros_like(x), np.zeros_like(x))
+    assert np.abs(xo - x).max() < 1e-13 * np.abs(x).max()
+    assert np.abs(vo).max() < 1e-9
+
+
+@pytest.mark.parametrize("term", [1, 2, 4, 8, 16])
+def test_gradient_central_differences(O, term):
+    rest, tris, T = small_rbc(O, 1)
+    rng = np.random.default_rng(9 + term)
+    x = rest * 1.08 + 0.08 * rng.standard_normal(rest.shape)
+    y = rest + 0.05 * rng.standard_normal(rest.shape)
+    e, g, _ = T.energy(x, y, mask=term)
+    h = 1e-6
+    fd = np.zeros_like(x)
+    for i in range(x.shape[0]):
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, c] += h
+            xm[i, c] -= h
+            fd[i, c] = (T.energy(xp, y, term, grad=False)[0] - T.energy(xm, y, term, grad=False)[0]) / (2 * h)
+    assert np.linalg.norm(g - fd) <= 1e-6 * np.linalg.norm(g), term
+
+
+def test_energy_rigid_invariance(O, plt):
+    mt, T = plt
+    rng = np.random.default_rng(10)
+    x = mt.rest * 1.1 + 0.05 * rng.standard_normal(mt.rest.shape)
+    y = mt.rest + 0.03 * rng.standard_normal(mt.rest.shape)
+    R, t = rot(11), np.array([-3.0, 40.0, 2.5])
+    e1, g1, t1 = T.energy(x, y)
+    e2, g2, t2 = T.energy(x @ R.T + t, y @ R.T + t)
+    assert np.allclose(t1, t2, rtol=1e-10, atol=1e-14)
+    assert np.allclose(g1 @ R.T, g2, atol=1e-10 * np.abs(g1).max())
+
+
+# -------------------------------------------------------------- time step
+def seeded_cell(mt, seed, amp=0.1):
+    g = I.materialise(I.Group(mt, 1, seed, amp=amp))
+    return g.x0[0], g.v0[0], g.f_ext[0]
+
+
+def test_step_rigid_motion_invariance(O, rbc):
+    mt, T = rbc
+    xn, vn, f = seeded_cell(mt, 12, amp=2.0)
+    vn = vn + 0.5 * np.random.default_rng(13).standard_normal(vn.shape)
+    x1, v1 = T.step(xn, vn, f)
+    R, t = rot(14), np.array([10.0, -20.0, 30.0])
+    x2, v2 = T.step(xn @ R.T + t, vn @ R.T, f @ R.T)
+    assert np.abs(x1 @ R.T + t - x2).max() < 1e-9 * mt.radius
+    assert np.abs(v1 @ R.T - v2).max() < 1e-6
+
+
+def test_step_conserves_linear_momentum(O, rbc):
+    mt, T = rbc
+    rng = np.random.default_rng(15)
+    xn = mt.rest * np.array([1.1, 0.95, 1.2]) + 0.03 * rng.standard_normal(mt.rest.shape)
+    vn = rng.standard_normal(mt.rest.shape)
+    x1, v1 = T.step(xn, vn, np.zeros_like(xn))
+    assert np.allclose(v1.mean(axis=0), vn.mean(axis=0), atol=1e-9)
+    assert not np.allclose(v1, vn)
+
+
+def test_step_energy_monotone(O, rbc):
+    mt, T = rbc
+    xn, vn, f = seeded_cell(mt, 16, amp=5.0)
+    vn = vn + np.random.default_rng(17).standard_normal(vn.shape)
+    for m in (5, 0):
+        x1, v1, tr = T.step(xn, vn, f, m=m, trace=True)
+        assert tr["caps"] == 0
+        assert np.all(np.diff(tr["g"]) <= 0), tr["g"]
+        assert tr["g"][-1] < tr["g"][0]
+
+
+def test_pure_pd_is_local_global_iteration(O):
+    # with no history and alpha = 1 accepted, x^{k+1} = P^{-1}(P x^k - grad g(x^k))
+    rest, tris, T = small_rbc(O, 2)
+    rng = np.random.default_rng(18)
+    xn = rest * 1.05 + 0.02 * rng.standard_normal(rest.shape)
+    vn = 0.1 * rng.standard_normal(rest.shape)
+    f = 0.1 * rng.standard_normal(rest.shape)
+    x1, _, tr = T.step(xn, vn, f, K=1, m=0, trace=True)
+    assert tr["alpha"][0] == 1.0
+    y = xn + T.dt * vn + T.dt ** 2 * rest.shape[0] * f
+    _, g, _ = T.energy(y, y)
+    P = T.P_dense()
+    assert np.allclose(x1, np.linalg.solve(P, P @ y - g), atol=1e-12)
+
+
+def test_step_converges_to_stationary_point_newtons_law(O, rbc):
+    # Eq. (Newton2nd) with C = 0:  M (v_{n+1} - v_n)/h = F_int(x_{n+1}) + F_ext
+    mt, T = rbc
+    xn, vn, f = seeded_cell(mt, 19, amp=20.0)
+    vn = vn + 2.0 * np.random.default_rng(20).standard_normal(vn.shape)
+    x1, v1 = T.step(xn, vn, f, K=40)
+    h, m = mt.material.dt, 1.0 / mt.nV
+    _, gint, _ = T.energy(x1, x1, mask=30)          # sum_i grad E_i = -F_int
+    resid = m * (v1 - vn) / h - (-gint + f)
+    assert np.abs(resid).max() < 1e-7 * np.abs(m * (v1 - vn) / h).max()
+
+
+def test_tetrahedron_matches_brute_force_newton(O):
+    v, tris = I.tetrahedron()
+    T = O.OracleType(v, tris, 1.0, 5.0, 0.05, 10.0, 0.05)
+    rng = np.random.default_rng(21)
+    xn = v + 0.05 * rng.standard_normal(v.shape)
+    vn = 2.0 * rng.standard_normal(v.shape)
+    f = 5.0 * rng.standard_normal(v.shape)
+    x_orc, _ = T.step(xn, vn, f, K=200)
+    y = xn + T.dt * vn + T.dt ** 2 * 4 * f
+    # damped Newton with a finite-difference Hessian of the analytic gradient
+    x = y.copy()
+    for _ in range(100):
+        e, g, _ = T.energy(x, y)
+        if np.linalg.norm(g) < 1e-13:
+            break
+        H = np.zeros((12, 12))
+        hh = 1e-6
+        for i in range(12):
+            xp, xm = x.ravel().copy(), x.ravel().copy()
+            xp[i] += hh
+            xm[i] -= hh
+            H[:, i] = (T.energy(xp, y)[1].ravel() - T.energy(xm, y)[1].ravel()) / (2 * hh)
+        H = 0.5 * (H + H.T)
+        w = np.linalg.eigvalsh(H)
+        mu = max(0.0, 1e-8 - w.min())
+        d = -np.linalg.solve(H + mu * np.eye(12), g.ravel()).reshape(4, 3)
+        a = 1.0
+        while T.energy(x + a * d, y, grad=False)[0] > e and a > 1e-12:
+            a *= 0.5
+        x = x + a * d
+    assert np.abs(x - x_orc).max() < 1e-9
+    assert np.abs(x - y).max() > 1e-3             # a non-trivial minimiser
