@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark of the npFEM time step on GB300: cell-iterations per second.
+
+Default workload: 50000 red blood cells (642-vertex Evans-Fung mesh) + 5000
+platelets (162-vertex ellipsoid) in a 200^3 box, seeded Fourier + shear
+forces of amplitude 0.3, BF16 tensor-core global step with FP32
+accumulation and FP64-residual refinement to 1e-6, FP32 local step, K = 10
+L-BFGS iterations per step, the step replayed as one CUDA graph.
+
+One "step" = one npfem_step over all cells.  value = cells x K x steps /
+time (device CUDA events on the solver's stream, max over ranks).  Inputs
+(positions, forces: ~1.6 GB) are larger than L2 (129 MB), so no flush is
+needed.  Also reported: the same workload in plain FP64 on the GPU, the
+relative position error of both against the FP64 oracle on sampled cells,
+the end-to-end number through the C ABI with host buffers, per-kernel
+CUDA-event times, the roofline of the dominant kernel and the oracle timed on
+the host cores.
+
+Multi-GPU: one process per GPU (torchrun); cells are independent, each rank
+steps its own suspension (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-iterations/sec at 50k cells, mixed vs FP64 GPU at ≤1e-6 rel pos error"
+UNIT = "cell-iterations/s"
+
+
+# ---------------------------------------------------------------- helpers
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes_iterate(nV, cells, K, m, b, bf16):
+    """Bytes one k_iterate launch must move on average (per type, all its cells).
+
+    Per cell and iteration k (vectors of 3 nV values of b bytes):
+      read z, grad g, delta, y_rel                          4 vectors
+      read the history pairs of the two L-BFGS loops       2 min(k, m) + 2 min(k+1, m) vectors
+      write delta, grad g, the new pair (s, y), q            5 vectors (+ BF16 copy of q)
+      last iteration instead of q and the first loop: read x_n, v_n, F_ext,
+      write x_{n+1}, v_{n+1} (FP64).
+    """
+    n3 = 3 * nV
+    tot = 0.0
+    for k in range(K):
+        last = k == K - 1
+        vec = 4 + 2 * min(k, m) + 4
+        byt = vec * n3 * b
+        if last:
+            byt += 5 * n3 * 8
+        else:
+            byt += (2 * min(k + 1, m) + 1) * n3 * b + (n3 * 2 if bf16 else 0)
+        tot += byt
+    return tot / K * cells
+
+
+def algorithmic_gemm(nV, cells, bf16):
+    """One global-step apply: read q (operand type), write z (FP32); 2 nV flops per element."""
+    n = 3 * cells * nV
+    return n * ((2 if bf16 else 4) + 4), 2.0 * nV * n
+
+
+# ---------------------------------------------------------------- reference
+def run_reference(args, workload):
+    """The FP64 CPU oracle timed on the host cores (the reference arm)."""
+    from paper_1911_03062_gb300 import inputs as I
+    from oracle import oracle as O
+    O.build()
+    groups = I.workload_groups(workload)
+    threads = os.cpu_count() or 1
+    sample_rbc, sample_plt = args.ref_sample
+    picks = []
+    for g, n in zip(groups, (sample_rbc, sample_plt)):
+        sub = I.Group(g.mtype, n, g.seed, g.amp)
+        picks.append((I.materialise(sub), O.OracleType.from_mesh_type(g.mtype)))
+    state = [(g.x0.copy(), g.v0.copy()) for g, _ in picks]
+
+    def one_step():
+        for i, (g, T) in enumerate(picks):
+            x, v = state[i]
+            state[i] = T.step_cells(x, v, g.f_ext, K=10, m=5, threads=threads)
+
+    for _ in range(args.warmup):
+        one_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step()
+    dt = time.perf_counter() - t0
+    cells = sample_rbc + sample_plt
+    value = cells * 10 * args.steps / dt
+    sample = f"{sample_rbc} RBC + {sample_plt} PLT cells of the workload per step (same seeds), K=10"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": workload, "cells_per_step": cells, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(workload, n_rbc=768, n_plt=96):
+    """Oracle on the host cores over a bounded sample (1 step, K=10)."""
+    from paper_1911_03062_gb300 import inputs as I
+    from oracle import oracle as O
+    O.build()
+    threads = os.cpu_count() or 1
+    groups = I.workload_groups(workload)
+    t_total, cells = 0.0, 0
+    for g, n in zip(groups, (n_rbc, n_plt)):
+        sub = I.materialise(I.Group(g.mtype, n, g.seed, g.amp))
+        T = O.OracleType.from_mesh_type(g.mtype)
+        t0 = time.perf_counter()
+        T.step_cells(sub.x0, sub.v0, sub.f_ext, K=10, m=5, threads=threads)
+        t_total += time.perf_counter() - t0
+        cells += n
+    return {"value": cells * 10 / t_total, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n_rbc} RBC + {n_plt} PLT cells of the workload, 1 step x 10 iterations, "
+                      f"cells split over {threads} host threads"}
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="rbc50k_plt5k")
+    ap.add_argument("--precision", default=None, help="bf16 | tf32 | fp64 (default: the workload's)")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 form (0: skip)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-sample", type=int, nargs=2, default=[160, 16])
+    args = ap.parse_args()
+    rank, world, local = env_rank()
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, args.workload)
+        return
+
+    import torch
+    from paper_1911_03062_gb300 import inputs as I
+    from paper_1911_03062_gb300.npfem import Solver
+    from paper_1911_03062_gb300 import build as B
+    B.build()
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    wl = I.WORKLOADS[args.workload]
+    precision = args.precision or wl["precision"]
+    groups = I.workload_groups(args.workload)
+    for g in groups:
+        g.seed += 7919 * rank           # each rank steps its own suspension
+        I.materialise(g)
+    ncells = sum(g.n_cells for g in groups)
+    K = 10
+    f_host = np.concatenate([g.f_ext.ravel() for g in groups])
+    stream = torch.cuda.Stream()
+
+    def make(prec):
+        s = Solver(precision=prec, stream=stream)
+        for g in groups:
+            s.add_cells(s.create_type(g.mtype), g.x0, g.v0)
+        return s
+
+    f_dev = torch.from_numpy(f_host).to("cuda")
+    s = make(precision)
+    ndofs = s.num_dofs
+
+    # ---- device-resident timed region (graph replay)
+    for _ in range(args.warmup):
+        s.step(f_dev)
+    s.sync()
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.step(f_dev)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    s.sync()
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    value = world * ncells * K * args.steps / t
+    st = s.stats()
+    launches = st["launches_per_step"] * args.steps
+
+    # ---- parity of the timed trajectory on sampled cells vs the FP64 oracle
+    total_steps = args.warmup + args.steps
+    parity = None
+    if rank == 0:
+        from oracle import oracle as O
+        x = s.positions()
+        errs, off = [], 0
+        for g in groups:
+            n = g.n_cells * g.mtype.nV * 3
+            xg = x[off:off + n].reshape(g.n_cells, g.mtype.nV, 3)
+            off += n
+            idx = np.unique(np.linspace(0, g.n_cells - 1, 3).astype(int))
+            T = O.OracleType.from_mesh_type(g.mtype)
+            xo, vo = g.x0[idx].copy(), g.v0[idx].copy()
+            for _ in range(total_steps):
+                xo, vo = T.step_cells(xo, vo, g.f_ext[idx], K=K, m=5, threads=4)
+            errs.append(float(np.linalg.norm(xg[idx] - xo, axis=2).max() / g.mtype.radius))
+        parity = {"rel_pos_err": max(errs), "sampled_cells": 3 * len(groups), "steps": total_steps,
+                  "tolerance": 1e-6 if precision != "fp64" else 1e-10}
+
+    # ---- per-kernel CUDA-event times (same steps, events around every launch)
+    s.profile(True)
+    s.step(f_dev)                        # capture + warm
+    s.profile_read(reset=True)
+    for _ in range(args.steps):
+        s.step(f_dev)
+    prof = s.profile_read(reset=True)
+    s.profile(False)
+
+    # ---- end to end: host forces in, host positions out, through the C ABI
+    e2e = None
+    if not args.no_e2e:
+        f_pin = torch.from_numpy(f_host).pin_memory()
+        x_pin = torch.empty(ndofs, dtype=torch.float64).pin_memory()
+        fnp, xnp = f_pin.numpy(), x_pin.numpy()
+        s.step(fnp)
+        s.positions(out=xnp)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s.step(fnp)
+            s.positions(out=xnp)
+        te = max_over_ranks(time.perf_counter() - t0)
+        barrier()
+        e2e = {"value": world * ncells * K * args.steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": ndofs * 8, "d2h_bytes_per_step": ndofs * 8}
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+
+    # ---- the plain FP64 GPU form on the same workload
+    fp64 = None
+    if args.fp64_steps > 0 and precision != "fp64":
+        s64 = make("fp64")
+        s64.step(f_dev)
+        s64.sync()
+        barrier()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(args.fp64_steps):
+            s64.step(f_dev)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        t64 = max_over_ranks(ea.elapsed_time(eb) / 1e3)
+        fp64 = {"value": world * ncells * K * args.fp64_steps / t64, "unit": UNIT, "steps": args.fp64_steps,
+                "ms_per_step": t64 / args.fp64_steps * 1e3}
+        if rank == 0:
+            from oracle import oracle as O
+            x = s64.positions()
+            errs, off = [], 0
+            for g in groups:
+                n = g.n_cells * g.mtype.nV * 3
+                xg = x[off:off + n].reshape(g.n_cells, g.mtype.nV, 3)
+                off += n
+                idx = np.array([0, g.n_cells - 1])
+                T = O.OracleType.from_mesh_type(g.mtype)
+                xo, vo = g.x0[idx].copy(), g.v0[idx].copy()
+                for _ in range(1 + args.fp64_steps):
+                    xo, vo = T.step_cells(xo, vo, g.f_ext[idx], K=K, m=5, threads=2)
+                errs.append(float(np.linalg.norm(xg[idx] - xo, axis=2).max() / g.mtype.radius))
+            fp64["rel_pos_err"] = max(errs)
+            fp64["mixed_over_fp64"] = value / fp64["value"]
+        s64.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (largest share of event time)
+    hbm, bf_burst, bf_sust, peak_src = load_peaks()
+    names = {k: v for k, v in prof.items()}
+    dom = max(names, key=lambda k: names[k][0]) if names else None
+    total_ms = sum(v[0] for v in names.values())
+    bf16 = precision == "bf16"
+    b = 8 if precision == "fp64" else 4
+    roof = None
+    if dom in ("iterate", "predict"):
+        byts = sum(algorithmic_bytes_iterate(g.mtype.nV, g.n_cells, K, 5, b, bf16) for g in groups)
+        launches_per_step = prof[dom][1] / args.steps
+        avg_ms = prof[dom][0] / prof[dom][1]
+        per_launch = byts / (launches_per_step if launches_per_step else 1)
+        ach = per_launch / (avg_ms / 1e3) / 1e9
+        roof = {"kernel": "k_iterate", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": peak_src}
+    elif dom in ("gemm", "gemm_refine"):
+        byts = sum(algorithmic_gemm(g.mtype.nV, g.n_cells, bf16)[0] for g in groups)
+        launches_per_step = prof[dom][1] / args.steps
+        avg_ms = prof[dom][0] / prof[dom][1]
+        ach = byts / launches_per_step / (avg_ms / 1e3) / 1e9
+        roof = {"kernel": "k_gemm_tc", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": peak_src}
+    kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / total_ms if total_ms else None}
+               for k, v in names.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": precision if precision != "fp64" else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "cells": ncells, "rbc_vertices": 642, "plt_vertices": 162,
+                       "iters_per_step": K, "history": 5, "precision": precision,
+                       "local_step": "fp32" if precision != "fp64" else "fp64",
+                       "l2": "inputs larger than L2 (state + forces ~1.6 GB), no flush",
+                       "parallelism": f"{world} independent ranks" if world > 1 else "1 GPU"},
+            "clocks": clk, "gpu_launches": launches, "parity": parity, "fp64_gpu": fp64, "e2e": e2e,
+            "roofline": roof, "kernels": kernels}
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * npfem.h -- C ABI of the GB300 npFEM cell-suspension solver.
+ *
+ * The library advances a batch of closed triangulated membranes (red blood
+ * cells, platelets) through implicit-Euler time steps of the nodal projective
+ * FEM solver of arXiv 1911.03062 (Supplementary Sec. 2.1):
+ *
+ *   v_{n+1} = (x_{n+1} - x_n) / h                                   Eq. (vel)
+ *   x_{n+1} = argmin g(x),  g(x) = 1/(2h^2) |M^{1/2}(x - y_n)|_F^2 + sum_i E_i(x)
+ *   y_n     = x_n + h v_n + h^2 M^{-1} F_ext                       Eq. (genericOptimizationNewton), C = 0
+ *
+ * minimised by a fixed number of quasi-Newton iterations
+ * x^{k+1} = x^k - H grad g(x^k) (the unnumbered update after that equation),
+ * with H an L-BFGS operator whose initial matrix is the inverse of the
+ * constant SPD matrix P = M/h^2 + sum_i w_i A_i^T A_i of the quadratic
+ * (projective) energies, and an Armijo line search.
+ *
+ * Conventions for every call below
+ *  - Return value: NPFEM_OK (0) or a negative NPFEM_E* code; the message of
+ *    the last failure is available from npfem_last_error().
+ *  - Host arrays are read or written during the call only; the caller keeps
+ *    ownership.  The context owns all device memory it allocates.
+ *  - Per-cell arrays use the public layout: cell-major in the order cells were
+ *    added, each cell nV_type x 3 doubles (vertex major, xyz innermost).
+ *  - Units are the caller's (the workloads are non-dimensional).
+ *  - A context is used by one host thread at a time.  All device work of a
+ *    context runs on its stream (npfem_options.cuda_stream or a stream the
+ *    context creates).
+ */
+#ifndef NPFEM_H
+#define NPFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NPFEM_OK 0
+#define NPFEM_EINVAL -1      /* bad argument, size, or mesh (open, non-manifold, degenerate) */
+#define NPFEM_ENOMEM -2      /* device or host allocation failed */
+#define NPFEM_ENOTSPD -3     /* the system matrix P is not positive definite */
+#define NPFEM_ECUDA -4       /* a CUDA call failed (message names it) */
+#define NPFEM_ENONFINITE -5  /* NaN/Inf in forces or state; message names the cell */
+#define NPFEM_ETIMEOUT -6    /* a bounded device wait expired (kernel returned early) */
+#define NPFEM_ESTATE -7      /* call not valid in the current state */
+
+#define NPFEM_MAX_HISTORY 8
+
+typedef struct npfem_ctx npfem_ctx;
+
+/* Arithmetic of the global-step apply z = P^{-1} q.
+ *  NPFEM_FP64        : everything in FP64 (SIMT); the comparison form.
+ *  NPFEM_MIXED_TF32  : FP32 local step; P^{-1} q on tcgen05 tensor cores in
+ *                      TF32 with FP32 accumulation, refined against an FP64
+ *                      residual q - P z until |r|/|q| <= refine_tol.
+ *  NPFEM_MIXED_BF16  : as above with BF16 operands. */
+typedef enum { NPFEM_FP64 = 0, NPFEM_MIXED_TF32 = 1, NPFEM_MIXED_BF16 = 2 } npfem_precision;
+
+typedef struct {
+    int precision;          /* npfem_precision */
+    int iters;              /* K quasi-Newton iterations per step (default 10) */
+    int history;            /* L-BFGS history m, 0..NPFEM_MAX_HISTORY (default 5) */
+    double armijo_c1;       /* sufficient-decrease constant (default 1e-4) */
+    int max_backtracks;     /* halvings of the step before the last trial is taken (default 8) */
+    double refine_tol;      /* mixed forms: target |q - P z| / |q| per cell and component (default 1e-6) */
+    int refine_max;         /* mixed forms: maximum refinement sweeps (default 3) */
+    int use_graph;          /* capture one step as a CUDA graph and replay it (default 1) */
+    int device;             /* CUDA device ordinal (default 0) */
+    void *cuda_stream;      /* cudaStream_t to run on, or NULL for a context-owned stream */
+    const char *autotune_cache; /* file for tuned GEMM tile choices, or NULL (tune, keep in memory) */
+} npfem_options;
+
+/* Material and time step of one mesh type.  Element weights follow the
+ * projective-dynamics reading of the paper's energies: w_strain = k_strain *
+ * rest area, w_area = k_area * rest area (per triangle), w_bend = k_bend (per
+ * interior edge), w_vol = k_vol (per cell). */
+typedef struct {
+    double k_strain, k_area, k_bend, k_vol;
+    double dt;              /* h */
+} npfem_material;
+
+/* Per-step counters of the last completed npfem_step (summed over cells). */
+typedef struct {
+    int64_t cell_iterations;   /* cells x K */
+    int64_t backtracks;        /* line-search halvings */
+    int64_t capped_searches;   /* searches that hit max_backtracks */
+    int64_t fallbacks;         /* non-descent directions replaced by -P^{-1} grad g */
+    int64_t refine_sweeps;     /* refinement sweeps applied (mixed forms) */
+    double max_refine_residual;/* largest final |q - P z|/|q| seen (mixed forms) */
+    double energy_sum;         /* sum over cells of g(x_{n+1}) */
+    int64_t launches_per_step; /* kernels one npfem_step launches */
+} npfem_step_stats;
+
+/* Kernel classes of the per-kernel timing (npfem_profile_read). */
+#define NPFEM_K_PREDICT 0        /* inertial predictor + first local step */
+#define NPFEM_K_ITERATE 1        /* fused L-BFGS + line search + local steps */
+#define NPFEM_K_FALLBACK 2       /* the same kernel over non-descent cells */
+#define NPFEM_K_GEMM 3           /* global-step apply z = P^{-1} q */
+#define NPFEM_K_GEMM_REFINE 4    /* refinement correction applies */
+#define NPFEM_K_RESIDUAL 5       /* FP64 refinement residuals */
+#define NPFEM_K_FALLBACK_APPLY 6 /* P^{-1} grad for non-descent cells */
+#define NPFEM_KCLASSES 8
+
+typedef struct {
+    double ms[NPFEM_KCLASSES];         /* summed CUDA-event time per class */
+    int64_t launches[NPFEM_KCLASSES];  /* launches timed per class */
+} npfem_kernel_times;
+
+/* Fill *opt with the defaults listed above. */
+void npfem_default_options(npfem_options *opt);
+
+/* Create a context on opt->device.  opt may be NULL (defaults).
+ * Errors: EINVAL (bad option values), ECUDA, ENOMEM. */
+int npfem_create(const npfem_options *opt, npfem_ctx **out);
+
+/* Release every resource of the context (NULL is ignored). */
+void npfem_destroy(npfem_ctx *ctx);
+
+/* Register a mesh type: a closed, consistently oriented (outward CCW)
+ * triangle surface with its rest shape, lumped vertex masses and material.
+ *   nV, rest_xyz : nV x 3 rest positions (the rest state of every cell of the type)
+ *   nT, tris     : nT x 3 vertex indices
+ *   vertex_mass  : nV masses, or NULL for 1/nV each (total mass 1; Supp. Sec. 2.1
+ *                  lumps the cell mass on its vertices)
+ * Builds the type's element constants and P (Supp. Sec. 2.1, the Hessian
+ * approximation "of quadratic form"), inverts P once on the GPU in FP64 and
+ * keeps P^{-1} (and its TF32/BF16 copy in the mixed forms).
+ * Errors: EINVAL (nV < 4, index out of range, open or non-manifold mesh,
+ * inconsistent orientation, degenerate triangle, inward orientation,
+ * non-positive mass or dt), ENOTSPD, ENOMEM, ECUDA, ESTATE (after cells were
+ * added to a graph-captured context the call is still allowed; the graph is
+ * rebuilt on the next step). */
+int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz,
+                           int nT, const int32_t *tris, const double *vertex_mass,
+                           const npfem_material *mat, int *type_id);
+
+/* Append n_cells cells of type type_id with initial positions x0 and
+ * velocities v0 (NULL = zero), both n_cells x nV x 3 doubles.  The new cells
+ * follow all earlier cells in the public layout; *first_cell (may be NULL)
+ * receives the index of the first new cell.
+ * Errors: EINVAL (unknown type, n_cells < 0), ENONFINITE, ENOMEM, ECUDA. */
+int npfem_add_cells(npfem_ctx *ctx, int type_id, int n_cells, const double *x0,
+                    const double *v0, int64_t *first_cell);
+
+/* Number of doubles of one per-cell array over all cells (sum of 3 nV). */
+size_t npfem_num_dofs(const npfem_ctx *ctx);
+
+/* Advance every cell by one time step of its type's h under the external
+ * forces f_ext (npfem_num_dofs doubles, public layout).  f_ext_on_device != 0
+ * means f_ext is a device pointer readable on the context's stream (no copy);
+ * otherwise it is host memory, copied to the device during the call.
+ * The call enqueues the work and returns; device errors are reported by the
+ * next call that synchronises (get_*, stats, npfem_sync).
+ * Errors: EINVAL, ESTATE (no cells), ECUDA. */
+int npfem_step(npfem_ctx *ctx, const double *f_ext, int f_ext_on_device);
+
+/* Wait for the context's stream; report device-side errors (ENONFINITE with
+ * the cell index, ETIMEOUT) raised since the last synchronising call. */
+int npfem_sync(npfem_ctx *ctx);
+
+/* Copy the current positions / velocities (n_doubles must equal
+ * npfem_num_dofs) into out: host memory, or device memory when
+ * out_on_device != 0.  Synchronises the stream.  Errors: EINVAL, ECUDA and
+ * pending device errors. */
+int npfem_get_positions(npfem_ctx *ctx, double *out, size_t n_doubles, int out_on_device);
+int npfem_get_velocities(npfem_ctx *ctx, double *out, size_t n_doubles, int out_on_device);
+
+/* Replace the state of all cells (checkpoint resume).  v may be NULL (zero).
+ * Errors: EINVAL, ENONFINITE, ECUDA. */
+int npfem_set_state(npfem_ctx *ctx, const double *x, const double *v, size_t n_doubles);
+
+/* Counters of the last completed step (synchronises). */
+int npfem_stats(npfem_ctx *ctx, npfem_step_stats *out);
+
+/* Global-step building block: z = P^{-1} q for n_cols right-hand sides of
+ * mesh type type_id, through the same apply (and, in the mixed forms, the
+ * same refinement) as npfem_step.  q, z: device pointers, n_cols x nV
+ * doubles (one column = one component of one cell, vertex contiguous).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int npfem_apply_pinv(npfem_ctx *ctx, int type_id, const double *q, double *z, int n_cols);
+
+/* Per-kernel timing: when enabled, every kernel launch of a step is
+ * bracketed by CUDA events on the context stream (recorded into the step's
+ * graph) and npfem_step waits for the step to finish to accumulate the
+ * elapsed times per kernel class.  Enabling or disabling rebuilds the graph.
+ * Errors: ECUDA. */
+int npfem_profile(npfem_ctx *ctx, int enable);
+
+/* Copy the accumulated per-class times and launch counts; reset != 0 zeroes
+ * them afterwards. */
+int npfem_profile_read(npfem_ctx *ctx, npfem_kernel_times *out, int reset);
+
+/* Message of the last failure of this context (never NULL). */
+const char *npfem_last_error(const npfem_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NPFEM_H */

@@ -1,0 +1,281 @@
+// gemm_tc.cuh -- the global step on tcgen05 tensor cores (sm_103a):
+//
+//   Z[r][v] (+)= sum_k Q[r][k] * Pinv[v][k]      (z = P^{-1} q for every RHS row r)
+//
+// Rows r are the stacked x/y/z right-hand sides of all cells of one mesh type
+// (one row = one component of one cell, vertex contiguous, stride nVp), so the
+// apply is one [3C x nV] x [nV x nV] product with the type's shared inverse
+// (Supplementary Sec. 2.1: the constant Hessian approximation of the
+// quadratic energies, applied to all cells at once).
+//
+// Mapping: MMA A operand = a 128-row tile of Q (K-major), B operand = an
+// N-row tile of P^{-1} (K-major, N <= 256), accumulator D = 128 x N FP32 in
+// tensor memory.  Operands are staged by TMA (128-byte swizzle) through an
+// S-stage mbarrier pipeline; one thread issues TMA, one thread issues
+// tcgen05.mma, all four warps drain TMEM (tcgen05.ld) and store Z.
+// Element type: BF16 (kind::f16) or FP32 read as TF32 (kind::tf32), FP32
+// accumulation in both.  Every wait is bounded: on expiry the kernel records
+// NPFEM_ETIMEOUT, waits (bounded) for its own copies, frees TMEM and returns.
+#pragma once
+
+#include <cuda.h>
+#include "common.cuh"
+
+namespace npfem {
+namespace tc {
+
+constexpr int BM = 128;          // rows of Q per tile (= TMEM lanes)
+constexpr int KB_BYTES = 128;    // bytes of K per stage row (one 128B swizzle atom)
+constexpr long long WAIT_LIMIT = 1ll << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (long long i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row core-matrix groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: D = FP32, A/B format (1 = BF16 for kind::f16,
+// 2 = TF32 for kind::tf32), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_fmt, int M, int N) {
+    return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    if (TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 lanes x 32 columns of 32-bit accumulators: thread (lane) gets its row's 32 columns.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct GemmArgs {
+    int rows, nV, nVp;           // Q / Z: rows x nVp (K = nV valid columns)
+    int n_tile;                  // N of one tile (multiple of 16, <= 256)
+    int stages;
+    int accumulate;              // Z += product
+    const int *conv;             // per cell: skip tiles whose cells are all converged (or null)
+    float *Z;
+    DevStatus *st;
+};
+
+// smem: [stages][A 128 x 128B | B n_tile x 128B] (1024-aligned), then
+// full[stages], empty[stages], accum barrier, tmem address.
+template <bool TF32>
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapQ,
+                                                     const __grid_constant__ CUtensorMap mapP, GemmArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_tc[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * a.n_tile;
+    const int m0 = blockIdx.y * BM;
+    if (a.conv) {
+        // all cells of this row tile converged: nothing to correct
+        int c0 = m0 / 3, c1 = min(a.rows - 1, m0 + BM - 1) / 3;
+        int any = 0;
+        for (int c = c0 + threadIdx.x; c <= c1; c += blockDim.x) any |= !a.conv[c];
+        if (!__syncthreads_or(any)) return;
+    }
+    uint32_t base = smem_u32(smem_tc);
+    uint32_t pad = ((base + 1023u) & ~1023u) - base;
+    uint8_t *tiles = smem_tc + pad;
+    const uint32_t a_bytes = BM * KB_BYTES, b_bytes = (uint32_t)a.n_tile * KB_BYTES;
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + (size_t)a.stages * stage_bytes);
+    uint64_t *empty = full + a.stages;
+    uint64_t *accum = empty + a.stages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+    __shared__ int abort_sh;
+    volatile int &abort_flag = abort_sh;
+
+    const int kblocks = (a.nV * (TF32 ? 4 : 2) + KB_BYTES - 1) / KB_BYTES;
+    const int k_per_block = TF32 ? 32 : 64;      // elements of K in one stage
+    const uint32_t tcols = a.n_tile <= 32 ? 32 : (a.n_tile <= 64 ? 64 : (a.n_tile <= 128 ? 128 : 256));
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < a.stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) tmem_alloc(tmem_slot, tcols);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = make_idesc(TF32 ? 2u : 1u, BM, a.n_tile);
+
+    if (warp == 0 && lane == 0) {
+        // producer: TMA loads of A (Q rows) and B (P^{-1} rows), K in 128-byte steps
+        int issued_phase[8];
+        for (int s = 0; s < 8; ++s) issued_phase[s] = -1;
+        for (int kb = 0; kb < kblocks; ++kb) {
+            const int s = kb % a.stages;
+            const uint32_t round = kb / a.stages;
+            if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
+                dev_raise(a.st, DEV_ETIMEOUT, 1);
+                abort_flag = 1;
+                break;
+            }
+            if (abort_flag) break;
+            uint8_t *sa = tiles + (size_t)s * stage_bytes;
+            mbar_expect_tx(&full[s], stage_bytes);
+            tma_load_2d(sa, &mapQ, &full[s], kb * k_per_block, m0);
+            tma_load_2d(sa + a_bytes, &mapP, &full[s], kb * k_per_block, n0);
+            issued_phase[s] = round & 1;
+        }
+        // copies in flight must land before the block may exit
+        for (int s = 0; s < a.stages && s < 8; ++s)
+            if (issued_phase[s] >= 0 && !mbar_wait(&full[s], (uint32_t)issued_phase[s]))
+                dev_raise(a.st, DEV_ETIMEOUT, 2);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        bool ok = true;
+        for (int kb = 0; kb < kblocks; ++kb) {
+            const int s = kb % a.stages;
+            const uint32_t round = kb / a.stages;
+            if (!mbar_wait(&full[s], round & 1) || abort_flag) {
+                dev_raise(a.st, DEV_ETIMEOUT, 3);
+                abort_flag = 1;
+                ok = false;
+                break;
+            }
+            fence_after();
+            const uint32_t sa = smem_u32(tiles + (size_t)s * stage_bytes);
+            const uint32_t sb = sa + a_bytes;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                // 32 bytes of K per instruction (16 BF16 or 8 TF32)
+                const uint64_t ad = desc_sw128(sa + 32 * k);
+                const uint64_t bd = desc_sw128(sb + 32 * k);
+                mma<TF32>(tmem, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+            }
+            mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(accum);
+    }
+    __syncwarp();
+    // epilogue: warp w owns TMEM lanes [32w, 32w + 32) = Q rows m0 + 32w + lane
+    bool have = mbar_wait(accum, 0);
+    if (!have) {
+        if (lane == 0) dev_raise(a.st, DEV_ETIMEOUT, 4);
+    }
+    __syncwarp();
+    fence_after();
+    const int row = m0 + warp * 32 + lane;
+    if (have) {
+        for (int c0 = 0; c0 < a.n_tile; c0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (row < a.rows && !(a.accumulate && a.conv && a.conv[row / 3])) {
+                float *zr = a.Z + (long long)row * a.nVp + n0 + c0;
+                const int lim = min(min(32, a.n_tile - c0), a.nV - (n0 + c0));
+                if (lim == 32) {
+                    float4 *z4 = reinterpret_cast<float4 *>(zr);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        float4 o = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        if (a.accumulate) {
+                            float4 p = z4[i];
+                            o.x += p.x; o.y += p.y; o.z += p.z; o.w += p.w;
+                        }
+                        z4[i] = o;
+                    }
+                } else {
+                    for (int i = 0; i < lim; ++i) zr[i] = a.accumulate ? zr[i] + v[i] : v[i];
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        fence_after();
+        tmem_dealloc(tmem, tcols);
+    }
+}
+
+}  // namespace tc
+}  // namespace npfem

@@ -1,0 +1,1168 @@
+// npfem.cu -- C ABI of the GB300 npFEM solver: context, mesh-type set-up,
+// cell storage, the time-step schedule (CUDA-graph captured) and the
+// global-step apply (FP64 SIMT, or tcgen05 TF32/BF16 with FP64-residual
+// iterative refinement).  See include/npfem.h for the contract of each call.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "npfem.h"
+#include "npfem_internal.h"
+
+using namespace npfem;
+
+// ------------------------------------------------------------ utilities
+namespace {
+
+struct Fail {
+    int code;
+};
+
+void fail(npfem_ctx *ctx, int code, const char *fmt, ...);
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) fail(ctx, NPFEM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+}  // namespace
+
+// ---------------------------------------------------------------- types
+struct MeshTypeImpl {
+    int nV = 0, nVp = 0, nT = 0, nH = 0;
+    double h = 0, ks = 0, ka = 0, kb = 0, kv = 0, V0 = 0;
+    // device constants
+    std::vector<void *> owned;
+    TypeConst<double> tc64{};
+    TypeConst<float> tc32{};
+    double *Pinv64 = nullptr;
+    float *Pinv32 = nullptr;
+    __nv_bfloat16 *Pinv16 = nullptr;
+    double *diag = nullptr, *minv = nullptr;
+    int *op = nullptr, *oj = nullptr;
+    float *ov = nullptr;
+    int n_off = 0;
+    // tensor-core GEMM configuration
+    int n_tile = 0, stages = 0;
+    CUtensorMap mapP{};
+    // cells
+    int ncells = 0, cap = 0;
+    std::vector<long long> pub_off_h;
+    long long *pub_off = nullptr;
+    double *xn = nullptr, *vn = nullptr;        // state SoA FP64
+    void *yrel = nullptr, *delta = nullptr, *grad = nullptr, *q = nullptr, *z = nullptr;
+    void *S = nullptr, *Y = nullptr, *rlo = nullptr;
+    __nv_bfloat16 *q16 = nullptr;
+    double *origin = nullptr, *rho = nullptr, *alpha = nullptr, *g = nullptr, *allow = nullptr;
+    int *hcount = nullptr, *hhead = nullptr, *conv = nullptr, *fb_list = nullptr, *fb_count = nullptr;
+    CUtensorMap mapQ{}, mapR{};
+    int ept = 8, block = 256, stash_T = 0;
+    size_t smem_step = 0;
+};
+
+struct npfem_ctx {
+    npfem_options opt{};
+    int device = 0, nsm = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<MeshTypeImpl *> types;
+    long long ndofs = 0;
+    double *d_f = nullptr;               // device copy of host forces (public layout)
+    double **d_fslot = nullptr;          // device slot: base of the forces read by the step
+    double *d_stage = nullptr;           // staging for get/set (public layout)
+    DevStatus *d_st = nullptr;
+    DevStatus *h_st = nullptr;           // pinned
+    int *d_any = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_valid = false;
+    bool stepped = false;
+    int smem_optin = 0;
+    // launch accounting and optional per-kernel CUDA-event timing
+    long long launches_per_step = 0, launch_counter = 0;
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;       // start/end pairs, one pair per launch of a step
+    std::vector<int> prof_cls;              // kernel class of each pair
+    size_t prof_next = 0, graph_prof_pairs = 0;
+    double prof_ms[NPFEM_KCLASSES] = {0};
+    long long prof_n[NPFEM_KCLASSES] = {0};
+    std::string err;
+};
+
+namespace {
+
+void fail(npfem_ctx *ctx, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    throw Fail{code};
+}
+
+template <typename F>
+int guard(npfem_ctx *ctx, F &&f) {
+    try {
+        f();
+        return NPFEM_OK;
+    } catch (Fail &e) {
+        return e.code;
+    } catch (std::bad_alloc &) {
+        if (ctx) ctx->err = "host allocation failed";
+        return NPFEM_ENOMEM;
+    }
+}
+
+template <typename T>
+T *dalloc(npfem_ctx *ctx, size_t n, std::vector<void *> *owned = nullptr) {
+    if (n == 0) n = 1;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(ctx, e == cudaErrorMemoryAllocation ? NPFEM_ENOMEM : NPFEM_ECUDA, "cudaMalloc(%zu bytes): %s",
+             n * sizeof(T), cudaGetErrorString(e));
+    }
+    e = cudaMemsetAsync(p, 0, n * sizeof(T), ctx->stream);
+    if (e != cudaSuccess) fail(ctx, NPFEM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    if (owned) owned->push_back(p);
+    return reinterpret_cast<T *>(p);
+}
+
+template <typename T>
+T *upload(npfem_ctx *ctx, const std::vector<T> &v, std::vector<void *> &owned) {
+    T *p = dalloc<T>(ctx, v.size(), &owned);
+    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return p;
+}
+
+void dfree(void *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+bool mixed(const npfem_ctx *ctx) { return ctx->opt.precision != NPFEM_FP64; }
+bool bf16(const npfem_ctx *ctx) { return ctx->opt.precision == NPFEM_MIXED_BF16; }
+size_t esize(const npfem_ctx *ctx) { return mixed(ctx) ? sizeof(float) : sizeof(double); }
+
+void get_encode(npfem_ctx *ctx) {
+    if (g_encode) return;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        fail(ctx, NPFEM_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+}
+
+// 2D tensor map over a row-major [rows][stride] matrix whose first `inner`
+// columns are valid; box = 128 bytes of K x box_rows, 128-byte swizzle.
+CUtensorMap make_map(npfem_ctx *ctx, const void *base, bool is_bf16, int inner, long long rows, int stride,
+                     int box_rows) {
+    get_encode(ctx);
+    CUtensorMap m;
+    const int es = is_bf16 ? 2 : 4;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)stride * es};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(&m, is_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                          const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(ctx, NPFEM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return m;
+}
+
+int grid_for(long long n, int block, int cap = 1 << 20) {
+    long long g = (n + block - 1) / block;
+    return (int)std::max(1ll, std::min<long long>(g, cap));
+}
+
+// Every kernel launch of a step goes through prof_begin / prof_end: counts
+// the launch and, when profiling, brackets it with a pair of CUDA events on
+// the context stream (captured into the graph as event nodes).
+void prof_begin(npfem_ctx *ctx, int cls) {
+    ctx->launch_counter++;
+    if (!ctx->prof_on) return;
+    if (ctx->prof_next + 2 > ctx->prof_ev.size()) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            ctx->prof_ev.push_back(e);
+        }
+        ctx->prof_cls.resize(ctx->prof_ev.size() / 2);
+    }
+    ctx->prof_cls[ctx->prof_next / 2] = cls;
+    CK(cudaEventRecord(ctx->prof_ev[ctx->prof_next], ctx->stream));
+}
+
+void prof_end(npfem_ctx *ctx) {
+    if (!ctx->prof_on) return;
+    CK(cudaEventRecord(ctx->prof_ev[ctx->prof_next + 1], ctx->stream));
+    ctx->prof_next += 2;
+}
+
+void prof_harvest(npfem_ctx *ctx, size_t pairs) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < pairs; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
+        ctx->prof_ms[ctx->prof_cls[i]] += ms;
+        ctx->prof_n[ctx->prof_cls[i]] += 1;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------ kernel dispatch
+namespace {
+
+template <typename T>
+IterArgs<T> make_args(npfem_ctx *ctx, MeshTypeImpl *t) {
+    IterArgs<T> a{};
+    if constexpr (sizeof(T) == 8) a.tc = t->tc64;
+    else a.tc = t->tc32;
+    a.ncells = t->ncells;
+    a.m = ctx->opt.history;
+    a.max_bt = ctx->opt.max_backtracks;
+    a.use_allow = mixed(ctx) ? 1 : 0;
+    a.stash_T = t->stash_T;
+    a.h = t->h;
+    a.c1 = ctx->opt.armijo_c1;
+    a.xn = t->xn;
+    a.vn = t->vn;
+    a.fptr = ctx->d_fslot;
+    a.pub_off = t->pub_off;
+    a.minv = t->minv;
+    a.yrel = (T *)t->yrel;
+    a.origin = t->origin;
+    a.delta = (T *)t->delta;
+    a.grad = (T *)t->grad;
+    a.q = (T *)t->q;
+    a.z = (T *)t->z;
+    a.q_bf16 = t->q16;
+    a.S = (T *)t->S;
+    a.Y = (T *)t->Y;
+    a.rho = t->rho;
+    a.alpha = t->alpha;
+    a.g = t->g;
+    a.allow = t->allow;
+    a.hcount = t->hcount;
+    a.hhead = t->hhead;
+    a.fb_list = t->fb_list;
+    a.fb_count = t->fb_count;
+    a.st = ctx->d_st;
+    return a;
+}
+
+template <typename T, int EPT, int MAXB>
+void run_predict_t(npfem_ctx *ctx, MeshTypeImpl *t) {
+    IterArgs<T> a = make_args<T>(ctx, t);
+    prof_begin(ctx, NPFEM_K_PREDICT);
+    k_predict<T, EPT, MAXB><<<t->ncells, t->block, t->smem_step, ctx->stream>>>(a);
+    CK(cudaGetLastError());
+    prof_end(ctx);
+}
+
+template <typename T, int EPT, int MAXB>
+void run_iterate_t(npfem_ctx *ctx, MeshTypeImpl *t, int last, bool fallback) {
+    IterArgs<T> a = make_args<T>(ctx, t);
+    a.last = last;
+    prof_begin(ctx, fallback ? NPFEM_K_FALLBACK : NPFEM_K_ITERATE);
+    if (!fallback) {
+        k_iterate<T, EPT, MAXB><<<t->ncells, t->block, t->smem_step, ctx->stream>>>(a, nullptr, nullptr);
+    } else {
+        int grid = std::min(t->ncells, 2 * ctx->nsm);
+        k_iterate<T, EPT, MAXB><<<grid, t->block, t->smem_step, ctx->stream>>>(a, t->fb_list, t->fb_count);
+    }
+    CK(cudaGetLastError());
+    prof_end(ctx);
+}
+
+#define DISPATCH_EPT(T, FN, ...)                                         \
+    do {                                                                 \
+        if (t->ept == 4) FN<T, 4, 256>(__VA_ARGS__);                     \
+        else if (t->ept == 8) FN<T, 8, 256>(__VA_ARGS__);                \
+        else FN<T, 16, 512>(__VA_ARGS__);                                \
+    } while (0)
+
+void run_predict(npfem_ctx *ctx, MeshTypeImpl *t) {
+    if (mixed(ctx)) DISPATCH_EPT(float, run_predict_t, ctx, t);
+    else DISPATCH_EPT(double, run_predict_t, ctx, t);
+}
+
+void run_iterate(npfem_ctx *ctx, MeshTypeImpl *t, int last, bool fallback) {
+    if (mixed(ctx)) DISPATCH_EPT(float, run_iterate_t, ctx, t, last, fallback);
+    else DISPATCH_EPT(double, run_iterate_t, ctx, t, last, fallback);
+}
+
+// --- global step: z = P^{-1} q for all rows of a type
+size_t gemm_smem(const MeshTypeImpl *t) {
+    return 1024 + (size_t)t->stages * (tc::BM + t->n_tile) * tc::KB_BYTES + (2 * t->stages + 2) * 8;
+}
+
+// Kernel attributes are set at set-up time (never inside a stream capture),
+// to the device's opt-in maximum so that every type's request fits.
+void set_kernel_attrs(npfem_ctx *ctx) {
+    int mx = 0;
+    CK(cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    auto all = [&](auto fn) { CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)); };
+    if (mixed(ctx)) {
+        all(k_predict<float, 4, 256>); all(k_predict<float, 8, 256>); all(k_predict<float, 16, 512>);
+        all(k_iterate<float, 4, 256>); all(k_iterate<float, 8, 256>); all(k_iterate<float, 16, 512>);
+        all(k_fallback_apply<float>);
+        all(tc::k_gemm_tc<false>);
+        all(tc::k_gemm_tc<true>);
+    } else {
+        all(k_predict<double, 4, 256>); all(k_predict<double, 8, 256>); all(k_predict<double, 16, 512>);
+        all(k_iterate<double, 4, 256>); all(k_iterate<double, 8, 256>); all(k_iterate<double, 16, 512>);
+        all(k_fallback_apply<double>);
+    }
+    all(k_residual);
+    ctx->smem_optin = mx;
+}
+
+void gemm_tc(npfem_ctx *ctx, MeshTypeImpl *t, const CUtensorMap &mapQ, int rows, float *Z, int accumulate,
+             const int *conv) {
+    tc::GemmArgs g{};
+    g.rows = rows;
+    g.nV = t->nV;
+    g.nVp = t->nVp;
+    g.n_tile = t->n_tile;
+    g.stages = t->stages;
+    g.accumulate = accumulate;
+    g.conv = conv;
+    g.Z = Z;
+    g.st = ctx->d_st;
+    dim3 grid((t->nV + t->n_tile - 1) / t->n_tile, (rows + tc::BM - 1) / tc::BM);
+    const size_t smem = gemm_smem(t);
+    prof_begin(ctx, accumulate ? NPFEM_K_GEMM_REFINE : NPFEM_K_GEMM);
+    if (bf16(ctx)) tc::k_gemm_tc<false><<<grid, 128, smem, ctx->stream>>>(mapQ, t->mapP, g);
+    else tc::k_gemm_tc<true><<<grid, 128, smem, ctx->stream>>>(mapQ, t->mapP, g);
+    CK(cudaGetLastError());
+    prof_end(ctx);
+}
+
+void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, const float *z, void *r,
+              int *conv, int first, int final_pass) {
+    ResidArgs a{};
+    a.ncells = rows_cells;
+    a.nV = t->nV;
+    a.nVp = t->nVp;
+    a.first = first;
+    a.final_pass = final_pass;
+    a.tol = ctx->opt.refine_tol;
+    a.diag = t->diag;
+    a.op = t->op;
+    a.oj = t->oj;
+    a.ov = t->ov;
+    a.q = q;
+    a.z = z;
+    a.r_bf16 = bf16(ctx) ? (__nv_bfloat16 *)r : nullptr;
+    a.r_f32 = bf16(ctx) ? nullptr : (float *)r;
+    a.conv = conv;
+    a.any_active = ctx->d_any;
+    a.st = ctx->d_st;
+    size_t smem = 128 * sizeof(double) + 3 * (size_t)t->nVp * sizeof(float);
+    prof_begin(ctx, NPFEM_K_RESIDUAL);
+    k_residual<<<rows_cells, 256, smem, ctx->stream>>>(a);
+    CK(cudaGetLastError());
+    prof_end(ctx);
+}
+
+// z = P^{-1} q for the `cells` cells stored in the type's q / z buffers.
+void apply_type(npfem_ctx *ctx, MeshTypeImpl *t) {
+    const int rows = 3 * t->ncells;
+    if (!mixed(ctx)) {
+        dim3 grid((t->nV + SG_T - 1) / SG_T, (rows + SG_T - 1) / SG_T);
+        prof_begin(ctx, NPFEM_K_GEMM);
+        k_gemm_simt<double><<<grid, 256, 0, ctx->stream>>>(rows, t->nV, t->nVp, (const double *)t->q, t->Pinv64,
+                                                           (double *)t->z);
+        CK(cudaGetLastError());
+        prof_end(ctx);
+        return;
+    }
+    gemm_tc(ctx, t, t->mapQ, rows, (float *)t->z, 0, nullptr);
+    for (int s = 0; s < ctx->opt.refine_max; ++s) {
+        residual(ctx, t, t->ncells, (const float *)t->q, (const float *)t->z, t->rlo, t->conv, s == 0, 0);
+        gemm_tc(ctx, t, t->mapR, rows, (float *)t->z, 1, t->conv);
+    }
+    residual(ctx, t, t->ncells, (const float *)t->q, (const float *)t->z, nullptr, t->conv,
+             ctx->opt.refine_max == 0, 1);
+}
+
+void fallback_apply(npfem_ctx *ctx, MeshTypeImpl *t) {
+    int grid = std::min(t->ncells, 2 * ctx->nsm);
+    size_t smem = 3 * (size_t)t->nVp * esize(ctx);
+    prof_begin(ctx, NPFEM_K_FALLBACK_APPLY);
+    if (mixed(ctx))
+        k_fallback_apply<float><<<grid, 256, smem, ctx->stream>>>(t->nV, t->nVp, t->Pinv32, (const float *)t->q,
+                                                                  (float *)t->z, t->fb_list, t->fb_count);
+    else
+        k_fallback_apply<double><<<grid, 256, smem, ctx->stream>>>(t->nV, t->nVp, t->Pinv64, (const double *)t->q,
+                                                                   (double *)t->z, t->fb_list, t->fb_count);
+    CK(cudaGetLastError());
+    prof_end(ctx);
+}
+
+__global__ void k_set_ptr(double **slot, const double *p) { *slot = const_cast<double *>(p); }
+
+void enqueue_step(npfem_ctx *ctx) {
+    // counters only: a pending error word survives until a synchronising call reads it
+    CK(cudaMemsetAsync(reinterpret_cast<char *>(ctx->d_st) + sizeof(unsigned long long), 0,
+                       sizeof(DevStatus) - sizeof(unsigned long long), ctx->stream));
+    for (auto *t : ctx->types)
+        if (t->ncells) run_predict(ctx, t);
+    const int K = ctx->opt.iters;
+    for (int k = 0; k < K; ++k) {
+        const int last = (k == K - 1);
+        for (auto *t : ctx->types) {
+            if (!t->ncells) continue;
+            apply_type(ctx, t);
+            CK(cudaMemsetAsync(t->fb_count, 0, sizeof(int), ctx->stream));
+            run_iterate(ctx, t, last, false);
+            fallback_apply(ctx, t);
+            run_iterate(ctx, t, last, true);
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------- mesh set-up
+namespace {
+
+struct V3 {
+    double x, y, z;
+};
+V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+V3 crs(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+double dt3(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+double nrm(V3 a) { return std::sqrt(dt3(a, a)); }
+
+struct HostType {
+    std::vector<int> tri;               // nT*3
+    std::vector<double> dinv, area;     // nT*4, nT
+    std::vector<int> hv;                // nH*4
+    std::vector<double> hc, hrest;      // nH*4, nH
+    std::vector<int> vt_ptr, vt_inc, vh_ptr, vh_inc;
+    std::vector<double> vt_g, vh_c;
+    std::vector<double> P;              // dense nV*nV
+    double V0 = 0;
+};
+
+// Validate the mesh and build the element constants:
+//   triangles: D_m^{-1} in the triangle's rest frame, rest area;
+//   hinges   : every edge shared by t1 = (a, b, c) and t2 = (b, a, d):
+//              x0 = a, x1 = b, x2 = c, x3 = d, cotangent stencil scaled by
+//              sqrt(3 / (A1 + A2)), rest |b|;
+//   incidence lists per vertex (sorted by element), rest volume, dense P.
+void build_host_type(npfem_ctx *ctx, int nV, const double *X, int nT, const int32_t *tris, const double *mass,
+                     const npfem_material &m, HostType &H) {
+    auto P3 = [&](int i) { return V3{X[3 * i], X[3 * i + 1], X[3 * i + 2]}; };
+    H.tri.assign(tris, tris + 3 * nT);
+    for (int i = 0; i < 3 * nT; ++i)
+        if (tris[i] < 0 || tris[i] >= nV) fail(ctx, NPFEM_EINVAL, "triangle index %d out of range", tris[i]);
+    for (int t = 0; t < nT; ++t) {
+        const int *v = &H.tri[3 * t];
+        if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2]) fail(ctx, NPFEM_EINVAL, "triangle %d repeats a vertex", t);
+    }
+    // half-edge twins
+    std::unordered_map<long long, int> he;
+    he.reserve(6 * nT);
+    for (int t = 0; t < nT; ++t)
+        for (int k = 0; k < 3; ++k) {
+            long long a = H.tri[3 * t + k], b = H.tri[3 * t + (k + 1) % 3];
+            if (!he.emplace(a * nV + b, 3 * t + k).second)
+                fail(ctx, NPFEM_EINVAL, "edge (%lld,%lld) used twice with the same orientation", a, b);
+        }
+    for (auto &kv : he) {
+        long long a = kv.first / nV, b = kv.first % nV;
+        if (!he.count(b * nV + a)) fail(ctx, NPFEM_EINVAL, "open or inconsistently oriented mesh at edge (%lld,%lld)", a, b);
+    }
+    // triangle constants
+    H.dinv.resize(4 * nT);
+    H.area.resize(nT);
+    for (int t = 0; t < nT; ++t) {
+        const int *v = &H.tri[3 * t];
+        V3 E1 = sub(P3(v[1]), P3(v[0])), E2 = sub(P3(v[2]), P3(v[0]));
+        V3 n = crs(E1, E2);
+        double nn = nrm(n), l1 = nrm(E1), l2 = nrm(E2);
+        if (!(nn > 1e-14 * l1 * l2)) fail(ctx, NPFEM_EINVAL, "degenerate triangle %d", t);
+        V3 u = {E1.x / l1, E1.y / l1, E1.z / l1};
+        V3 nh = {n.x / nn, n.y / nn, n.z / nn};
+        V3 w = crs(nh, u);
+        double a = dt3(E1, u), b = dt3(E2, u), c = dt3(E1, w), d = dt3(E2, w);
+        double det = a * d - b * c;
+        H.dinv[4 * t + 0] = d / det;
+        H.dinv[4 * t + 1] = -b / det;
+        H.dinv[4 * t + 2] = -c / det;
+        H.dinv[4 * t + 3] = a / det;
+        H.area[t] = 0.5 * nn;
+    }
+    // rest volume (relative to vertex 0); outward orientation required
+    {
+        V3 o = P3(0);
+        double V = 0;
+        for (int t = 0; t < nT; ++t) {
+            const int *v = &H.tri[3 * t];
+            V += dt3(sub(P3(v[0]), o), crs(sub(P3(v[1]), o), sub(P3(v[2]), o)));
+        }
+        H.V0 = V / 6.0;
+        if (!(H.V0 > 0)) fail(ctx, NPFEM_EINVAL, "mesh is not outward oriented (rest volume %g)", H.V0);
+    }
+    // hinges in order of the first half-edge of each edge
+    auto cot_at = [&](V3 a, V3 b, V3 c) {
+        V3 u = sub(b, a), v = sub(c, a);
+        return dt3(u, v) / nrm(crs(u, v));
+    };
+    for (int t = 0; t < nT; ++t)
+        for (int k = 0; k < 3; ++k) {
+            int a = H.tri[3 * t + k], b = H.tri[3 * t + (k + 1) % 3], c = H.tri[3 * t + (k + 2) % 3];
+            int tw = he[(long long)b * nV + a];
+            if (tw < 3 * t + k) continue;   // the edge was met earlier as its twin
+            int t2 = tw / 3, k2 = tw % 3;
+            int d = H.tri[3 * t2 + (k2 + 2) % 3];
+            V3 X0 = P3(a), X1 = P3(b), X2 = P3(c), X3 = P3(d);
+            double c10 = cot_at(X0, X1, X2), c11 = cot_at(X1, X2, X0);
+            double c20 = cot_at(X0, X3, X1), c21 = cot_at(X1, X0, X3);
+            double sc = std::sqrt(3.0 / (H.area[t] + H.area[t2]));
+            double cc[4] = {sc * (c11 + c21), sc * (c10 + c20), -sc * (c10 + c11), -sc * (c20 + c21)};
+            int idx[4] = {a, b, c, d};
+            V3 bb = {0, 0, 0};
+            for (int j = 0; j < 4; ++j) {
+                V3 p = P3(idx[j]);
+                bb.x += cc[j] * p.x;
+                bb.y += cc[j] * p.y;
+                bb.z += cc[j] * p.z;
+                H.hv.push_back(idx[j]);
+                H.hc.push_back(cc[j]);
+            }
+            H.hrest.push_back(nrm(bb));
+        }
+    const int nH = (int)H.hrest.size();
+    // incidence lists (counting sort keeps element order)
+    H.vt_ptr.assign(nV + 1, 0);
+    for (int i = 0; i < 3 * nT; ++i) H.vt_ptr[H.tri[i] + 1]++;
+    for (int v = 0; v < nV; ++v) H.vt_ptr[v + 1] += H.vt_ptr[v];
+    H.vt_inc.resize(3 * nT);
+    H.vt_g.resize(6 * nT);
+    {
+        std::vector<int> fill(H.vt_ptr.begin(), H.vt_ptr.end() - 1);
+        for (int t = 0; t < nT; ++t)
+            for (int k = 0; k < 3; ++k) {
+                int v = H.tri[3 * t + k], pos = fill[v]++;
+                const double *Di = &H.dinv[4 * t];
+                double g0, g1;
+                if (k == 1) { g0 = Di[0]; g1 = Di[1]; }
+                else if (k == 2) { g0 = Di[2]; g1 = Di[3]; }
+                else { g0 = -Di[0] - Di[2]; g1 = -Di[1] - Di[3]; }
+                H.vt_inc[pos] = (t << 2) | k;
+                H.vt_g[2 * pos] = g0;
+                H.vt_g[2 * pos + 1] = g1;
+            }
+    }
+    H.vh_ptr.assign(nV + 1, 0);
+    for (int i = 0; i < 4 * nH; ++i) H.vh_ptr[H.hv[i] + 1]++;
+    for (int v = 0; v < nV; ++v) H.vh_ptr[v + 1] += H.vh_ptr[v];
+    H.vh_inc.resize(4 * nH);
+    H.vh_c.resize(4 * nH);
+    {
+        std::vector<int> fill(H.vh_ptr.begin(), H.vh_ptr.end() - 1);
+        for (int h = 0; h < nH; ++h)
+            for (int j = 0; j < 4; ++j) {
+                int v = H.hv[4 * h + j], pos = fill[v]++;
+                H.vh_inc[pos] = (h << 2) | j;
+                H.vh_c[pos] = H.hc[4 * h + j];
+            }
+    }
+    // P = M/h^2 + k_vol I + sum_t (ws + wa) A_t^T A_t + sum_e kb A_e^T A_e
+    H.P.assign((size_t)nV * nV, 0.0);
+    const double ih2 = 1.0 / (m.dt * m.dt);
+    for (int v = 0; v < nV; ++v) H.P[(size_t)v * nV + v] += mass[v] * ih2 + m.k_vol;
+    for (int t = 0; t < nT; ++t) {
+        const double *Di = &H.dinv[4 * t];
+        double G[3][2] = {{-Di[0] - Di[2], -Di[1] - Di[3]}, {Di[0], Di[1]}, {Di[2], Di[3]}};
+        double w = (m.k_strain + m.k_area) * H.area[t];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                H.P[(size_t)H.tri[3 * t + i] * nV + H.tri[3 * t + j]] += w * (G[i][0] * G[j][0] + G[i][1] * G[j][1]);
+    }
+    for (int h = 0; h < nH; ++h)
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j)
+                H.P[(size_t)H.hv[4 * h + i] * nV + H.hv[4 * h + j]] += m.k_bend * H.hc[4 * h + i] * H.hc[4 * h + j];
+}
+
+template <typename T>
+std::vector<T> cvt(const std::vector<double> &v) {
+    return std::vector<T>(v.begin(), v.end());
+}
+
+template <typename T>
+TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, const std::vector<double> &mass) {
+    TypeConst<T> c{};
+    c.nV = t->nV;
+    c.nVp = t->nVp;
+    c.nT = t->nT;
+    c.nH = t->nH;
+    std::vector<int4> tri(t->nT), hv(t->nH);
+    for (int i = 0; i < t->nT; ++i) tri[i] = make_int4(H.tri[3 * i], H.tri[3 * i + 1], H.tri[3 * i + 2], 0);
+    for (int i = 0; i < t->nH; ++i) hv[i] = make_int4(H.hv[4 * i], H.hv[4 * i + 1], H.hv[4 * i + 2], H.hv[4 * i + 3]);
+    std::vector<double> wtri(2 * t->nT), mh2(t->nV);
+    for (int i = 0; i < t->nT; ++i) {
+        wtri[2 * i] = t->ks * H.area[i];
+        wtri[2 * i + 1] = t->ka * H.area[i];
+    }
+    for (int v = 0; v < t->nV; ++v) mh2[v] = mass[v] / (t->h * t->h);
+    c.tri = upload(ctx, tri, t->owned);
+    c.dinv = upload(ctx, cvt<T>(H.dinv), t->owned);
+    c.wtri = upload(ctx, cvt<T>(wtri), t->owned);
+    c.hv = upload(ctx, hv, t->owned);
+    c.hc = upload(ctx, cvt<T>(H.hc), t->owned);
+    c.hrest = upload(ctx, cvt<T>(H.hrest), t->owned);
+    c.vt_ptr = upload(ctx, H.vt_ptr, t->owned);
+    c.vt_inc = upload(ctx, H.vt_inc, t->owned);
+    c.vt_g = upload(ctx, cvt<T>(H.vt_g), t->owned);
+    c.vh_ptr = upload(ctx, H.vh_ptr, t->owned);
+    c.vh_inc = upload(ctx, H.vh_inc, t->owned);
+    c.vh_c = upload(ctx, cvt<T>(H.vh_c), t->owned);
+    c.mh2 = upload(ctx, cvt<T>(mh2), t->owned);
+    c.V0 = H.V0;
+    c.kb = (T)t->kb;
+    c.kv = (T)t->kv;
+    return c;
+}
+
+// P^{-1} in FP64 on the GPU (Gauss-Jordan), then the operand copies.
+void invert_on_gpu(npfem_ctx *ctx, MeshTypeImpl *t, const std::vector<double> &P) {
+    const int n = t->nV;
+    std::vector<void *> tmp;
+    double *A = dalloc<double>(ctx, (size_t)n * n, &tmp);
+    double *rowk = dalloc<double>(ctx, n, &tmp), *colk = dalloc<double>(ctx, n, &tmp);
+    int *bad = dalloc<int>(ctx, 1, &tmp);
+    try {
+        CK(cudaMemcpyAsync(A, P.data(), (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        const int g1 = grid_for(n, 256), g2 = grid_for((long long)n * n, 256, 4 * ctx->nsm);
+        for (int k = 0; k < n; ++k) {
+            k_gj_prep<<<g1, 256, 0, ctx->stream>>>(n, k, A, rowk, colk, bad);
+            k_gj_update<<<g2, 256, 0, ctx->stream>>>(n, k, A, rowk, colk, bad);
+        }
+        CK(cudaGetLastError());
+        int hbad = 0;
+        CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (hbad) fail(ctx, NPFEM_ENOTSPD, "system matrix P is not positive definite");
+        t->Pinv64 = dalloc<double>(ctx, (size_t)n * t->nVp, &t->owned);
+        if (mixed(ctx)) t->Pinv32 = dalloc<float>(ctx, (size_t)n * t->nVp, &t->owned);
+        if (bf16(ctx)) t->Pinv16 = dalloc<__nv_bfloat16>(ctx, (size_t)n * t->nVp, &t->owned);
+        k_convert_pinv<<<grid_for((long long)n * t->nVp, 256, 4096), 256, 0, ctx->stream>>>(n, t->nVp, A, t->Pinv64,
+                                                                                          t->Pinv32, t->Pinv16);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(ctx->stream));
+    } catch (...) {
+        for (void *p : tmp) cudaFree(p);
+        throw;
+    }
+    for (void *p : tmp) cudaFree(p);
+}
+
+void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
+    const int ntiles = (t->nV + 255) / 256;
+    int nt = (t->nV + ntiles - 1) / ntiles;
+    nt = (nt + 15) / 16 * 16;
+    t->n_tile = nt;
+    const size_t stage = (size_t)(tc::BM + nt) * tc::KB_BYTES;
+    t->stages = (int)std::min<size_t>(4, (200 * 1024) / stage);
+    (void)ctx;
+}
+
+void free_cells(MeshTypeImpl *t) {
+    void **bufs[] = {(void **)&t->pub_off, (void **)&t->xn, (void **)&t->vn, &t->yrel, &t->delta, &t->grad, &t->q,
+                     &t->z, &t->S, &t->Y, &t->rlo, (void **)&t->q16, (void **)&t->origin, (void **)&t->rho,
+                     (void **)&t->alpha, (void **)&t->g, (void **)&t->allow, (void **)&t->hcount,
+                     (void **)&t->hhead, (void **)&t->conv, (void **)&t->fb_list, (void **)&t->fb_count};
+    for (void **b : bufs) dfree(*b);
+}
+
+// (Re)allocate the per-cell arrays of a type for `cap` cells, keeping the state.
+void alloc_cells(npfem_ctx *ctx, MeshTypeImpl *t, int cap) {
+    MeshTypeImpl old = *t;
+    const size_t n3 = 3 * (size_t)t->nVp, es = esize(ctx), m = std::max(1, ctx->opt.history);
+    t->pub_off = dalloc<long long>(ctx, cap);
+    t->xn = dalloc<double>(ctx, cap * n3);
+    t->vn = dalloc<double>(ctx, cap * n3);
+    auto vec = [&](void *&p) { p = dalloc<unsigned char>(ctx, cap * n3 * es); };
+    vec(t->yrel); vec(t->delta); vec(t->grad); vec(t->q); vec(t->z);
+    t->S = dalloc<unsigned char>(ctx, cap * n3 * es * m);
+    t->Y = dalloc<unsigned char>(ctx, cap * n3 * es * m);
+    t->q16 = bf16(ctx) ? dalloc<__nv_bfloat16>(ctx, cap * n3) : nullptr;
+    t->rlo = mixed(ctx) ? dalloc<unsigned char>(ctx, cap * n3 * (bf16(ctx) ? 2 : 4)) : nullptr;
+    t->origin = dalloc<double>(ctx, 3 * (size_t)cap);
+    t->rho = dalloc<double>(ctx, m * cap);
+    t->alpha = dalloc<double>(ctx, m * cap);
+    t->g = dalloc<double>(ctx, cap);
+    t->allow = dalloc<double>(ctx, cap);
+    t->hcount = dalloc<int>(ctx, cap);
+    t->hhead = dalloc<int>(ctx, cap);
+    t->conv = dalloc<int>(ctx, cap);
+    t->fb_list = dalloc<int>(ctx, cap);
+    t->fb_count = dalloc<int>(ctx, 1);
+    t->cap = cap;
+    if (old.ncells) {
+        CK(cudaMemcpyAsync(t->xn, old.xn, old.ncells * n3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(t->vn, old.vn, old.ncells * n3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    free_cells(&old);
+    if (mixed(ctx)) {
+        t->mapQ = make_map(ctx, bf16(ctx) ? (const void *)t->q16 : t->q, bf16(ctx), t->nV, 3ll * cap, t->nVp, tc::BM);
+        t->mapR = make_map(ctx, t->rlo, bf16(ctx), t->nV, 3ll * cap, t->nVp, tc::BM);
+    }
+}
+
+void invalidate_graph(npfem_ctx *ctx) {
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->gexec = nullptr;
+    ctx->graph = nullptr;
+    ctx->graph_valid = false;
+}
+
+int pending_error(npfem_ctx *ctx) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) fail(ctx, NPFEM_ECUDA, "device error: %s", cudaGetErrorString(e));
+    CK(cudaMemcpy(ctx->h_st, ctx->d_st, sizeof(DevStatus), cudaMemcpyDeviceToHost));
+    unsigned long long err = ctx->h_st->err;
+    if (err) {
+        int code = (int)(err >> 32);
+        long long where = (long long)(err & 0xffffffffull);
+        CK(cudaMemsetAsync(&ctx->d_st->err, 0, sizeof(unsigned long long), ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (code == DEV_ENONFINITE) fail(ctx, NPFEM_ENONFINITE, "non-finite value in cell %lld (type-local index)", where);
+        fail(ctx, NPFEM_ETIMEOUT, "a bounded device wait expired (site %lld)", where);
+    }
+    return NPFEM_OK;
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+extern "C" {
+
+void npfem_default_options(npfem_options *o) {
+    std::memset(o, 0, sizeof *o);
+    o->precision = NPFEM_FP64;
+    o->iters = 10;
+    o->history = 5;
+    o->armijo_c1 = 1e-4;
+    o->max_backtracks = 8;
+    o->refine_tol = 1e-6;
+    o->refine_max = 3;
+    o->use_graph = 1;
+    o->device = 0;
+    o->cuda_stream = nullptr;
+    o->autotune_cache = nullptr;
+}
+
+int npfem_create(const npfem_options *opt, npfem_ctx **out) {
+    if (!out) return NPFEM_EINVAL;
+    *out = nullptr;
+    npfem_ctx *ctx = new (std::nothrow) npfem_ctx;
+    if (!ctx) return NPFEM_ENOMEM;
+    if (opt) ctx->opt = *opt;
+    else npfem_default_options(&ctx->opt);
+    int rc = guard(ctx, [&] {
+        const npfem_options &o = ctx->opt;
+        if (o.precision < 0 || o.precision > 2 || o.iters < 1 || o.history < 0 || o.history > NPFEM_MAX_HISTORY ||
+            o.max_backtracks < 0 || !(o.armijo_c1 > 0 && o.armijo_c1 < 1) || o.refine_max < 0 || !(o.refine_tol > 0))
+            fail(ctx, NPFEM_EINVAL, "invalid option value");
+        CK(cudaSetDevice(o.device));
+        ctx->device = o.device;
+        CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, o.device));
+        if (mixed(ctx)) {
+            int major = 0, minor = 0;
+            CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, o.device));
+            CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, o.device));
+            if (major != 10 || minor != 3)
+                fail(ctx, NPFEM_EINVAL, "mixed-precision forms need tcgen05 on sm_103 (device is sm_%d%d)", major, minor);
+        }
+        if (o.cuda_stream) {
+            ctx->stream = (cudaStream_t)o.cuda_stream;
+        } else {
+            CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+            ctx->own_stream = true;
+        }
+        ctx->d_st = dalloc<DevStatus>(ctx, 1);
+        ctx->d_fslot = dalloc<double *>(ctx, 1);
+        ctx->d_any = dalloc<int>(ctx, 1);
+        CK(cudaMallocHost(&ctx->h_st, sizeof(DevStatus)));
+        set_kernel_attrs(ctx);
+        CK(cudaStreamSynchronize(ctx->stream));
+    });
+    if (rc) {
+        npfem_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return NPFEM_OK;
+}
+
+void npfem_destroy(npfem_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    invalidate_graph(ctx);
+    for (auto *t : ctx->types) {
+        free_cells(t);
+        for (void *p : t->owned) cudaFree(p);
+        delete t;
+    }
+    void *bufs[] = {ctx->d_f, ctx->d_fslot, ctx->d_stage, ctx->d_st, ctx->d_any};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (ctx->h_st) cudaFreeHost(ctx->h_st);
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *npfem_last_error(const npfem_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t npfem_num_dofs(const npfem_ctx *ctx) { return ctx ? (size_t)ctx->ndofs : 0; }
+
+int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int nT, const int32_t *tris,
+                           const double *vertex_mass, const npfem_material *mat, int *type_id) {
+    if (!ctx) return NPFEM_EINVAL;
+    auto *t = new (std::nothrow) MeshTypeImpl;
+    if (!t) return NPFEM_ENOMEM;
+    int rc = guard(ctx, [&] {
+        if (!rest_xyz || !tris || !mat || nV < 4 || nT < 4) fail(ctx, NPFEM_EINVAL, "bad mesh arguments");
+        if (nV > 2720) fail(ctx, NPFEM_EINVAL, "nV = %d exceeds the supported 2720 vertices per cell", nV);
+        if (!(mat->dt > 0) || mat->k_strain < 0 || mat->k_area < 0 || mat->k_bend < 0 || mat->k_vol < 0)
+            fail(ctx, NPFEM_EINVAL, "bad material");
+        std::vector<double> mass(nV);
+        for (int v = 0; v < nV; ++v) {
+            mass[v] = vertex_mass ? vertex_mass[v] : 1.0 / nV;
+            if (!(mass[v] > 0)) fail(ctx, NPFEM_EINVAL, "vertex mass must be positive");
+        }
+        for (int i = 0; i < 3 * nV; ++i)
+            if (!std::isfinite(rest_xyz[i])) fail(ctx, NPFEM_ENONFINITE, "non-finite rest position");
+        HostType H;
+        build_host_type(ctx, nV, rest_xyz, nT, tris, mass.data(), *mat, H);
+        t->nV = nV;
+        t->nVp = (nV + 7) / 8 * 8;
+        t->nT = nT;
+        t->nH = (int)H.hrest.size();
+        t->h = mat->dt;
+        t->ks = mat->k_strain;
+        t->ka = mat->k_area;
+        t->kb = mat->k_bend;
+        t->kv = mat->k_vol;
+        t->V0 = H.V0;
+        if (mixed(ctx)) t->tc32 = upload_consts<float>(ctx, t, H, mass);
+        else t->tc64 = upload_consts<double>(ctx, t, H, mass);
+        std::vector<double> minv(nV), diag(nV);
+        std::vector<int> op(nV + 1, 0), oj;
+        std::vector<float> ov;
+        for (int v = 0; v < nV; ++v) {
+            minv[v] = 1.0 / mass[v];
+            diag[v] = H.P[(size_t)v * nV + v];
+            for (int u = 0; u < nV; ++u) {
+                double p = H.P[(size_t)v * nV + u];
+                if (u != v && p != 0.0) {
+                    oj.push_back(u);
+                    ov.push_back((float)p);
+                }
+            }
+            op[v + 1] = (int)oj.size();
+        }
+        t->minv = upload(ctx, minv, t->owned);
+        t->diag = upload(ctx, diag, t->owned);
+        t->op = upload(ctx, op, t->owned);
+        t->oj = upload(ctx, oj, t->owned);
+        t->ov = upload(ctx, ov, t->owned);
+        t->n_off = (int)oj.size();
+        invert_on_gpu(ctx, t, H.P);
+        // per-cell kernel shape: EPT elements per thread, block <= 256 (<= 512 for big meshes)
+        const int n3 = 3 * t->nVp;
+        if ((n3 + 3) / 4 <= 256) t->ept = 4;
+        else if ((n3 + 7) / 8 <= 256) t->ept = 8;
+        else t->ept = 16;
+        t->block = ((n3 + t->ept - 1) / t->ept + 31) / 32 * 32;
+        const size_t es = esize(ctx);
+        const size_t stash_cap = mixed(ctx) ? 16384 : 12288;
+        t->stash_T = (int)std::min<size_t>(6 * (size_t)nT, stash_cap);
+        t->smem_step = 128 * sizeof(double) + (3 * (size_t)t->nVp + t->stash_T) * es;
+        if (mixed(ctx)) {
+            choose_tiles(ctx, t);
+            const void *pb = bf16(ctx) ? (const void *)t->Pinv16 : (const void *)t->Pinv32;
+            t->mapP = make_map(ctx, pb, bf16(ctx), nV, nV, t->nVp, t->n_tile);
+        }
+        if (t->smem_step > (size_t)ctx->smem_optin || gemm_smem(t) > (size_t)ctx->smem_optin)
+            fail(ctx, NPFEM_EINVAL, "mesh type needs more shared memory than the device offers");
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->types.push_back(t);
+        invalidate_graph(ctx);
+        if (type_id) *type_id = (int)ctx->types.size() - 1;
+    });
+    if (rc) {
+        free_cells(t);
+        for (void *p : t->owned) cudaFree(p);
+        delete t;
+    }
+    return rc;
+}
+
+int npfem_add_cells(npfem_ctx *ctx, int type_id, int n_cells, const double *x0, const double *v0,
+                    int64_t *first_cell) {
+    if (!ctx) return NPFEM_EINVAL;
+    return guard(ctx, [&] {
+        if (type_id < 0 || type_id >= (int)ctx->types.size() || n_cells < 0 || (n_cells > 0 && !x0))
+            fail(ctx, NPFEM_EINVAL, "bad add_cells arguments");
+        MeshTypeImpl *t = ctx->types[type_id];
+        const long long per = 3ll * t->nV, total = per * n_cells;
+        for (long long i = 0; i < total; ++i)
+            if (!std::isfinite(x0[i]) || (v0 && !std::isfinite(v0[i])))
+                fail(ctx, NPFEM_ENONFINITE, "non-finite initial state in new cell %lld", i / per);
+        // index of the first new cell in the public order = cells added so far
+        long long first = 0;
+        for (auto *u : ctx->types) first += u->ncells;
+        if (first_cell) *first_cell = first;
+        if (n_cells == 0) return;
+        if (t->ncells + n_cells > t->cap) alloc_cells(ctx, t, std::max(t->ncells + n_cells, 2 * t->cap));
+        for (int c = 0; c < n_cells; ++c) t->pub_off_h.push_back(ctx->ndofs + per * c);
+        CK(cudaMemcpyAsync(t->pub_off, t->pub_off_h.data(), t->pub_off_h.size() * sizeof(long long),
+                           cudaMemcpyHostToDevice, ctx->stream));
+        // stage x0 / v0 in the public layout and scatter into SoA
+        std::vector<void *> tmp;
+        double *sx = dalloc<double>(ctx, total, &tmp), *sv = dalloc<double>(ctx, total, &tmp);
+        long long *offs = dalloc<long long>(ctx, n_cells, &tmp);
+        try {
+            std::vector<long long> lo(n_cells);
+            for (int c = 0; c < n_cells; ++c) lo[c] = per * c;
+            CK(cudaMemcpyAsync(offs, lo.data(), n_cells * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(sx, x0, total * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+            if (v0) CK(cudaMemcpyAsync(sv, v0, total * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+            const long long n3 = 3ll * t->nVp;
+            k_pub_to_soa<<<grid_for(n_cells * n3, 256, 8192), 256, 0, ctx->stream>>>(n_cells, t->nV, t->nVp, offs, sx,
+                                                                                   t->xn + t->ncells * n3);
+            k_pub_to_soa<<<grid_for(n_cells * n3, 256, 8192), 256, 0, ctx->stream>>>(
+                n_cells, t->nV, t->nVp, offs, v0 ? sv : nullptr, t->vn + t->ncells * n3);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(ctx->stream));
+        } catch (...) {
+            for (void *p : tmp) cudaFree(p);
+            throw;
+        }
+        for (void *p : tmp) cudaFree(p);
+        t->ncells += n_cells;
+        ctx->ndofs += total;
+        // the public layout grew: re-stage buffers
+        dfree((void *&)ctx->d_f);
+        dfree((void *&)ctx->d_stage);
+        ctx->d_f = dalloc<double>(ctx, ctx->ndofs);
+        ctx->d_stage = dalloc<double>(ctx, ctx->ndofs);
+        invalidate_graph(ctx);
+    });
+}
+
+int npfem_step(npfem_ctx *ctx, const double *f_ext, int f_ext_on_device) {
+    if (!ctx) return NPFEM_EINVAL;
+    return guard(ctx, [&] {
+        if (ctx->ndofs == 0) fail(ctx, NPFEM_ESTATE, "no cells");
+        if (!f_ext) fail(ctx, NPFEM_EINVAL, "f_ext is null");
+        const double *fd = f_ext;
+        if (!f_ext_on_device) {
+            CK(cudaMemcpyAsync(ctx->d_f, f_ext, ctx->ndofs * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+            fd = ctx->d_f;
+        }
+        k_set_ptr<<<1, 1, 0, ctx->stream>>>(ctx->d_fslot, fd);
+        CK(cudaGetLastError());
+        ctx->prof_next = 0;
+        if (ctx->opt.use_graph) {
+            if (!ctx->graph_valid) {
+                invalidate_graph(ctx);
+                ctx->launch_counter = 0;
+                CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+                try {
+                    enqueue_step(ctx);
+                    ctx->launches_per_step = ctx->launch_counter + 1;   // + the force-pointer kernel
+                } catch (...) {
+                    cudaGraph_t g = nullptr;
+                    cudaStreamEndCapture(ctx->stream, &g);
+                    if (g) cudaGraphDestroy(g);
+                    throw;
+                }
+                CK(cudaStreamEndCapture(ctx->stream, &ctx->graph));
+                CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
+                ctx->graph_valid = true;
+                ctx->graph_prof_pairs = ctx->prof_next / 2;
+            }
+            CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+        } else {
+            ctx->launch_counter = 0;
+            enqueue_step(ctx);
+            ctx->launches_per_step = ctx->launch_counter + 1;
+        }
+        if (ctx->prof_on) prof_harvest(ctx, ctx->opt.use_graph ? ctx->graph_prof_pairs : ctx->prof_next / 2);
+        ctx->stepped = true;
+    });
+}
+
+int npfem_sync(npfem_ctx *ctx) {
+    if (!ctx) return NPFEM_EINVAL;
+    return guard(ctx, [&] { pending_error(ctx); });
+}
+
+static int get_state(npfem_ctx *ctx, bool pos, double *out, size_t n, int on_device) {
+    if (!ctx) return NPFEM_EINVAL;
+    return guard(ctx, [&] {
+        if (!out || (long long)n != ctx->ndofs) fail(ctx, NPFEM_EINVAL, "output size %zu != %lld", n, ctx->ndofs);
+        double *dst = on_device ? out : ctx->d_stage;
+        for (auto *t : ctx->types) {
+            if (!t->ncells) continue;
+            long long tot = 3ll * t->nV * t->ncells;
+            k_soa_to_pub<<<grid_for(tot, 256, 8192), 256, 0, ctx->stream>>>(t->ncells, t->nV, t->nVp, t->pub_off,
+                                                                            pos ? t->xn : t->vn, dst);
+        }
+        CK(cudaGetLastError());
+        if (!on_device) CK(cudaMemcpyAsync(out, ctx->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        pending_error(ctx);
+    });
+}
+
+int npfem_get_positions(npfem_ctx *ctx, double *out, size_t n, int on_device) {
+    return get_state(ctx, true, out, n, on_device);
+}
+
+int npfem_get_velocities(npfem_ctx *ctx, double *out, size_t n, int on_device) {
+    return get_state(ctx, false, out, n, on_device);
+}
+
+int npfem_set_state(npfem_ctx *ctx, const double *x, const double *v, size_t n) {
+    if (!ctx) return NPFEM_EINVAL;
+    return guard(ctx, [&] {
+        if (!x || (long long)n != ctx->ndofs) fail(ctx, NPFEM_EINVAL, "state size %zu != %lld", n, ctx->ndofs);
+        for (size_t i = 0; i < n; ++i)
+            if (!std::isfinite(x[i]) || (v && !std::isfinite(v[i])))
+                fail(ctx, NPFEM_ENONFINITE, "non-finite state value at %zu", i);
+        for (int pass = 0; pass < 2; ++pass) {
+            const double *src = pass == 0 ? x : v;
+            if (src) CK(cudaMemcpyAsync(ctx->d_stage, src, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+            for (auto *t : ctx->types) {
+                if (!t->ncells) continue;
+                long long tot = 3ll * t->nVp * t->ncells;
+                k_pub_to_soa<<<grid_for(tot, 256, 8192), 256, 0, ctx->stream>>>(
+                    t->ncells, t->nV, t->nVp, t->pub_off, src ? ctx->d_stage : nullptr, pass == 0 ? t->xn : t->vn);
+            }
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+    });
+}
+
+int npfem_stats(npfem_ctx *ctx, npfem_step_stats *out) {
+    if (!ctx || !out) return NPFEM_EINVAL;
+    return guard(ctx, [&] {
+        pending_error(ctx);
+        const DevStatus &s = *ctx->h_st;
+        long long cells = 0;
+        for (auto *t : ctx->types) cells += t->ncells;
+        out->cell_iterations = ctx->stepped ? cells * ctx->opt.iters : 0;
+        out->backtracks = s.backtracks;
+        out->capped_searches = s.capped;
+        out->fallbacks = s.fallbacks;
+        out->refine_sweeps = s.refine_sweeps;
+        float r;
+        std::memcpy(&r, &s.max_resid_bits, sizeof r);
+        out->max_refine_residual = r;
+        out->energy_sum = s.energy_sum;
+        out->launches_per_step = ctx->launches_per_step;
+    });
+}
+
+int npfem_profile(npfem_ctx *ctx, int enable) {
+    if (!ctx) return NPFEM_EINVAL;
+    return guard(ctx, [&] {
+        CK(cudaStreamSynchronize(ctx->stream));
+        if ((bool)enable != ctx->prof_on) invalidate_graph(ctx);
+        ctx->prof_on = enable != 0;
+    });
+}
+
+int npfem_profile_read(npfem_ctx *ctx, npfem_kernel_times *out, int reset) {
+    if (!ctx || !out) return NPFEM_EINVAL;
+    return guard(ctx, [&] {
+        for (int i = 0; i < NPFEM_KCLASSES; ++i) {
+            out->ms[i] = ctx->prof_ms[i];
+            out->launches[i] = ctx->prof_n[i];
+            if (reset) {
+                ctx->prof_ms[i] = 0;
+                ctx->prof_n[i] = 0;
+            }
+        }
+    });
+}
+
+int npfem_apply_pinv(npfem_ctx *ctx, int type_id, const double *q, double *z, int n_cols) {
+    if (!ctx) return NPFEM_EINVAL;
+    return guard(ctx, [&] {
+        if (type_id < 0 || type_id >= (int)ctx->types.size() || n_cols < 0 || !q || !z)
+            fail(ctx, NPFEM_EINVAL, "bad apply arguments");
+        if (n_cols == 0) return;
+        MeshTypeImpl *t = ctx->types[type_id];
+        const int ncell = (n_cols + 2) / 3, rows = 3 * ncell;
+        const size_t nvec = (size_t)rows * t->nVp;
+        std::vector<void *> tmp;
+        try {
+            if (!mixed(ctx)) {
+                double *qi = dalloc<double>(ctx, nvec, &tmp), *zi = dalloc<double>(ctx, nvec, &tmp);
+                k_cols_in<double><<<grid_for(nvec, 256, 8192), 256, 0, ctx->stream>>>(n_cols, t->nV, t->nVp, q, qi, nullptr);
+                dim3 grid((t->nV + SG_T - 1) / SG_T, (rows + SG_T - 1) / SG_T);
+                k_gemm_simt<double><<<grid, 256, 0, ctx->stream>>>(rows, t->nV, t->nVp, qi, t->Pinv64, zi);
+                k_cols_out<double><<<grid_for((long long)n_cols * t->nV, 256, 8192), 256, 0, ctx->stream>>>(
+                    n_cols, t->nV, t->nVp, zi, z);
+            } else {
+                float *qi = dalloc<float>(ctx, nvec, &tmp), *zi = dalloc<float>(ctx, nvec, &tmp);
+                __nv_bfloat16 *q16 = bf16(ctx) ? dalloc<__nv_bfloat16>(ctx, nvec, &tmp) : nullptr;
+                void *rl = dalloc<unsigned char>(ctx, nvec * (bf16(ctx) ? 2 : 4), &tmp);
+                int *conv = dalloc<int>(ctx, ncell, &tmp);
+                k_cols_in<float><<<grid_for(nvec, 256, 8192), 256, 0, ctx->stream>>>(n_cols, t->nV, t->nVp, q, qi, q16);
+                CUtensorMap mq = make_map(ctx, bf16(ctx) ? (const void *)q16 : qi, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
+                CUtensorMap mr = make_map(ctx, rl, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
+                gemm_tc(ctx, t, mq, rows, zi, 0, nullptr);
+                for (int s = 0; s < ctx->opt.refine_max; ++s) {
+                    residual(ctx, t, ncell, qi, zi, rl, conv, s == 0, 0);
+                    gemm_tc(ctx, t, mr, rows, zi, 1, conv);
+                }
+                residual(ctx, t, ncell, qi, zi, nullptr, conv, ctx->opt.refine_max == 0, 1);
+                k_cols_out<float><<<grid_for((long long)n_cols * t->nV, 256, 8192), 256, 0, ctx->stream>>>(
+                    n_cols, t->nV, t->nVp, zi, z);
+            }
+            CK(cudaGetLastError());
+            pending_error(ctx);
+        } catch (...) {
+            cudaStreamSynchronize(ctx->stream);
+            for (void *p : tmp) cudaFree(p);
+            throw;
+        }
+        for (void *p : tmp) cudaFree(p);
+    });
+}
+
+}  // extern "C"

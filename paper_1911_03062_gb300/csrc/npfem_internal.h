@@ -1,0 +1,8 @@
+// npfem_internal.h -- kernels of the npFEM CUDA path, collected for npfem.cu.
+#pragma once
+
+#include "common.cuh"
+#include "local.cuh"
+#include "step_kernels.cuh"
+#include "gemm_simt.cuh"
+#include "gemm_tc.cuh"

@@ -1,0 +1,118 @@
+"""Mixed-precision CUDA path (FP32 local step, tcgen05 TF32 / BF16 global
+step with FP64-residual refinement) vs the FP64 oracle: bar 1e-6 relative
+position error.  All calls go through libnpfem.so."""
+import numpy as np
+import pytest
+
+from paper_1911_03062_gb300 import inputs as I
+
+from helpers import make_groups, public, rel_pos_err, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as G
+    G.build()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_apply_pinv_tensor_cores(prec):
+    # z = P^{-1} q on tcgen05 + refinement vs the exact FP64 solve; 131 columns
+    # (two 128-row tiles, ragged), both mesh sizes (three 224-wide N tiles / one)
+    import torch
+    from oracle import oracle as O
+    from paper_1911_03062_gb300.npfem import Solver
+    for mt in (I.rbc_type(), I.plt_type()):
+        s = Solver(precision=prec)
+        tid = s.create_type(mt)
+        P = O.OracleType.from_mesh_type(mt).P_dense()
+        q = np.random.default_rng(7).standard_normal((131, mt.nV))
+        z = s.apply_pinv(tid, torch.tensor(q, device="cuda"),
+                         torch.empty((131, mt.nV), dtype=torch.float64, device="cuda")).cpu().numpy()
+        ref = np.linalg.solve(P, q.T).T
+        resid = np.linalg.norm(q - z @ P, axis=1) / np.linalg.norm(q, axis=1)
+        assert resid.max() <= 1e-6, (prec, mt.name, resid.max())
+        assert np.abs(z - ref).max() <= 2e-6 * np.abs(ref).max()
+        st = s.stats()
+        assert st["max_refine_residual"] <= 1e-6
+        s.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_unrefined_apply_is_low_precision(prec):
+    # with no refinement sweep the apply carries the operand rounding (proves
+    # the tensor-core path, not an FP64 shortcut, produced the refined result)
+    import torch
+    from oracle import oracle as O
+    from paper_1911_03062_gb300.npfem import Solver
+    mt = I.rbc_type()
+    s = Solver(precision=prec, refine_max=0)
+    tid = s.create_type(mt)
+    P = O.OracleType.from_mesh_type(mt).P_dense()
+    q = np.random.default_rng(8).standard_normal((60, mt.nV))
+    z = s.apply_pinv(tid, torch.tensor(q, device="cuda"),
+                     torch.empty((60, mt.nV), dtype=torch.float64, device="cuda")).cpu().numpy()
+    resid = (np.linalg.norm(q - z @ P, axis=1) / np.linalg.norm(q, axis=1)).max()
+    assert 1e-6 < resid < (2e-2 if prec == "bf16" else 5e-3), resid
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_two_types_ragged_tiles(prec):
+    groups = make_groups([(I.rbc_type(), 50, 0.3), (I.plt_type(), 7, 0.3)])
+    xg, _, st = run_gpu(groups, 3, precision=prec)
+    xo, _ = run_oracle(groups, 3)
+    assert rel_pos_err(xg, xo, groups) <= TOL_MIXED
+    assert st["max_refine_residual"] <= 1e-6
+
+
+def test_one_rbc_twenty_steps_bf16():
+    groups = [I.materialise(I.Group(I.rbc_type(), 1, seed=0, amp=0.1))]
+    xg, _, _ = run_gpu(groups, 20, precision="bf16")
+    xo, _ = run_oracle(groups, 20)
+    assert rel_pos_err(xg, xo, groups) <= TOL_MIXED
+
+
+def test_rest_state_and_momentum_bf16():
+    g = I.materialise(I.Group(I.rbc_type(), 3, seed=9))
+    g.f_ext[:] = 0.0
+    xg, vg, _ = run_gpu([g], 2, precision="bf16")
+    assert np.abs(xg[0] - g.x0).max() <= 1e-9 * I.RBC_R0
+    g.v0 = np.random.default_rng(10).standard_normal(g.v0.shape)
+    _, vg, _ = run_gpu([g], 2, precision="bf16")
+    assert np.allclose(vg[0].mean(axis=1), g.v0.mean(axis=1), atol=1e-6)
+
+
+def test_checkpoint_resume_bitwise_bf16():
+    from paper_1911_03062_gb300.npfem import Solver
+    groups = make_groups([(I.rbc_type(), 3, 0.3), (I.plt_type(), 2, 0.3)])
+    f = public(groups, "f_ext")
+
+    def solver():
+        s = Solver(precision="bf16")
+        for g in groups:
+            s.add_cells(s.create_type(g.mtype), g.x0, g.v0)
+        return s
+
+    a = solver()
+    a.step(f)
+    x1, v1 = a.positions(), a.velocities()
+    a.step(f)
+    b = solver()
+    b.set_state(x1, v1)
+    b.step(f)
+    assert np.array_equal(a.positions(), b.positions())
+
+
+def test_sampled_cells_at_50k_bf16():
+    # the 50000 RBC + 5000 platelet workload in the bench's configuration (graph,
+    # BF16 apply, refinement to 1e-6), 1 step, sampled cells vs the oracle
+    groups = [I.materialise(g) for g in I.workload_groups("rbc50k_plt5k")]
+    xg, _, st = run_gpu(groups, 1, precision="bf16")
+    sample = [[0, 1, 25000, 49999], [0, 2500, 4999]]
+    xo, _ = run_oracle(groups, 1, sample=sample)
+    assert rel_pos_err(xg, xo, groups) <= TOL_MIXED
+    assert st["max_refine_residual"] <= 1e-6
