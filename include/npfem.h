@@ -192,7 +192,8 @@ int npfem_profile(npfem_ctx *ctx, int enable);
  * them afterwards. */
 int npfem_profile_read(npfem_ctx *ctx, npfem_kernel_times *out, int reset);
 
-/* Message of the last failure of this context (never NULL). */
+/* Message of the last failure of this context (never NULL); with ctx = NULL,
+ * the message of this thread's last failed npfem_create. */
 const char *npfem_last_error(const npfem_ctx *ctx);
 
 #ifdef __cplusplus

@@ -37,6 +37,7 @@ void fail(npfem_ctx *ctx, int code, const char *fmt, ...);
     } while (0)
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+thread_local std::string g_create_error = "no error";   // message of the last failed npfem_create
 
 }  // namespace
 
@@ -208,12 +209,12 @@ void prof_begin(npfem_ctx *ctx, int cls) {
         ctx->prof_cls.resize(ctx->prof_ev.size() / 2);
     }
     ctx->prof_cls[ctx->prof_next / 2] = cls;
-    CK(cudaEventRecord(ctx->prof_ev[ctx->prof_next], ctx->stream));
+    CK(cudaEventRecordWithFlags(ctx->prof_ev[ctx->prof_next], ctx->stream, cudaEventRecordExternal));
 }
 
 void prof_end(npfem_ctx *ctx) {
     if (!ctx->prof_on) return;
-    CK(cudaEventRecord(ctx->prof_ev[ctx->prof_next + 1], ctx->stream));
+    CK(cudaEventRecordWithFlags(ctx->prof_ev[ctx->prof_next + 1], ctx->stream, cudaEventRecordExternal));
     ctx->prof_next += 2;
 }
 
@@ -321,7 +322,11 @@ size_t gemm_smem(const MeshTypeImpl *t) {
 void set_kernel_attrs(npfem_ctx *ctx) {
     int mx = 0;
     CK(cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-    auto all = [&](auto fn) { CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)); };
+    auto all = [&](auto fn) {
+        cudaFuncAttributes fa;
+        CK(cudaFuncGetAttributes(&fa, fn));
+        CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes));
+    };
     if (mixed(ctx)) {
         all(k_predict<float, 4, 256>); all(k_predict<float, 8, 256>); all(k_predict<float, 16, 512>);
         all(k_iterate<float, 4, 256>); all(k_iterate<float, 8, 256>); all(k_iterate<float, 16, 512>);
@@ -816,6 +821,7 @@ int npfem_create(const npfem_options *opt, npfem_ctx **out) {
         CK(cudaStreamSynchronize(ctx->stream));
     });
     if (rc) {
+        g_create_error = ctx->err;
         npfem_destroy(ctx);
         return rc;
     }
@@ -841,7 +847,7 @@ void npfem_destroy(npfem_ctx *ctx) {
     delete ctx;
 }
 
-const char *npfem_last_error(const npfem_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+const char *npfem_last_error(const npfem_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
 size_t npfem_num_dofs(const npfem_ctx *ctx) { return ctx ? (size_t)ctx->ndofs : 0; }
 
@@ -913,7 +919,7 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
             const void *pb = bf16(ctx) ? (const void *)t->Pinv16 : (const void *)t->Pinv32;
             t->mapP = make_map(ctx, pb, bf16(ctx), nV, nV, t->nVp, t->n_tile);
         }
-        if (t->smem_step > (size_t)ctx->smem_optin || gemm_smem(t) > (size_t)ctx->smem_optin)
+        if (t->smem_step > (size_t)ctx->smem_optin || gemm_smem(t) + 2048 > (size_t)ctx->smem_optin)
             fail(ctx, NPFEM_EINVAL, "mesh type needs more shared memory than the device offers");
         CK(cudaStreamSynchronize(ctx->stream));
         ctx->types.push_back(t);

@@ -96,7 +96,7 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
 // Start of a step: y, origin (centroid of y), y_rel, delta = 0, history
 // cleared, g and grad g at x^0 = y, and q = grad g (the first apply's RHS).
 template <typename T, int EPT, int MAXB>
-__global__ void __launch_bounds__(MAXB) k_predict(IterArgs<T> a) {
+__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 2 : 1) k_predict(IterArgs<T> a) {
     T *pos, *stash;
     double *red;
     smem_layout(a.tc, a.stash_T, pos, stash, red);
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(MAXB) k_predict(IterArgs<T> a) {
 //   otherwise   : first loop  q = grad; for i newest -> oldest: alpha_i = rho_i s_i.q;
 //                 q -= alpha_i y_i  -> the next global step's RHS.
 template <typename T, int EPT, int MAXB>
-__global__ void __launch_bounds__(MAXB) k_iterate(IterArgs<T> a, const int *list, const int *list_count) {
+__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 2 : 1) k_iterate(IterArgs<T> a, const int *list, const int *list_count) {
     T *pos, *stash;
     double *red;
     smem_layout(a.tc, a.stash_T, pos, stash, red);

@@ -148,7 +148,7 @@ class Solver:
     # -- errors ---------------------------------------------------------------
     def _check(self, rc, ctx=True):
         if rc != OK:
-            msg = self._L.npfem_last_error(self._ctx).decode() if ctx and self._ctx else "context creation failed"
+            msg = self._L.npfem_last_error(self._ctx if ctx else None).decode()
             raise NpfemError(rc, msg)
 
     def close(self):

@@ -80,7 +80,11 @@ def test_rest_state_and_momentum_bf16():
     g = I.materialise(I.Group(I.rbc_type(), 3, seed=9))
     g.f_ext[:] = 0.0
     xg, vg, _ = run_gpu([g], 2, precision="bf16")
-    assert np.abs(xg[0] - g.x0).max() <= 1e-9 * I.RBC_R0
+    # Within a step the mixed forms hold positions as FP32 offsets from the cell
+    # centroid (half-ulp 1.2e-7 at R = 3.91), so the local step sees the rest
+    # shape perturbed by that much and relaxes it by about
+    # ulp x (elastic stiffness / (m/h^2)) ~ 1e-8 per step.
+    assert np.abs(xg[0] - g.x0).max() <= 1e-7 * I.RBC_R0
     g.v0 = np.random.default_rng(10).standard_normal(g.v0.shape)
     _, vg, _ = run_gpu([g], 2, precision="bf16")
     assert np.allclose(vg[0].mean(axis=1), g.v0.mean(axis=1), atol=1e-6)
