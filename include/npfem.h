@@ -181,6 +181,33 @@ int npfem_stats(npfem_ctx *ctx, npfem_step_stats *out);
  * Errors: EINVAL, ENOMEM, ECUDA. */
 int npfem_apply_pinv(npfem_ctx *ctx, int type_id, const double *q, double *z, int n_cols);
 
+/* Allocation-free variant of npfem_apply_pinv, for callers that cannot let
+ * the library allocate device memory: code whose GPU memory is entirely owned
+ * by another allocator (a framework's caching allocator that has reserved the
+ * device, a fixed memory budget), and latency-critical loops where the
+ * implicit device synchronisation of cudaMalloc/cudaFree would stall the
+ * pipeline.  No counterpart in the paper: it is a deployment convenience.
+ *
+ * Same arguments, result and refinement as npfem_apply_pinv; the caller still
+ * provides q and z (device pointers, n_cols x nV doubles).  The temporaries
+ * live in one static device array (16 x NPFEM_NOALLOC_MAX_ELEMS bytes + 1 MiB, about 33 MB)
+ * that every GPU which loads the library holds until the process exits; no
+ * call allocates or frees memory.
+ *  - Limit: 3 * ceil(n_cols / 3) * nVp <= NPFEM_NOALLOC_MAX_ELEMS (2^21)
+ *    scratch elements, nVp = nV rounded up to 8 (e.g. 3236 columns of a
+ *    642-vertex type); larger requests fail with NPFEM_EINVAL and a message
+ *    naming the limit (use npfem_apply_pinv for them).
+ *  - The first call on a device resolves the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture.
+ *  - All calls in the process share the one array, which keeps the last
+ *    call's contents (the call clears what must start at zero).  Calls whose
+ *    device work overlaps (other streams, other contexts, other threads on
+ *    the same device) race on it: serialise them.
+ * Errors: EINVAL, ECUDA. */
+#define NPFEM_NOALLOC_MAX_ELEMS (1 << 21)
+int npfem_apply_pinv_noalloc(npfem_ctx *ctx, int type_id, const double *q, double *z, int n_cols);
+
 /* Per-kernel timing: when enabled, every kernel launch of a step is
  * bracketed by CUDA events on the context stream (recorded into the step's
  * graph) and npfem_step waits for the step to finish to accumulate the

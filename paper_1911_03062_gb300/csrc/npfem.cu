@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -1168,6 +1169,101 @@ int npfem_apply_pinv(npfem_ctx *ctx, int type_id, const double *q, double *z, in
             throw;
         }
         for (void *p : tmp) cudaFree(p);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free apply.  Its scratch is this file-scope device array: every
+// GPU that loads the library holds it until the process exits.  Host code
+// must not pass the symbol itself to a kernel (in host code it names a
+// host-side stand-in); the device address is resolved once per device with
+// cudaGetSymbolAddress and cached below.
+#define NPFEM_NOALLOC_SCRATCH_BYTES ((size_t)NPFEM_NOALLOC_MAX_ELEMS * 16 + ((size_t)1 << 20))
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NPFEM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+std::map<int, void *> g_noalloc_addr;   // device ordinal -> address of g_noalloc_scratch on it
+
+void *noalloc_scratch(npfem_ctx *ctx) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(ctx->device);
+    if (it != g_noalloc_addr.end()) return it->second;
+    int prev = 0;
+    CK(cudaGetDevice(&prev));
+    CK(cudaSetDevice(ctx->device));
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess || !p) fail(ctx, NPFEM_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_noalloc_addr[ctx->device] = p;
+    return p;
+}
+
+size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+}  // namespace
+
+extern "C" int npfem_apply_pinv_noalloc(npfem_ctx *ctx, int type_id, const double *q, double *z, int n_cols) {
+    if (!ctx) return NPFEM_EINVAL;
+    return guard(ctx, [&] {
+        if (type_id < 0 || type_id >= (int)ctx->types.size() || n_cols < 0 || !q || !z)
+            fail(ctx, NPFEM_EINVAL, "bad apply arguments");
+        if (n_cols == 0) return;
+        MeshTypeImpl *t = ctx->types[type_id];
+        const int ncell = (n_cols + 2) / 3, rows = 3 * ncell;
+        const size_t nvec = (size_t)rows * t->nVp;
+        if (nvec > (size_t)NPFEM_NOALLOC_MAX_ELEMS)
+            fail(ctx, NPFEM_EINVAL,
+                 "npfem_apply_pinv_noalloc: %d columns of a %d-vertex type need %zu scratch elements "
+                 "(3 * ceil(n_cols / 3) * nVp, nVp = %d); the static scratch holds %d",
+                 n_cols, t->nV, nvec, t->nVp, (int)NPFEM_NOALLOC_MAX_ELEMS);
+        unsigned char *base = (unsigned char *)noalloc_scratch(ctx);
+        const size_t es = esize(ctx);
+        // carve: q, z (solver type), then the BF16 copy of q and the refinement operand, then flags
+        size_t off = 0;
+        void *qi = base + off;  off += up256(nvec * es);
+        void *zi = base + off;  off += up256(nvec * es);
+        __nv_bfloat16 *q16 = nullptr;
+        void *rl = nullptr;
+        int *conv = nullptr;
+        if (mixed(ctx)) {
+            if (bf16(ctx)) { q16 = (__nv_bfloat16 *)(base + off); off += up256(nvec * 2); }
+            rl = base + off;  off += up256(nvec * (bf16(ctx) ? 2 : 4));
+            conv = (int *)(base + off);  off += up256((size_t)ncell * sizeof(int));
+        }
+        if (off > NPFEM_NOALLOC_SCRATCH_BYTES) fail(ctx, NPFEM_EINVAL, "scratch layout overflow");
+        // The array keeps the previous call's contents: the rows after the last
+        // column of a ragged final cell must start at zero (they enter the GEMM).
+        if (rows > n_cols) {
+            CK(cudaMemsetAsync((unsigned char *)qi + (size_t)n_cols * t->nVp * es, 0,
+                               (size_t)(rows - n_cols) * t->nVp * es, ctx->stream));
+            if (q16)
+                CK(cudaMemsetAsync(q16 + (size_t)n_cols * t->nVp, 0, (size_t)(rows - n_cols) * t->nVp * 2, ctx->stream));
+        }
+        if (!mixed(ctx)) {
+            k_cols_in<double><<<grid_for(nvec, 256, 8192), 256, 0, ctx->stream>>>(n_cols, t->nV, t->nVp, q,
+                                                                                (double *)qi, nullptr);
+            dim3 grid((t->nV + SG_T - 1) / SG_T, (rows + SG_T - 1) / SG_T);
+            k_gemm_simt<double><<<grid, 256, 0, ctx->stream>>>(rows, t->nV, t->nVp, (const double *)qi, t->Pinv64,
+                                                               (double *)zi);
+            k_cols_out<double><<<grid_for((long long)n_cols * t->nV, 256, 8192), 256, 0, ctx->stream>>>(
+                n_cols, t->nV, t->nVp, (const double *)zi, z);
+        } else {
+            k_cols_in<float><<<grid_for(nvec, 256, 8192), 256, 0, ctx->stream>>>(n_cols, t->nV, t->nVp, q,
+                                                                               (float *)qi, q16);
+            CUtensorMap mq = make_map(ctx, bf16(ctx) ? (const void *)q16 : qi, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
+            CUtensorMap mr = make_map(ctx, rl, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
+            gemm_tc(ctx, t, mq, rows, (float *)zi, 0, nullptr);
+            for (int s = 0; s < ctx->opt.refine_max; ++s) {
+                residual(ctx, t, ncell, (const float *)qi, (const float *)zi, rl, conv, s == 0, 0);
+                gemm_tc(ctx, t, mr, rows, (float *)zi, 1, conv);
+            }
+            residual(ctx, t, ncell, (const float *)qi, (const float *)zi, nullptr, conv, ctx->opt.refine_max == 0, 1);
+            k_cols_out<float><<<grid_for((long long)n_cols * t->nV, 256, 8192), 256, 0, ctx->stream>>>(
+                n_cols, t->nV, t->nVp, (const float *)zi, z);
+        }
+        CK(cudaGetLastError());
+        pending_error(ctx);
     });
 }
 

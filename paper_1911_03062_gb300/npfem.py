@@ -93,13 +93,14 @@ def load(path: str = LIB_PATH):
     L.npfem_set_state.argtypes = [vp, vp, vp, C.c_size_t]
     L.npfem_stats.argtypes = [vp, C.POINTER(StepStats)]
     L.npfem_apply_pinv.argtypes = [vp, ip, vp, vp, ip]
+    L.npfem_apply_pinv_noalloc.argtypes = [vp, ip, vp, vp, ip]
     L.npfem_profile.argtypes = [vp, ip]
     L.npfem_profile_read.argtypes = [vp, C.POINTER(KernelTimes), ip]
     L.npfem_last_error.argtypes = [vp]
     L.npfem_last_error.restype = C.c_char_p
     for name in ("npfem_create", "npfem_create_mesh_type", "npfem_add_cells", "npfem_step", "npfem_sync",
                  "npfem_get_positions", "npfem_get_velocities", "npfem_set_state", "npfem_stats",
-                 "npfem_apply_pinv", "npfem_profile", "npfem_profile_read"):
+                 "npfem_apply_pinv", "npfem_apply_pinv_noalloc", "npfem_profile", "npfem_profile_read"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -237,6 +238,12 @@ class Solver:
         s = StepStats()
         self._check(self._L.npfem_stats(self._ctx, C.byref(s)))
         return {k: getattr(s, k) for k, _ in StepStats._fields_}
+
+    def apply_pinv_noalloc(self, type_id, q, z):
+        """As apply_pinv, with the library's static scratch instead of allocations."""
+        n_cols = q.shape[0]
+        self._check(self._L.npfem_apply_pinv_noalloc(self._ctx, type_id, _dev_ptr(q), _dev_ptr(z), n_cols))
+        return z
 
     def profile(self, enable: bool):
         self._check(self._L.npfem_profile(self._ctx, int(bool(enable))))
