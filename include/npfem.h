@@ -70,6 +70,9 @@ typedef struct {
     int device;             /* CUDA device ordinal (default 0) */
     void *cuda_stream;      /* cudaStream_t to run on, or NULL for a context-owned stream */
     const char *autotune_cache; /* file for tuned GEMM tile choices, or NULL (tune, keep in memory) */
+    int residual_fp64;      /* mixed forms: refinement residual with FP64 arithmetic (1) or with exact
+                               FP32 fused multiply-adds on a float-pair diagonal (0, default); both
+                               evaluate q - diag(P) z without cancellation error */
 } npfem_options;
 
 /* Material and time step of one mesh type.  Element weights follow the

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libnpfem.so")
 BUILD = os.path.join(ROOT, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-prec-div=false", "-prec-sqrt=false", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 SOURCES = ["npfem.cu"]
 
 

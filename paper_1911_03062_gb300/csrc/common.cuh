@@ -60,6 +60,9 @@ template <> struct Acc<double> {
     __device__ __forceinline__ void add(double x) { v += x; }
     __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
     __device__ __forceinline__ void merge_shfl(unsigned mask, int off) { v += __shfl_down_sync(mask, v, off); }
+    __device__ __forceinline__ void merge(const Acc &o) { v += o.v; }
+    __device__ __forceinline__ void store(double *p) const { *p = v; }
+    __device__ __forceinline__ void load(const double *p) { v = *p; }
     __device__ __forceinline__ double get() const { return v; }
 };
 
@@ -75,6 +78,13 @@ template <> struct Acc<float> {
     __device__ __forceinline__ void merge_shfl(unsigned mask, int off) {
         DF o{__shfl_down_sync(mask, v.hi, off), __shfl_down_sync(mask, v.lo, off)};
         v = df_add(v, o);
+    }
+    __device__ __forceinline__ void merge(const Acc &o) { v = df_add(v, o.v); }
+    __device__ __forceinline__ void store(double *p) const { *reinterpret_cast<float2 *>(p) = make_float2(v.hi, v.lo); }
+    __device__ __forceinline__ void load(const double *p) {
+        float2 f = *reinterpret_cast<const float2 *>(p);
+        v.hi = f.x;
+        v.lo = f.y;
     }
     __device__ __forceinline__ double get() const { return (double)v.hi + (double)v.lo; }
 };
@@ -105,7 +115,39 @@ __device__ __forceinline__ void block_reduce(Acc<T> (&a)[N], double (&out)[N], d
     __syncthreads();
 }
 
-template <typename T> __device__ __forceinline__ bool is_finite_t(T x) { return isfinite(x); }
+// Block-wide sums of N accumulators, combined by thread 0 (warps in index
+// order), which then calls fn(sums) with the totals in FP64; fn writes the
+// scalars the block needs to shared memory, visible to every thread when this
+// returns.  Only thread 0 does FP64 arithmetic.  Scratch: red[32 * N] doubles.
+template <typename T, int N, typename F>
+__device__ __forceinline__ void block_reduce_t0(Acc<T> (&a)[N], double *red, F &&fn) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i) a[i].merge_shfl(0xffffffffu, off);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) a[i].store(red + warp * N + i);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            Acc<T> t;
+            t.load(red + i);
+            for (int w = 1; w < nw; ++w) {
+                Acc<T> u;
+                u.load(red + w * N + i);
+                t.merge(u);
+            }
+            s[i] = t.get();
+        }
+        fn(s);
+    }
+    __syncthreads();
+}
 
 // ------------------------------------------------------------ type traits
 template <typename T> struct Prec;

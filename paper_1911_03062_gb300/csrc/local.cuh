@@ -10,30 +10,38 @@
 // projections p_i.  Layout: one cell's vectors are SoA [3][nVp] (component
 // major, vertex contiguous); thread t owns elements t + j*blockDim (j < EPT).
 // Positions are relative to a per-cell origin; x = y_rel + delta.
+//
+// Per-element contributions are gathered vertex by vertex through the
+// one-ring incidence lists (all three components per visit), in a fixed
+// order, so the result is deterministic.
 #pragma once
 
 #include "common.cuh"
 
 namespace npfem {
 
+// vertex -> triangle incidence: triangle, the two other vertices in CCW order
+// from this one (vb | vc << 16), and G[corner][0..1] with F[:,c] = sum_j G[j][c] x_j
+template <typename T> struct alignas(16) TriInc { int t; int bc; T g0, g1; };
+// vertex -> hinge incidence: hinge and the vertex's stencil coefficient
+template <typename T> struct alignas(2 * sizeof(T)) HingeInc { int h; T c; };
+
 template <typename T>
 struct TypeConst {
     int nV, nVp, nT, nH;
-    const int4 *tri;      // nT: (i0, i1, i2, 0), outward CCW
-    const T *dinv;        // nT x 4: inverse rest edge matrix D_m^{-1}, row major
-    const T *wtri;        // nT x 2: (k_strain, k_area) x rest area
-    const int4 *hv;       // nH: hinge (x0, x1, x2, x3)
-    const T *hc;          // nH x 4: cotangent stencil
-    const T *hrest;       // nH: |b| at rest
-    const int *vt_ptr;    // nV + 1: vertex -> triangle incidences (sorted by triangle)
-    const int *vt_inc;    //   (t << 2) | corner
-    const T *vt_g;        //   (G[corner][0], G[corner][1])
-    const int *vh_ptr;    // nV + 1: vertex -> hinge incidences (sorted by hinge)
-    const int *vh_inc;    //   (h << 2) | slot
-    const T *vh_c;        //   stencil coefficient of the vertex in that hinge
-    const T *mh2;         // nV: m_v / h^2
-    double V0;            // rest volume
-    T kb, kv;             // bending and volume weights
+    const int4 *tri;        // nT: (i0, i1, i2, 0), outward CCW
+    const T *dinv;          // nT x 4: inverse rest edge matrix D_m^{-1}, row major
+    const T *wtri;          // nT x 2: (k_strain, k_area) x rest area
+    const int4 *hv;         // nH: hinge (x0, x1, x2, x3)
+    const T *hc;            // nH x 4: cotangent stencil
+    const T *hrest;         // nH: |b| at rest
+    const int *vt_ptr;      // nV + 1: vertex -> triangle incidences (sorted by triangle)
+    const TriInc<T> *vt;
+    const int *vh_ptr;      // nV + 1: vertex -> hinge incidences (sorted by hinge)
+    const HingeInc<T> *vh;
+    const T *mh2;           // nV: m_v / h^2
+    double V0;              // rest volume
+    T kb, kv;               // bending and volume weights
 };
 
 __device__ __forceinline__ int elem_cv(int e, int nVp, int &v) {
@@ -41,6 +49,37 @@ __device__ __forceinline__ int elem_cv(int e, int nVp, int &v) {
     v = e - c * nVp;
     return c;
 }
+
+// Values broadcast by thread 0 after a block reduction.
+template <typename T>
+struct Bcast {
+    double d[8];
+    T t[8];
+    int i[8];
+};
+
+// Shared-memory layout of the per-cell kernels:
+//   red[128] doubles | Bcast | pos[3 nVp] | grad[3 nVp] | stash[stash_T]
+template <typename T>
+struct Smem {
+    double *red;
+    Bcast<T> *bc;
+    T *pos, *gsh, *stash;
+};
+
+template <typename T>
+__device__ __forceinline__ Smem<T> smem_layout(int nVp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<T> s;
+    s.red = reinterpret_cast<double *>(smem_raw);
+    s.bc = reinterpret_cast<Bcast<T> *>(smem_raw + 128 * sizeof(double));
+    s.pos = reinterpret_cast<T *>(smem_raw + 128 * sizeof(double) + sizeof(Bcast<double>) + 64);
+    s.gsh = s.pos + 3 * nVp;
+    s.stash = s.gsh + 3 * nVp;
+    return s;
+}
+
+__host__ __device__ constexpr size_t smem_header_bytes() { return 128 * sizeof(double) + sizeof(Bcast<double>) + 64; }
 
 // ---------------------------------------------------------------- 3x2 SVD
 // Closed-form eigen-decomposition of S = F^T F (2x2 symmetric):
@@ -52,7 +91,8 @@ __device__ __forceinline__ void svd32(const T F[6], T U[6], T V[4], T s[2]) {
     T b = F[0] * F[1] + F[2] * F[3] + F[4] * F[5];
     T c = F[1] * F[1] + F[3] * F[3] + F[5] * F[5];
     T half = T(0.5) * (a + c);
-    T dd = hypot(T(0.5) * (a - c), b);
+    T hd = T(0.5) * (a - c);
+    T dd = sqrt(hd * hd + b * b);
     T l1 = half + dd;
     T det = a * c - b * b;
     T l2 = (l1 > T(0)) ? det / l1 : T(0);
@@ -63,8 +103,8 @@ __device__ __forceinline__ void svd32(const T F[6], T U[6], T V[4], T s[2]) {
     } else {
         T w1x = l1 - c, w1y = b, w2x = b, w2y = l1 - a;
         T n1 = w1x * w1x + w1y * w1y, n2 = w2x * w2x + w2y * w2y;
-        if (n1 >= n2) { T n = sqrt(n1); v1x = w1x / n; v1y = w1y / n; }
-        else          { T n = sqrt(n2); v1x = w2x / n; v1y = w2y / n; }
+        if (n1 >= n2) { T n = T(1) / sqrt(n1); v1x = w1x * n; v1y = w1y * n; }
+        else          { T n = T(1) / sqrt(n2); v1x = w2x * n; v1y = w2y * n; }
     }
     T v2x = -v1y, v2y = v1x;
     V[0] = v1x; V[1] = v2x; V[2] = v1y; V[3] = v2y;
@@ -75,11 +115,13 @@ __device__ __forceinline__ void svd32(const T F[6], T U[6], T V[4], T s[2]) {
         u1[0] = 1; u1[1] = 0; u1[2] = 0;
         u2[0] = 0; u2[1] = 1; u2[2] = 0;
     } else {
+        const T i0 = T(1) / s[0];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) u1[r] = (F[2 * r] * v1x + F[2 * r + 1] * v1y) / s[0];
+        for (int r = 0; r < 3; ++r) u1[r] = (F[2 * r] * v1x + F[2 * r + 1] * v1y) * i0;
         if (s[1] > T(Prec<T>::degen_tol) * s[0]) {
+            const T i1 = T(1) / s[1];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) u2[r] = (F[2 * r] * v2x + F[2 * r + 1] * v2y) / s[1];
+            for (int r = 0; r < 3; ++r) u2[r] = (F[2 * r] * v2x + F[2 * r + 1] * v2y) * i1;
         } else {
             int ax = 0;
             if (fabs(u1[1]) < fabs(u1[ax])) ax = 1;
@@ -89,9 +131,9 @@ __device__ __forceinline__ void svd32(const T F[6], T U[6], T V[4], T s[2]) {
             T pr = e[0] * u1[0] + e[1] * u1[1] + e[2] * u1[2];
 #pragma unroll
             for (int r = 0; r < 3; ++r) u2[r] = e[r] - pr * u1[r];
-            T n = sqrt(u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
+            T n = T(1) / sqrt(u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
 #pragma unroll
-            for (int r = 0; r < 3; ++r) u2[r] /= n;
+            for (int r = 0; r < 3; ++r) u2[r] *= n;
         }
     }
 #pragma unroll
@@ -122,24 +164,27 @@ __device__ __forceinline__ void area_target(T s1, T s2, T d[2]) {
             if (step <= T(Prec<T>::area_tol)) break;
         }
     }
-    T q = T(1) - lam * lam;
-    d[0] = (s1 + lam * s2) / q;
-    d[1] = (s2 + lam * s1) / q;
+    T iq = T(1) / (T(1) - lam * lam);
+    d[0] = (s1 + lam * s2) * iq;
+    d[1] = (s2 + lam * s1) * iq;
 }
 
-// Strain + area projection of one triangle.  R = w_s (F - T_s) + w_a (F - T_a)
-// is stashed; the vertex gradient is sum_c R[:, c] G[corner][c].
+// Strain + area projection of one triangle.  Stashes R = w_s (F - T_s) +
+// w_a (F - T_a) (the vertex gradient is sum_c R[:, c] G[corner][c]) and
+// returns the signed-volume term (x0 - o).(e1 x e2) of the triangle.
 template <typename T>
-__device__ __forceinline__ void tri_local(const T *pos, int nVp, int4 tv, const T *Di, T ws, T wa,
-                                          T R[6], Acc<T> &en, Acc<T> &al) {
-    T F[6];
+__device__ __forceinline__ T tri_local(const T *pos, int nVp, int4 tv, const T *Di, T ws, T wa, const T o[3],
+                                       T R[6], Acc<T> &en, Acc<T> &al) {
+    T F[6], E1[3], E2[3], A0[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const T *pc = pos + c * nVp;
         T x0 = pc[tv.x];
-        T e1 = pc[tv.y] - x0, e2 = pc[tv.z] - x0;
-        F[2 * c] = e1 * Di[0] + e2 * Di[2];
-        F[2 * c + 1] = e1 * Di[1] + e2 * Di[3];
+        E1[c] = pc[tv.y] - x0;
+        E2[c] = pc[tv.z] - x0;
+        A0[c] = x0 - o[c];
+        F[2 * c] = E1[c] * Di[0] + E2[c] * Di[2];
+        F[2 * c + 1] = E1[c] * Di[1] + E2[c] * Di[3];
     }
     T U[6], V[4], s[2], d[2];
     svd32(F, U, V, s);
@@ -159,8 +204,9 @@ __device__ __forceinline__ void tri_local(const T *pos, int nVp, int4 tv, const 
         }
     en.add(T(0.5) * ws * ns);
     en.add(T(0.5) * wa * na);
-    T rf = sqrt(nf);
-    al.add(ws * sqrt(ns) * rf + wa * sqrt(na) * rf);
+    al.add((ws * sqrt(ns) + wa * sqrt(na)) * sqrt(nf));
+    return A0[0] * (E1[1] * E2[2] - E1[2] * E2[1]) + A0[1] * (E1[2] * E2[0] - E1[0] * E2[2]) +
+           A0[2] * (E1[0] * E2[1] - E1[1] * E2[0]);
 }
 
 // Bending of one hinge: b = sum_j c_j x_j, p = b |b_rest| / |b|; stash kb (b - p).
@@ -186,79 +232,84 @@ __device__ __forceinline__ void hinge_local(const T *pos, int nVp, int4 hv, cons
     al.add(kb * sqrt(n2) * nb);
 }
 
+// Signed volume of the current positions in pos (relative to vertex 0), partial per thread.
+template <typename T>
+__device__ __forceinline__ void volume_pass(const TypeConst<T> &tc, const T *pos, int nVp, Acc<T> &aV) {
+    const T o0 = pos[0], o1 = pos[nVp], o2 = pos[2 * nVp];
+    for (int t = threadIdx.x; t < tc.nT; t += blockDim.x) {
+        int4 tv = tc.tri[t];
+        T ax = pos[tv.x] - o0, ay = pos[nVp + tv.x] - o1, az = pos[2 * nVp + tv.x] - o2;
+        T e1x = pos[tv.y] - pos[tv.x], e1y = pos[nVp + tv.y] - pos[nVp + tv.x], e1z = pos[2 * nVp + tv.y] - pos[2 * nVp + tv.x];
+        T e2x = pos[tv.z] - pos[tv.x], e2y = pos[nVp + tv.z] - pos[nVp + tv.x], e2z = pos[2 * nVp + tv.z] - pos[2 * nVp + tv.x];
+        aV.add(ax * (e1y * e2z - e1z * e2y) + ay * (e1z * e2x - e1x * e2z) + az * (e1x * e2y - e1y * e2x));
+    }
+}
+
 // -------------------------------------------------------- the local step
 // dt: this thread's elements of delta (x = y_rel + delta); gr receives the
-// gradient; returns g(x) (all threads) and, in allow, a bound on the rounding
-// error of g for the FP32 path (8 u sum_i w_i |A_i x - p_i| |A_i x| + u * inertia).
-// Shared memory: pos[3 nVp], stash[stash_T], red[reduction scratch].
-template <typename T, int EPT>
-__device__ double local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, const T (&dt)[EPT],
-                             T (&gr)[EPT], double &allow, T *pos, T *stash, int stash_T, double *red) {
+// gradient.  After the final reduction thread 0 calls done(g, allow) with
+// g(x) and the rounding-error bound of g for the FP32 path
+// (8 u sum_i w_i |A_i x - p_i| |A_i x| + u * inertia); done writes what the
+// caller needs into S.bc before the closing barrier.
+template <typename T, int EPT, typename Done>
+__device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, const T (&dt)[EPT], T (&gr)[EPT],
+                           const Smem<T> &S, int stash_T, Done &&done) {
     const int B = blockDim.x, tid = threadIdx.x;
     const int nVp = tc.nVp, nV = tc.nV, n3 = 3 * nVp;
+    T *pos = S.pos, *gsh = S.gsh, *stash = S.stash;
     T x[EPT];
     Acc<T> en, al;
     en.zero();
     al.zero();
-    // 1. positions and the inertia term M/h^2 (x - y) = M/h^2 delta
+    // 1. positions; gradient buffer starts with the inertia term M/h^2 (x - y)
 #pragma unroll
     for (int j = 0; j < EPT; ++j) {
-        int e = tid + j * B;
-        int v;
+        int e = tid + j * B, v;
         x[j] = T(0);
-        gr[j] = T(0);
-        if (e < n3) {
-            elem_cv(e, nVp, v);
-            if (v < nV) {
-                x[j] = yrel[e] + dt[j];
-                pos[e] = x[j];
-                T mh = tc.mh2[v];
-                gr[j] = mh * dt[j];
-                T q = T(0.5) * mh * dt[j] * dt[j];
-                en.add(q);
-                al.add(q);
-            }
-        }
+        if (e >= n3) continue;
+        elem_cv(e, nVp, v);
+        if (v >= nV) { gsh[e] = T(0); continue; }
+        x[j] = yrel[e] + dt[j];
+        pos[e] = x[j];
+        T mh = tc.mh2[v];
+        gsh[e] = mh * dt[j];
+        T q = T(0.5) * mh * dt[j] * dt[j];
+        en.add(q);
+        al.add(q);
     }
     __syncthreads();
-    // 2. triangles (strain + area), chunked through the stash
+    Acc<T> aV;
+    aV.zero();
+    const T o[3] = {pos[0], pos[nVp], pos[2 * nVp]};
+    // 2. triangles (strain + area, and the volume of x), chunked through the stash
     {
         const int ct = stash_T / 6;
-        int cur[EPT];
-#pragma unroll
-        for (int j = 0; j < EPT; ++j) {
-            int e = tid + j * B, v;
-            cur[j] = 0;
-            if (e < n3) { elem_cv(e, nVp, v); if (v < nV) cur[j] = tc.vt_ptr[v]; }
-        }
         for (int t0 = 0; t0 < tc.nT; t0 += ct) {
             const int t1 = min(tc.nT, t0 + ct);
             for (int t = t0 + tid; t < t1; t += B) {
                 T R[6];
                 const T *Di = tc.dinv + 4 * t;
-                tri_local(pos, nVp, tc.tri[t], Di, tc.wtri[2 * t], tc.wtri[2 * t + 1], R, en, al);
+                aV.add(tri_local(pos, nVp, tc.tri[t], Di, tc.wtri[2 * t], tc.wtri[2 * t + 1], o, R, en, al));
                 T *st = stash + 6 * (t - t0);
 #pragma unroll
                 for (int i = 0; i < 6; ++i) st[i] = R[i];
             }
             __syncthreads();
-#pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                int e = tid + j * B, v;
-                if (e >= n3) continue;
-                int c = elem_cv(e, nVp, v);
-                if (v >= nV) continue;
+            for (int v = tid; v < nV; v += B) {
+                T g0 = T(0), g1 = T(0), g2 = T(0);
                 const int end = tc.vt_ptr[v + 1];
-                T acc = gr[j];
-                int k = cur[j];
-                for (; k < end; ++k) {
-                    int tt = tc.vt_inc[k] >> 2;
-                    if (tt >= t1) break;
-                    const T *st = stash + 6 * (tt - t0) + 2 * c;
-                    acc += st[0] * tc.vt_g[2 * k] + st[1] * tc.vt_g[2 * k + 1];
+                for (int k = tc.vt_ptr[v]; k < end; ++k) {
+                    const TriInc<T> inc = tc.vt[k];
+                    if (inc.t < t0) continue;
+                    if (inc.t >= t1) break;
+                    const T *st = stash + 6 * (inc.t - t0);
+                    g0 += st[0] * inc.g0 + st[1] * inc.g1;
+                    g1 += st[2] * inc.g0 + st[3] * inc.g1;
+                    g2 += st[4] * inc.g0 + st[5] * inc.g1;
                 }
-                cur[j] = k;
-                gr[j] = acc;
+                gsh[v] += g0;
+                gsh[nVp + v] += g1;
+                gsh[2 * nVp + v] += g2;
             }
             __syncthreads();
         }
@@ -266,13 +317,6 @@ __device__ double local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel,
     // 3. hinges (bending), chunked through the stash
     {
         const int ch = stash_T / 3;
-        int cur[EPT];
-#pragma unroll
-        for (int j = 0; j < EPT; ++j) {
-            int e = tid + j * B, v;
-            cur[j] = 0;
-            if (e < n3) { elem_cv(e, nVp, v); if (v < nV) cur[j] = tc.vh_ptr[v]; }
-        }
         for (int h0 = 0; h0 < tc.nH; h0 += ch) {
             const int h1 = min(tc.nH, h0 + ch);
             for (int h = h0 + tid; h < h1; h += B) {
@@ -282,22 +326,21 @@ __device__ double local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel,
                 st[0] = R[0]; st[1] = R[1]; st[2] = R[2];
             }
             __syncthreads();
-#pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                int e = tid + j * B, v;
-                if (e >= n3) continue;
-                int c = elem_cv(e, nVp, v);
-                if (v >= nV) continue;
+            for (int v = tid; v < nV; v += B) {
+                T g0 = T(0), g1 = T(0), g2 = T(0);
                 const int end = tc.vh_ptr[v + 1];
-                T acc = gr[j];
-                int k = cur[j];
-                for (; k < end; ++k) {
-                    int hh = tc.vh_inc[k] >> 2;
-                    if (hh >= h1) break;
-                    acc += tc.vh_c[k] * stash[3 * (hh - h0) + c];
+                for (int k = tc.vh_ptr[v]; k < end; ++k) {
+                    const HingeInc<T> inc = tc.vh[k];
+                    if (inc.h < h0) continue;
+                    if (inc.h >= h1) break;
+                    const T *st = stash + 3 * (inc.h - h0);
+                    g0 += inc.c * st[0];
+                    g1 += inc.c * st[1];
+                    g2 += inc.c * st[2];
                 }
-                cur[j] = k;
-                gr[j] = acc;
+                gsh[v] += g0;
+                gsh[nVp + v] += g1;
+                gsh[2 * nVp + v] += g2;
             }
             __syncthreads();
         }
@@ -305,82 +348,90 @@ __device__ double local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel,
     // 4. volume: p = closest point with V(p) = V0 by the Gauss-Newton
     //    iteration p_{j+1} = x + lambda_j gV(p_j),
     //    lambda_j = (V0 - V(p_j) - gV(p_j).(x - p_j)) / |gV(p_j)|^2,
-    //    stopped once |V(p_j) - V0| <= tol V0 or after 8 updates.  pos holds p.
+    //    stopped once |V(p_j) - V0| <= tol V0 or after 8 updates.  pos holds p;
+    //    the stash holds gV (vertex by vertex, all three components).
+    T p[EPT];
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) p[j] = x[j];
     {
-        T p[EPT];
-#pragma unroll
-        for (int j = 0; j < EPT; ++j) p[j] = x[j];
-        for (int it = 0;; ++it) {
-            const T o0 = pos[0], o1 = pos[nVp], o2 = pos[2 * nVp];
-            Acc<T> a[3];
-            a[0].zero(); a[1].zero(); a[2].zero();
-            for (int t = tid; t < tc.nT; t += B) {
-                int4 tv = tc.tri[t];
-                T ax = pos[tv.x] - o0, ay = pos[nVp + tv.x] - o1, az = pos[2 * nVp + tv.x] - o2;
-                T bx = pos[tv.y] - o0, by = pos[nVp + tv.y] - o1, bz = pos[2 * nVp + tv.y] - o2;
-                T cx = pos[tv.z] - o0, cy = pos[nVp + tv.z] - o1, cz = pos[2 * nVp + tv.z] - o2;
-                a[0].add(ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx));
-            }
-            T gV[EPT];
-#pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                gV[j] = T(0);
-                int e = tid + j * B, v;
-                if (e >= n3) continue;
-                int c = elem_cv(e, nVp, v);
-                if (v >= nV) continue;
-                const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-                const T oc1 = c1 == 0 ? o0 : (c1 == 1 ? o1 : o2);
-                const T oc2 = c2 == 0 ? o0 : (c2 == 1 ? o1 : o2);
-                T acc = T(0);
-                for (int k = tc.vt_ptr[v]; k < tc.vt_ptr[v + 1]; ++k) {
-                    int inc = tc.vt_inc[k];
-                    int4 tv = tc.tri[inc >> 2];
-                    int corner = inc & 3;
-                    int vb = corner == 0 ? tv.y : (corner == 1 ? tv.z : tv.x);
-                    int vc = corner == 0 ? tv.z : (corner == 1 ? tv.x : tv.y);
-                    // component c of (p_b - o) x (p_c - o)
-                    T b1 = pos[c1 * nVp + vb] - oc1, b2 = pos[c2 * nVp + vb] - oc2;
-                    T q1 = pos[c1 * nVp + vc] - oc1, q2 = pos[c2 * nVp + vc] - oc2;
-                    acc += b1 * q2 - b2 * q1;
+        Acc<T> a1[1] = {aV};
+        block_reduce_t0<T, 1>(a1, S.red, [&](const double *s) {
+            const double V = s[0] / 6.0;
+            S.bc->d[0] = V;
+            S.bc->i[0] = fabs(V - tc.V0) <= Prec<T>::vol_tol * fabs(tc.V0);
+        });
+        T *gV = stash;
+        for (int it = 0; !S.bc->i[0]; ++it) {
+            const T q0 = pos[0], q1 = pos[nVp], q2 = pos[2 * nVp];
+            for (int v = tid; v < nV; v += B) {
+                T g[3] = {T(0), T(0), T(0)};
+                const int end = tc.vt_ptr[v + 1];
+                for (int k = tc.vt_ptr[v]; k < end; ++k) {
+                    const int bc = tc.vt[k].bc;
+                    const int vb = bc & 0xffff, vc = bc >> 16;
+                    T bx = pos[vb] - q0, by = pos[nVp + vb] - q1, bz = pos[2 * nVp + vb] - q2;
+                    T cx = pos[vc] - q0, cy = pos[nVp + vc] - q1, cz = pos[2 * nVp + vc] - q2;
+                    g[0] += by * cz - bz * cy;
+                    g[1] += bz * cx - bx * cz;
+                    g[2] += bx * cy - by * cx;
                 }
-                gV[j] = acc / T(6);
-                a[1].add_prod(gV[j], gV[j]);
-                a[2].add_prod(gV[j], x[j] - p[j]);
+                gV[v] = g[0] / T(6);
+                gV[nVp + v] = g[1] / T(6);
+                gV[2 * nVp + v] = g[2] / T(6);
             }
-            double r[3];
-            block_reduce<T, 3>(a, r, red);
-            const double V = r[0] / 6.0;
-            if (fabs(V - tc.V0) <= Prec<T>::vol_tol * fabs(tc.V0) || it == 8) break;
-            const T lam = T((tc.V0 - V - r[2]) / r[1]);
+            __syncthreads();
+            Acc<T> a2[2];
+            a2[0].zero();
+            a2[1].zero();
 #pragma unroll
             for (int j = 0; j < EPT; ++j) {
                 int e = tid + j * B, v;
                 if (e >= n3) continue;
                 elem_cv(e, nVp, v);
                 if (v >= nV) continue;
-                p[j] = x[j] + lam * gV[j];
+                T gv = gV[e];
+                a2[0].add_prod(gv, gv);
+                a2[1].add_prod(gv, x[j] - p[j]);
+            }
+            block_reduce_t0<T, 2>(a2, S.red, [&](const double *s) {
+                S.bc->t[0] = T((tc.V0 - S.bc->d[0] - s[1]) / s[0]);
+            });
+            const T lam = S.bc->t[0];
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                int e = tid + j * B, v;
+                if (e >= n3) continue;
+                elem_cv(e, nVp, v);
+                if (v >= nV) continue;
+                p[j] = x[j] + lam * gV[e];
                 pos[e] = p[j];
             }
             __syncthreads();
-        }
-#pragma unroll
-        for (int j = 0; j < EPT; ++j) {
-            int e = tid + j * B, v;
-            if (e >= n3) continue;
-            elem_cv(e, nVp, v);
-            if (v >= nV) continue;
-            T r = x[j] - p[j];
-            en.add(T(0.5) * tc.kv * r * r);
-            al.add(tc.kv * fabs(r) * fabs(x[j]));
-            gr[j] += tc.kv * r;
+            Acc<T> a3[1];
+            a3[0].zero();
+            volume_pass(tc, pos, nVp, a3[0]);
+            block_reduce_t0<T, 1>(a3, S.red, [&](const double *s) {
+                const double V = s[0] / 6.0;
+                S.bc->d[0] = V;
+                S.bc->i[0] = fabs(V - tc.V0) <= Prec<T>::vol_tol * fabs(tc.V0) || it == 7;
+            });
         }
     }
+    // 5. gradient to registers (+ volume term), energy
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+        int e = tid + j * B, v;
+        gr[j] = T(0);
+        if (e >= n3) continue;
+        elem_cv(e, nVp, v);
+        if (v >= nV) continue;
+        T r = x[j] - p[j];
+        en.add(T(0.5) * tc.kv * r * r);
+        al.add(tc.kv * fabs(r) * fabs(x[j]));
+        gr[j] = gsh[e] + tc.kv * r;
+    }
     Acc<T> fin[2] = {en, al};
-    double out[2];
-    block_reduce<T, 2>(fin, out, red);
-    allow = 8.0 * Prec<T>::round_unit * out[1];
-    return out[0];
+    block_reduce_t0<T, 2>(fin, S.red, [&](const double *s) { done(s[0], 8.0 * Prec<T>::round_unit * s[1]); });
 }
 
 }  // namespace npfem

@@ -54,6 +54,7 @@ struct MeshTypeImpl {
     float *Pinv32 = nullptr;
     __nv_bfloat16 *Pinv16 = nullptr;
     double *diag = nullptr, *minv = nullptr;
+    float *dhi = nullptr, *dlo = nullptr;
     int *op = nullptr, *oj = nullptr;
     float *ov = nullptr;
     int n_off = 0;
@@ -339,7 +340,8 @@ void set_kernel_attrs(npfem_ctx *ctx) {
         all(k_iterate<double, 4, 256>); all(k_iterate<double, 8, 256>); all(k_iterate<double, 16, 512>);
         all(k_fallback_apply<double>);
     }
-    all(k_residual);
+    all(k_residual<false>);
+    all(k_residual<true>);
     ctx->smem_optin = mx;
 }
 
@@ -374,6 +376,8 @@ void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, c
     a.final_pass = final_pass;
     a.tol = ctx->opt.refine_tol;
     a.diag = t->diag;
+    a.dhi = t->dhi;
+    a.dlo = t->dlo;
     a.op = t->op;
     a.oj = t->oj;
     a.ov = t->ov;
@@ -384,9 +388,10 @@ void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, c
     a.conv = conv;
     a.any_active = ctx->d_any;
     a.st = ctx->d_st;
-    size_t smem = 128 * sizeof(double) + 3 * (size_t)t->nVp * sizeof(float);
+    size_t smem = 128 * sizeof(double) + 16 + 3 * (size_t)t->nVp * sizeof(float);
     prof_begin(ctx, NPFEM_K_RESIDUAL);
-    k_residual<<<rows_cells, 256, smem, ctx->stream>>>(a);
+    if (ctx->opt.residual_fp64) k_residual<true><<<rows_cells, 256, smem, ctx->stream>>>(a);
+    else k_residual<false><<<rows_cells, 256, smem, ctx->stream>>>(a);
     CK(cudaGetLastError());
     prof_end(ctx);
 }
@@ -642,12 +647,24 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
     c.hv = upload(ctx, hv, t->owned);
     c.hc = upload(ctx, cvt<T>(H.hc), t->owned);
     c.hrest = upload(ctx, cvt<T>(H.hrest), t->owned);
+    std::vector<TriInc<T>> vt(H.vt_inc.size());
+    for (size_t k = 0; k < vt.size(); ++k) {
+        const int tt = H.vt_inc[k] >> 2, corner = H.vt_inc[k] & 3;
+        const int vb = H.tri[3 * tt + (corner + 1) % 3], vc = H.tri[3 * tt + (corner + 2) % 3];
+        vt[k].t = tt;
+        vt[k].bc = vb | (vc << 16);
+        vt[k].g0 = (T)H.vt_g[2 * k];
+        vt[k].g1 = (T)H.vt_g[2 * k + 1];
+    }
+    std::vector<HingeInc<T>> vh(H.vh_inc.size());
+    for (size_t k = 0; k < vh.size(); ++k) {
+        vh[k].h = H.vh_inc[k] >> 2;
+        vh[k].c = (T)H.vh_c[k];
+    }
     c.vt_ptr = upload(ctx, H.vt_ptr, t->owned);
-    c.vt_inc = upload(ctx, H.vt_inc, t->owned);
-    c.vt_g = upload(ctx, cvt<T>(H.vt_g), t->owned);
+    c.vt = upload(ctx, vt, t->owned);
     c.vh_ptr = upload(ctx, H.vh_ptr, t->owned);
-    c.vh_inc = upload(ctx, H.vh_inc, t->owned);
-    c.vh_c = upload(ctx, cvt<T>(H.vh_c), t->owned);
+    c.vh = upload(ctx, vh, t->owned);
     c.mh2 = upload(ctx, cvt<T>(mh2), t->owned);
     c.V0 = H.V0;
     c.kb = (T)t->kb;
@@ -784,6 +801,7 @@ void npfem_default_options(npfem_options *o) {
     o->device = 0;
     o->cuda_stream = nullptr;
     o->autotune_cache = nullptr;
+    o->residual_fp64 = 0;
 }
 
 int npfem_create(const npfem_options *opt, npfem_ctx **out) {
@@ -900,6 +918,13 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         }
         t->minv = upload(ctx, minv, t->owned);
         t->diag = upload(ctx, diag, t->owned);
+        std::vector<float> dhi(nV), dlo(nV);
+        for (int v = 0; v < nV; ++v) {
+            dhi[v] = (float)diag[v];
+            dlo[v] = (float)(diag[v] - (double)dhi[v]);
+        }
+        t->dhi = upload(ctx, dhi, t->owned);
+        t->dlo = upload(ctx, dlo, t->owned);
         t->op = upload(ctx, op, t->owned);
         t->oj = upload(ctx, oj, t->owned);
         t->ov = upload(ctx, ov, t->owned);
@@ -913,8 +938,9 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         t->block = ((n3 + t->ept - 1) / t->ept + 31) / 32 * 32;
         const size_t es = esize(ctx);
         const size_t stash_cap = mixed(ctx) ? 16384 : 12288;
-        t->stash_T = (int)std::min<size_t>(6 * (size_t)nT, stash_cap);
-        t->smem_step = 128 * sizeof(double) + (3 * (size_t)t->nVp + t->stash_T) * es;
+        // the stash also holds the volume gradient (3 nVp values)
+        t->stash_T = (int)std::max<size_t>(3 * (size_t)t->nVp, std::min<size_t>(6 * (size_t)nT, stash_cap));
+        t->smem_step = smem_header_bytes() + (6 * (size_t)t->nVp + t->stash_T) * es;
         if (mixed(ctx)) {
             choose_tiles(ctx, t);
             const void *pb = bf16(ctx) ? (const void *)t->Pinv16 : (const void *)t->Pinv32;

@@ -54,25 +54,6 @@ __device__ __forceinline__ void store_vec(T *__restrict__ p, const T (&r)[EPT], 
     }
 }
 
-template <typename T, int EPT>
-__device__ __forceinline__ double bdot(const T (&a)[EPT], const T (&b)[EPT], double *red) {
-    Acc<T> s[1];
-    s[0].zero();
-#pragma unroll
-    for (int j = 0; j < EPT; ++j) s[0].add_prod(a[j], b[j]);
-    double o[1];
-    block_reduce<T, 1>(s, o, red);
-    return o[0];
-}
-
-template <typename T>
-__device__ __forceinline__ void smem_layout(const TypeConst<T> &tc, int stash_T, T *&pos, T *&stash, double *&red) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    red = reinterpret_cast<double *>(smem_raw);                      // 128 doubles
-    pos = reinterpret_cast<T *>(smem_raw + 128 * sizeof(double));
-    stash = pos + 3 * tc.nVp;
-}
-
 // y = x_n + h v_n + h^2 M^{-1} F_ext in FP64 for this thread's elements.
 template <typename T, int EPT>
 __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, double (&y)[EPT], double (&xo)[EPT]) {
@@ -96,10 +77,8 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
 // Start of a step: y, origin (centroid of y), y_rel, delta = 0, history
 // cleared, g and grad g at x^0 = y, and q = grad g (the first apply's RHS).
 template <typename T, int EPT, int MAXB>
-__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 2 : 1) k_predict(IterArgs<T> a) {
-    T *pos, *stash;
-    double *red;
-    smem_layout(a.tc, a.stash_T, pos, stash, red);
+__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 3 : 1) k_predict(IterArgs<T> a) {
+    const Smem<T> S = smem_layout<T>(a.tc.nVp);
     const int nVp = a.tc.nVp, n3 = 3 * nVp;
     for (int cell = blockIdx.x; cell < a.ncells; cell += gridDim.x) {
         const long long base = (long long)cell * n3;
@@ -116,10 +95,12 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 2 : 1) k_predict(IterArgs<
             if (v >= a.tc.nV) continue;
             s[c].add(y[j]);
         }
-        double o[3];
-        block_reduce<double, 3>(s, o, red);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) o[c] /= a.tc.nV;
+        block_reduce_t0<double, 3>(s, S.red, [&](const double *o) {
+            for (int c = 0; c < 3; ++c) {
+                S.bc->d[c] = o[c] / a.tc.nV;
+                a.origin[3 * cell + c] = S.bc->d[c];
+            }
+        });
         T yr[EPT], dl[EPT], gr[EPT];
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
@@ -129,21 +110,18 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 2 : 1) k_predict(IterArgs<
             if (e >= n3) continue;
             int c = elem_cv(e, nVp, v);
             if (v >= a.tc.nV) continue;
-            yr[j] = T(y[j] - o[c]);
+            yr[j] = T(y[j] - S.bc->d[c]);
         }
         store_vec<T, EPT>(a.yrel + base, yr, n3);
         store_vec<T, EPT>(a.delta + base, dl, n3);
-        if (threadIdx.x < 3) a.origin[3 * cell + threadIdx.x] = o[threadIdx.x];
         __syncthreads();
-        double allow;
-        double g = local_eval<T, EPT>(a.tc, a.yrel + base, dl, gr, allow, pos, stash, a.stash_T, red);
-        if (threadIdx.x == 0) {
+        local_eval<T, EPT>(a.tc, a.yrel + base, dl, gr, S, a.stash_T, [&](double g, double allow) {
             a.g[cell] = g;
             a.allow[cell] = allow;
             a.hcount[cell] = 0;
             a.hhead[cell] = 0;
             if (!isfinite(g)) dev_raise(a.st, DEV_ENONFINITE, cell);
-        }
+        });
         store_vec<T, EPT>(a.grad + base, gr, n3);
         store_vec<T, EPT>(a.q + base, gr, n3);
         if (a.q_bf16) {
@@ -167,69 +145,88 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 2 : 1) k_predict(IterArgs<
 //   last        : x_{n+1} = y + delta, v_{n+1} = (x_{n+1} - x_n)/h  (Eq. vel)
 //   otherwise   : first loop  q = grad; for i newest -> oldest: alpha_i = rho_i s_i.q;
 //                 q -= alpha_i y_i  -> the next global step's RHS.
+// Scalars (dots, coefficients, the Armijo and curvature tests) are formed by
+// thread 0 in FP64 and broadcast through shared memory.
 template <typename T, int EPT, int MAXB>
-__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 2 : 1) k_iterate(IterArgs<T> a, const int *list, const int *list_count) {
-    T *pos, *stash;
-    double *red;
-    smem_layout(a.tc, a.stash_T, pos, stash, red);
+__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 3 : 1) k_iterate(IterArgs<T> a, const int *list,
+                                                                      const int *list_count) {
+    const Smem<T> S = smem_layout<T>(a.tc.nVp);
     const int nVp = a.tc.nVp, n3 = 3 * nVp, m = a.m;
     const int nitems = list ? *list_count : a.ncells;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int cell = list ? list[item] : item;
         const long long base = (long long)cell * n3;
-        T *S = a.S + (long long)cell * m * n3;
-        T *Y = a.Y + (long long)cell * m * n3;
+        T *Sh = a.S + (long long)cell * m * n3;
+        T *Yh = a.Y + (long long)cell * m * n3;
         double *rho = a.rho + (long long)cell * m, *alp = a.alpha + (long long)cell * m;
         int cnt = a.hcount[cell], head = a.hhead[cell];
         T r[EPT], d[EPT], gr[EPT], dl[EPT];
         load_vec<T, EPT>(a.z + base, r, n3);
         for (int l = cnt - 1; l >= 0; --l) {
-            int i = ((head - 1 - l) % m + m) % m;
+            const int i = ((head - 1 - l) % m + m) % m;
             T yi[EPT], si[EPT];
-            load_vec<T, EPT>(Y + (long long)i * n3, yi, n3);
-            double be = rho[i] * bdot<T, EPT>(yi, r, red);
-            load_vec<T, EPT>(S + (long long)i * n3, si, n3);
-            T coef = T(alp[i] - be);
+            load_vec<T, EPT>(Yh + (long long)i * n3, yi, n3);
+            load_vec<T, EPT>(Sh + (long long)i * n3, si, n3);
+            Acc<T> ac[1];
+            ac[0].zero();
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) ac[0].add_prod(yi[j], r[j]);
+            block_reduce_t0<T, 1>(ac, S.red, [&](const double *s) { S.bc->t[0] = T(alp[i] - rho[i] * s[0]); });
+            const T coef = S.bc->t[0];
 #pragma unroll
             for (int j = 0; j < EPT; ++j) r[j] += si[j] * coef;
         }
 #pragma unroll
         for (int j = 0; j < EPT; ++j) d[j] = -r[j];
         load_vec<T, EPT>(a.grad + base, gr, n3);
-        const double gd = bdot<T, EPT>(gr, d, red);
-        if (gd >= 0.0 && cnt > 0) {
-            if (threadIdx.x == 0) {
-                a.hcount[cell] = 0;
-                a.hhead[cell] = 0;
-                a.fb_list[atomicAdd(a.fb_count, 1)] = cell;
-                atomicAdd(&a.st->fallbacks, 1ull);
-            }
+        {
+            Acc<T> ac[1];
+            ac[0].zero();
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) ac[0].add_prod(gr[j], d[j]);
+            block_reduce_t0<T, 1>(ac, S.red, [&](const double *s) {
+                S.bc->d[1] = s[0];                       // grad . d
+                S.bc->d[2] = 1.0;                        // alpha
+                S.bc->i[2] = 0;                          // halvings
+                S.bc->i[1] = (s[0] >= 0.0 && cnt > 0);   // not a descent direction
+                if (S.bc->i[1]) {
+                    a.hcount[cell] = 0;
+                    a.hhead[cell] = 0;
+                    a.fb_list[atomicAdd(a.fb_count, 1)] = cell;
+                    atomicAdd(&a.st->fallbacks, 1ull);
+                }
+            });
+        }
+        if (S.bc->i[1]) {
             store_vec<T, EPT>(a.q + base, gr, n3);
             __syncthreads();
             continue;
         }
         load_vec<T, EPT>(a.delta + base, dl, n3);
-        const double g0 = a.g[cell];
-        const double allow0 = a.use_allow ? a.allow[cell] : 0.0;
         T dt[EPT], gt[EPT];
-        double gtv = 0.0, allow_t = 0.0, alpha = 1.0;
-        int bt = 0;
+        T alpha = T(1);
         for (;;) {
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) dt[j] = dl[j] + T(alpha) * d[j];
-            gtv = local_eval<T, EPT>(a.tc, a.yrel + base, dt, gt, allow_t, pos, stash, a.stash_T, red);
-            double slack = a.use_allow ? (allow0 + allow_t) : 0.0;
-            if (gtv <= g0 + a.c1 * alpha * gd + slack) break;
-            if (bt == a.max_bt) {
-                if (threadIdx.x == 0) atomicAdd(&a.st->capped, 1ull);
-                break;
-            }
-            alpha *= 0.5;
-            ++bt;
-        }
-        if (threadIdx.x == 0) {
-            if (bt) atomicAdd(&a.st->backtracks, (unsigned long long)bt);
-            if (!isfinite(gtv)) dev_raise(a.st, DEV_ENONFINITE, cell);
+            for (int j = 0; j < EPT; ++j) dt[j] = dl[j] + alpha * d[j];
+            local_eval<T, EPT>(a.tc, a.yrel + base, dt, gt, S, a.stash_T, [&](double g, double allow) {
+                const double al = S.bc->d[2], gd = S.bc->d[1];
+                const double slack = a.use_allow ? (a.allow[cell] + allow) : 0.0;
+                S.bc->d[3] = g;
+                S.bc->d[4] = allow;
+                if (g <= a.g[cell] + a.c1 * al * gd + slack) {
+                    S.bc->i[3] = 1;
+                } else if (S.bc->i[2] == a.max_bt) {
+                    S.bc->i[3] = 2;
+                    atomicAdd(&a.st->capped, 1ull);
+                } else {
+                    S.bc->i[3] = 0;
+                    S.bc->d[2] = 0.5 * al;
+                    S.bc->t[2] = T(0.5 * al);
+                    S.bc->i[2] += 1;
+                }
+            });
+            if (S.bc->i[3]) break;
+            alpha = S.bc->t[2];
         }
         // history pair
         T sv[EPT], yv[EPT];
@@ -243,20 +240,26 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 2 : 1) k_iterate(IterArgs<
             h3[1].add_prod(sv[j], sv[j]);
             h3[2].add_prod(yv[j], yv[j]);
         }
-        double hs[3];
-        block_reduce<T, 3>(h3, hs, red);
-        if (m > 0 && hs[0] > 1e-12 * sqrt(hs[1]) * sqrt(hs[2])) {
-            store_vec<T, EPT>(S + (long long)head * n3, sv, n3);
-            store_vec<T, EPT>(Y + (long long)head * n3, yv, n3);
-            if (threadIdx.x == 0) rho[head] = 1.0 / hs[0];
+        block_reduce_t0<T, 3>(h3, S.red, [&](const double *hs) {
+            const int keep = m > 0 && hs[0] > 1e-12 * sqrt(hs[1]) * sqrt(hs[2]);
+            S.bc->i[4] = keep;
+            if (keep) rho[head] = 1.0 / hs[0];
+            const double gtv = S.bc->d[3];
+            a.g[cell] = gtv;
+            a.allow[cell] = S.bc->d[4];
+            if (S.bc->i[2]) atomicAdd(&a.st->backtracks, (unsigned long long)S.bc->i[2]);
+            if (!isfinite(gtv)) dev_raise(a.st, DEV_ENONFINITE, cell);
+            if (a.last) atomicAdd(&a.st->energy_sum, gtv);
+        });
+        if (S.bc->i[4]) {
+            store_vec<T, EPT>(Sh + (long long)head * n3, sv, n3);
+            store_vec<T, EPT>(Yh + (long long)head * n3, yv, n3);
             head = (head + 1) % m;
             if (cnt < m) ++cnt;
         }
         store_vec<T, EPT>(a.delta + base, dt, n3);
         store_vec<T, EPT>(a.grad + base, gt, n3);
         if (threadIdx.x == 0) {
-            a.g[cell] = gtv;
-            a.allow[cell] = allow_t;
             a.hcount[cell] = cnt;
             a.hhead[cell] = head;
         }
@@ -271,20 +274,25 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 2 : 1) k_iterate(IterArgs<
                 a.xn[base + e] = x;
                 a.vn[base + e] = (x - xo[j]) / a.h;
             }
-            if (threadIdx.x == 0) atomicAdd(&a.st->energy_sum, gtv);
         } else {
-            __syncthreads();   // rho/alpha of this block visible to all its threads
             T qv[EPT];
 #pragma unroll
             for (int j = 0; j < EPT; ++j) qv[j] = gt[j];
             for (int l = 0; l < cnt; ++l) {
-                int i = ((head - 1 - l) % m + m) % m;
+                const int i = ((head - 1 - l) % m + m) % m;
                 T si[EPT], yi[EPT];
-                load_vec<T, EPT>(S + (long long)i * n3, si, n3);
-                double al = rho[i] * bdot<T, EPT>(si, qv, red);
-                if (threadIdx.x == 0) alp[i] = al;
-                load_vec<T, EPT>(Y + (long long)i * n3, yi, n3);
-                T ca = T(al);
+                load_vec<T, EPT>(Sh + (long long)i * n3, si, n3);
+                load_vec<T, EPT>(Yh + (long long)i * n3, yi, n3);
+                Acc<T> ac[1];
+                ac[0].zero();
+#pragma unroll
+                for (int j = 0; j < EPT; ++j) ac[0].add_prod(si[j], qv[j]);
+                block_reduce_t0<T, 1>(ac, S.red, [&](const double *s) {
+                    const double al = rho[i] * s[0];
+                    alp[i] = al;
+                    S.bc->t[0] = T(al);
+                });
+                const T ca = S.bc->t[0];
 #pragma unroll
                 for (int j = 0; j < EPT; ++j) qv[j] -= ca * yi[j];
             }
@@ -327,17 +335,26 @@ __global__ void k_fallback_apply(int nV, int nVp, const T *__restrict__ Pinv, co
     }
 }
 
-// FP64 refinement residual of the global step (mixed forms):
-//   r = q - P z = (q - diag(P) z)  [FP64]  - offdiag(P) z  [FP32],
-// written in the GEMM operand type for the correction apply; per cell
-// conv = |r| <= tol |q| (2-norms over the cell's three components).
-// first: evaluate every cell; otherwise cells already converged are skipped
-// (the correction GEMM leaves their rows untouched).  final_pass: norms only,
-// for the statistics of cells that never converged.
+// Refinement residual of the global step (mixed forms), r = q - P z with
+// P = diag(P) + offdiag(P).  The cancellation sits in q - diag(P) z (r is
+// ~1e-3 of q after a BF16 apply), so that part must be exact:
+//   FP64R = true : r = (q - diag z) in FP64, minus offdiag z in FP32;
+//   FP64R = false: diag(P) held as a float pair hi + lo, r = fma(-lo, z,
+//                  fma(-hi, z, q)) - offdiag z.  Both products are exact in
+//                  the fused multiply-adds and q, z are FP32 values, so the
+//                  result carries one rounding of r itself, not of q.
+// The off-diagonal part is ~1% of q; its FP32 rounding puts the floor of the
+// residual near 1e-9 |q| in both variants.  The residual is written in the
+// GEMM operand type for the correction apply; per cell conv = |r| <= tol |q|
+// (2-norms over the cell's three components).  first: evaluate every cell;
+// otherwise cells already converged are skipped (the correction GEMM leaves
+// their rows untouched).  final_pass: norms only, for the statistics of
+// cells that never converged.
 struct ResidArgs {
     int ncells, nV, nVp, first, final_pass;
     double tol;
-    const double *diag;      // [nV]
+    const double *diag;      // [nV] diag(P)
+    const float *dhi, *dlo;  // [nV] diag(P) = dhi + dlo (+ O(2^-48))
     const int *op, *oj;      // off-diagonal CSR
     const float *ov;
     const float *q, *z;
@@ -348,39 +365,43 @@ struct ResidArgs {
     DevStatus *st;
 };
 
-__global__ void k_residual(ResidArgs a) {
+template <bool FP64R>
+__global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *red = reinterpret_cast<double *>(smem_raw);
-    float *zs = reinterpret_cast<float *>(smem_raw + 128 * sizeof(double));
+    float *zs = reinterpret_cast<float *>(smem_raw + 128 * sizeof(double) + 16);
     const int nVp = a.nVp, n3 = 3 * nVp;
     for (int cell = blockIdx.x; cell < a.ncells; cell += gridDim.x) {
         if (!a.first && a.conv[cell]) continue;
         const long long base = (long long)cell * n3;
         for (int e = threadIdx.x; e < n3; e += blockDim.x) zs[e] = a.z[base + e];
         __syncthreads();
-        Acc<double> s[2];
+        Acc<float> s[2];
         s[0].zero(); s[1].zero();
         for (int e = threadIdx.x; e < n3; e += blockDim.x) {
             int v, c = elem_cv(e, nVp, v);
-            double r = 0.0;
+            float r = 0.f;
             if (v < a.nV) {
-                const double qv = (double)a.q[base + e];
-                r = fma(-a.diag[v], (double)zs[e], qv);
+                const float qv = a.q[base + e], zv = zs[e];
                 float off = 0.f;
                 const float *zc = zs + c * nVp;
                 for (int k = a.op[v]; k < a.op[v + 1]; ++k) off = fmaf(a.ov[k], zc[a.oj[k]], off);
-                r -= (double)off;
-                s[0].add(r * r);
-                s[1].add(qv * qv);
+                if (FP64R) {
+                    r = (float)(fma(-a.diag[v], (double)zv, (double)qv) - (double)off);
+                } else {
+                    r = __fmaf_rn(-a.dhi[v], zv, qv);
+                    r = __fmaf_rn(-a.dlo[v], zv, r);
+                    r = __fsub_rn(r, off);
+                }
+                s[0].add_prod(r, r);
+                s[1].add_prod(qv, qv);
             }
             if (!a.final_pass) {
-                if (a.r_bf16) a.r_bf16[base + e] = __float2bfloat16_rn((float)r);
-                else a.r_f32[base + e] = (float)r;
+                if (a.r_bf16) a.r_bf16[base + e] = __float2bfloat16_rn(r);
+                else a.r_f32[base + e] = r;
             }
         }
-        double nr[2];
-        block_reduce<double, 2>(s, nr, red);
-        if (threadIdx.x == 0) {
+        block_reduce_t0<float, 2>(s, red, [&](const double *nr) {
             const bool ok = nr[0] <= a.tol * a.tol * nr[1];
             const float ratio = nr[1] > 0 ? (float)sqrt(nr[0] / nr[1]) : 0.f;
             if (a.final_pass || ok) atomicMax(&a.st->max_resid_bits, __float_as_uint(ratio));
@@ -391,8 +412,7 @@ __global__ void k_residual(ResidArgs a) {
                     atomicAdd(&a.st->refine_sweeps, 1ull);
                 }
             }
-        }
-        __syncthreads();
+        });
     }
 }
 
