@@ -377,7 +377,8 @@ def main():
     b = 8 if precision == "fp64" else 4
     roof = None
     if dom in ("iterate", "predict"):
-        byts = sum(algorithmic_bytes_iterate(g.mtype.nV, g.n_cells, K, 5, b, bf16) for g in groups)
+        # bytes of one step's k_iterate launches (K per type) / launches per step
+        byts = K * sum(algorithmic_bytes_iterate(g.mtype.nV, g.n_cells, K, 5, b, bf16) for g in groups)
         launches_per_step = prof[dom][1] / args.steps
         avg_ms = prof[dom][0] / prof[dom][1]
         per_launch = byts / (launches_per_step if launches_per_step else 1)
@@ -385,7 +386,7 @@ def main():
         roof = {"kernel": "k_iterate", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": None, "peak_source": peak_src}
     elif dom in ("gemm", "gemm_refine"):
-        byts = sum(algorithmic_gemm(g.mtype.nV, g.n_cells, bf16)[0] for g in groups)
+        byts = K * sum(algorithmic_gemm(g.mtype.nV, g.n_cells, bf16)[0] for g in groups)
         launches_per_step = prof[dom][1] / args.steps
         avg_ms = prof[dom][0] / prof[dom][1]
         ach = byts / launches_per_step / (avg_ms / 1e3) / 1e9

@@ -115,10 +115,12 @@ __device__ __forceinline__ void block_reduce(Acc<T> (&a)[N], double (&out)[N], d
     __syncthreads();
 }
 
-// Block-wide sums of N accumulators, combined by thread 0 (warps in index
-// order), which then calls fn(sums) with the totals in FP64; fn writes the
-// scalars the block needs to shared memory, visible to every thread when this
-// returns.  Only thread 0 does FP64 arithmetic.  Scratch: red[32 * N] doubles.
+// Block-wide sums of N accumulators: each warp reduces by shuffles, warp 0
+// combines the per-warp partials by a second shuffle tree (fixed order, so
+// the result is deterministic), and thread 0 calls fn(sums) with the totals
+// in FP64; fn writes the scalars the block needs to shared memory, visible
+// to every thread when this returns.  Only thread 0 does FP64 arithmetic.
+// Scratch: red[32 * N] doubles.
 template <typename T, int N, typename F>
 __device__ __forceinline__ void block_reduce_t0(Acc<T> (&a)[N], double *red, F &&fn) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -131,20 +133,24 @@ __device__ __forceinline__ void block_reduce_t0(Acc<T> (&a)[N], double *red, F &
 #pragma unroll
         for (int i = 0; i < N; ++i) a[i].store(red + warp * N + i);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s[N];
+    if (warp == 0) {
+        Acc<T> t[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            Acc<T> t;
-            t.load(red + i);
-            for (int w = 1; w < nw; ++w) {
-                Acc<T> u;
-                u.load(red + w * N + i);
-                t.merge(u);
-            }
-            s[i] = t.get();
+            if (lane < nw) t[i].load(red + lane * N + i);
+            else t[i].zero();
         }
-        fn(s);
+        for (int off = 16; off > 0; off >>= 1) {
+            if (off >= nw * 2) continue;       // lanes >= nw hold zeros: skip empty levels
+#pragma unroll
+            for (int i = 0; i < N; ++i) t[i].merge_shfl(0xffffffffu, off);
+        }
+        if (lane == 0) {
+            double s[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) s[i] = t[i].get();
+            fn(s);
+        }
     }
     __syncthreads();
 }

@@ -59,12 +59,12 @@ struct Bcast {
 };
 
 // Shared-memory layout of the per-cell kernels:
-//   red[128] doubles | Bcast | pos[3 nVp] | grad[3 nVp] | stash[stash_T]
+//   red[128] doubles | Bcast | pos[3 nVp] | grad[3 nVp] | gva[3 nVp] | stash[stash_T]
 template <typename T>
 struct Smem {
     double *red;
     Bcast<T> *bc;
-    T *pos, *gsh, *stash;
+    T *pos, *gsh, *gva, *stash;
 };
 
 template <typename T>
@@ -75,11 +75,13 @@ __device__ __forceinline__ Smem<T> smem_layout(int nVp) {
     s.bc = reinterpret_cast<Bcast<T> *>(smem_raw + 128 * sizeof(double));
     s.pos = reinterpret_cast<T *>(smem_raw + 128 * sizeof(double) + sizeof(Bcast<double>) + 64);
     s.gsh = s.pos + 3 * nVp;
-    s.stash = s.gsh + 3 * nVp;
+    s.gva = s.gsh + 3 * nVp;
+    s.stash = s.gva + 3 * nVp;
     return s;
 }
 
 __host__ __device__ constexpr size_t smem_header_bytes() { return 128 * sizeof(double) + sizeof(Bcast<double>) + 64; }
+constexpr int SMEM_VECS = 3;   // pos, grad, gva: 3 nVp values each
 
 // ---------------------------------------------------------------- 3x2 SVD
 // Closed-form eigen-decomposition of S = F^T F (2x2 symmetric):
@@ -169,12 +171,13 @@ __device__ __forceinline__ void area_target(T s1, T s2, T d[2]) {
     d[1] = (s2 + lam * s1) * iq;
 }
 
-// Strain + area projection of one triangle.  Stashes R = w_s (F - T_s) +
-// w_a (F - T_a) (the vertex gradient is sum_c R[:, c] G[corner][c]) and
-// returns the signed-volume term (x0 - o).(e1 x e2) of the triangle.
+// Strain + area projection of one triangle.  Returns R = w_s (F - T_s) +
+// w_a (F - T_a) (the vertex gradient is sum_c R[:, c] G[corner][c]), N =
+// (e1 x e2) / 6 (each corner's share of the volume gradient) and the
+// signed-volume term (x0 - o).(e1 x e2) of the triangle.
 template <typename T>
 __device__ __forceinline__ T tri_local(const T *pos, int nVp, int4 tv, const T *Di, T ws, T wa, const T o[3],
-                                       T R[6], Acc<T> &en, Acc<T> &al) {
+                                       T R[6], T N[3], T &en, T &al) {
     T F[6], E1[3], E2[3], A0[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -202,17 +205,19 @@ __device__ __forceinline__ T tri_local(const T *pos, int nVp, int4 tv, const T *
             nf += F[2 * r + c] * F[2 * r + c];
             R[2 * r + c] = ws * rs + wa * ra;
         }
-    en.add(T(0.5) * ws * ns);
-    en.add(T(0.5) * wa * na);
-    al.add((ws * sqrt(ns) + wa * sqrt(na)) * sqrt(nf));
-    return A0[0] * (E1[1] * E2[2] - E1[2] * E2[1]) + A0[1] * (E1[2] * E2[0] - E1[0] * E2[2]) +
-           A0[2] * (E1[0] * E2[1] - E1[1] * E2[0]);
+    en += T(0.5) * ws * ns + T(0.5) * wa * na;
+    al += (ws * sqrt(ns) + wa * sqrt(na)) * sqrt(nf);
+    T C0 = E1[1] * E2[2] - E1[2] * E2[1], C1 = E1[2] * E2[0] - E1[0] * E2[2], C2 = E1[0] * E2[1] - E1[1] * E2[0];
+    N[0] = C0 / T(6);
+    N[1] = C1 / T(6);
+    N[2] = C2 / T(6);
+    return A0[0] * C0 + A0[1] * C1 + A0[2] * C2;
 }
 
 // Bending of one hinge: b = sum_j c_j x_j, p = b |b_rest| / |b|; stash kb (b - p).
 template <typename T>
 __device__ __forceinline__ void hinge_local(const T *pos, int nVp, int4 hv, const T *hc, T rest, T kb,
-                                            T R[3], Acc<T> &en, Acc<T> &al) {
+                                            T R[3], T &en, T &al) {
     T b[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -228,8 +233,8 @@ __device__ __forceinline__ void hinge_local(const T *pos, int nVp, int4 hv, cons
         n2 += r * r;
         R[c] = kb * r;
     }
-    en.add(T(0.5) * kb * n2);
-    al.add(kb * sqrt(n2) * nb);
+    en += T(0.5) * kb * n2;
+    al += kb * sqrt(n2) * nb;
 }
 
 // Signed volume of the current positions in pos (relative to vertex 0), partial per thread.
@@ -256,11 +261,9 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                            const Smem<T> &S, int stash_T, Done &&done) {
     const int B = blockDim.x, tid = threadIdx.x;
     const int nVp = tc.nVp, nV = tc.nV, n3 = 3 * nVp;
-    T *pos = S.pos, *gsh = S.gsh, *stash = S.stash;
+    T *pos = S.pos, *gsh = S.gsh, *gva = S.gva, *stash = S.stash;
     T x[EPT];
-    Acc<T> en, al;
-    en.zero();
-    al.zero();
+    T en = T(0), al = T(0);      // energy and allowance partials (per thread: a handful of terms)
     // 1. positions; gradient buffer starts with the inertia term M/h^2 (x - y)
 #pragma unroll
     for (int j = 0; j < EPT; ++j) {
@@ -268,48 +271,56 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
         x[j] = T(0);
         if (e >= n3) continue;
         elem_cv(e, nVp, v);
+        gva[e] = T(0);
         if (v >= nV) { gsh[e] = T(0); continue; }
         x[j] = yrel[e] + dt[j];
         pos[e] = x[j];
         T mh = tc.mh2[v];
         gsh[e] = mh * dt[j];
         T q = T(0.5) * mh * dt[j] * dt[j];
-        en.add(q);
-        al.add(q);
+        en += q;
+        al += q;
     }
     __syncthreads();
     Acc<T> aV;
     aV.zero();
     const T o[3] = {pos[0], pos[nVp], pos[2 * nVp]};
-    // 2. triangles (strain + area, and the volume of x), chunked through the stash
+    // 2. triangles (strain + area, the volume of x and its gradient), chunked through the stash
     {
-        const int ct = stash_T / 6;
+        const int ct = stash_T / 9;
         for (int t0 = 0; t0 < tc.nT; t0 += ct) {
             const int t1 = min(tc.nT, t0 + ct);
             for (int t = t0 + tid; t < t1; t += B) {
-                T R[6];
+                T R[6], N[3];
                 const T *Di = tc.dinv + 4 * t;
-                aV.add(tri_local(pos, nVp, tc.tri[t], Di, tc.wtri[2 * t], tc.wtri[2 * t + 1], o, R, en, al));
-                T *st = stash + 6 * (t - t0);
+                aV.add(tri_local(pos, nVp, tc.tri[t], Di, tc.wtri[2 * t], tc.wtri[2 * t + 1], o, R, N, en, al));
+                T *st = stash + 9 * (t - t0);
 #pragma unroll
                 for (int i = 0; i < 6; ++i) st[i] = R[i];
+                st[6] = N[0]; st[7] = N[1]; st[8] = N[2];
             }
             __syncthreads();
             for (int v = tid; v < nV; v += B) {
-                T g0 = T(0), g1 = T(0), g2 = T(0);
+                T g0 = T(0), g1 = T(0), g2 = T(0), n0 = T(0), n1 = T(0), n2 = T(0);
                 const int end = tc.vt_ptr[v + 1];
                 for (int k = tc.vt_ptr[v]; k < end; ++k) {
                     const TriInc<T> inc = tc.vt[k];
                     if (inc.t < t0) continue;
                     if (inc.t >= t1) break;
-                    const T *st = stash + 6 * (inc.t - t0);
+                    const T *st = stash + 9 * (inc.t - t0);
                     g0 += st[0] * inc.g0 + st[1] * inc.g1;
                     g1 += st[2] * inc.g0 + st[3] * inc.g1;
                     g2 += st[4] * inc.g0 + st[5] * inc.g1;
+                    n0 += st[6];
+                    n1 += st[7];
+                    n2 += st[8];
                 }
                 gsh[v] += g0;
                 gsh[nVp + v] += g1;
                 gsh[2 * nVp + v] += g2;
+                gva[v] += n0;
+                gva[nVp + v] += n1;
+                gva[2 * nVp + v] += n2;
             }
             __syncthreads();
         }
@@ -348,54 +359,65 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
     // 4. volume: p = closest point with V(p) = V0 by the Gauss-Newton
     //    iteration p_{j+1} = x + lambda_j gV(p_j),
     //    lambda_j = (V0 - V(p_j) - gV(p_j).(x - p_j)) / |gV(p_j)|^2,
-    //    stopped once |V(p_j) - V0| <= tol V0 or after 8 updates.  pos holds p;
-    //    the stash holds gV (vertex by vertex, all three components).
+    //    stopped once |V(p_j) - V0| <= tol V0 or after 8 updates.  pos holds p.
+    //    gV(x) was gathered with the triangles (gva); later gradients go to the stash.
     T p[EPT];
 #pragma unroll
     for (int j = 0; j < EPT; ++j) p[j] = x[j];
     {
-        Acc<T> a1[1] = {aV};
-        block_reduce_t0<T, 1>(a1, S.red, [&](const double *s) {
-            const double V = s[0] / 6.0;
-            S.bc->d[0] = V;
-            S.bc->i[0] = fabs(V - tc.V0) <= Prec<T>::vol_tol * fabs(tc.V0);
-        });
-        T *gV = stash;
-        for (int it = 0; !S.bc->i[0]; ++it) {
-            const T q0 = pos[0], q1 = pos[nVp], q2 = pos[2 * nVp];
-            for (int v = tid; v < nV; v += B) {
-                T g[3] = {T(0), T(0), T(0)};
-                const int end = tc.vt_ptr[v + 1];
-                for (int k = tc.vt_ptr[v]; k < end; ++k) {
-                    const int bc = tc.vt[k].bc;
-                    const int vb = bc & 0xffff, vc = bc >> 16;
-                    T bx = pos[vb] - q0, by = pos[nVp + vb] - q1, bz = pos[2 * nVp + vb] - q2;
-                    T cx = pos[vc] - q0, cy = pos[nVp + vc] - q1, cz = pos[2 * nVp + vc] - q2;
-                    g[0] += by * cz - bz * cy;
-                    g[1] += bz * cx - bx * cz;
-                    g[2] += bx * cy - by * cx;
-                }
-                gV[v] = g[0] / T(6);
-                gV[nVp + v] = g[1] / T(6);
-                gV[2 * nVp + v] = g[2] / T(6);
-            }
-            __syncthreads();
-            Acc<T> a2[2];
-            a2[0].zero();
-            a2[1].zero();
+        Acc<T> a1[2];
+        a1[0] = aV;
+        a1[1].zero();
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                int e = tid + j * B, v;
-                if (e >= n3) continue;
-                elem_cv(e, nVp, v);
-                if (v >= nV) continue;
-                T gv = gV[e];
-                a2[0].add_prod(gv, gv);
-                a2[1].add_prod(gv, x[j] - p[j]);
+        for (int j = 0; j < EPT; ++j) {
+            int e = tid + j * B;
+            if (e < n3) a1[1].add_prod(gva[e], gva[e]);    // zero on padding
+        }
+        block_reduce_t0<T, 2>(a1, S.red, [&](const double *s) {
+            const double V = s[0] / 6.0;
+            S.bc->i[0] = fabs(V - tc.V0) <= Prec<T>::vol_tol * fabs(tc.V0);
+            S.bc->t[0] = T((tc.V0 - V) / s[1]);            // p_0 = x: gV.(x - p_0) = 0
+        });
+        T *gV = gva;
+        for (int it = 0; !S.bc->i[0]; ++it) {
+            if (it > 0) {
+                // gradient at p_it, vertex by vertex: sum over the one-ring of (p_b - q) x (p_c - q) / 6
+                // (overwrites gva: p_it is already formed from it)
+                const T q0 = pos[0], q1 = pos[nVp], q2 = pos[2 * nVp];
+                for (int v = tid; v < nV; v += B) {
+                    T g[3] = {T(0), T(0), T(0)};
+                    const int end = tc.vt_ptr[v + 1];
+                    for (int k = tc.vt_ptr[v]; k < end; ++k) {
+                        const int bc = tc.vt[k].bc;
+                        const int vb = bc & 0xffff, vc = bc >> 16;
+                        T bx = pos[vb] - q0, by = pos[nVp + vb] - q1, bz = pos[2 * nVp + vb] - q2;
+                        T cx = pos[vc] - q0, cy = pos[nVp + vc] - q1, cz = pos[2 * nVp + vc] - q2;
+                        g[0] += by * cz - bz * cy;
+                        g[1] += bz * cx - bx * cz;
+                        g[2] += bx * cy - by * cx;
+                    }
+                    gV[v] = g[0] / T(6);
+                    gV[nVp + v] = g[1] / T(6);
+                    gV[2 * nVp + v] = g[2] / T(6);
+                }
+                __syncthreads();
+                Acc<T> a2[2];
+                a2[0].zero();
+                a2[1].zero();
+#pragma unroll
+                for (int j = 0; j < EPT; ++j) {
+                    int e = tid + j * B, v;
+                    if (e >= n3) continue;
+                    elem_cv(e, nVp, v);
+                    if (v >= nV) continue;
+                    T gv = gV[e];
+                    a2[0].add_prod(gv, gv);
+                    a2[1].add_prod(gv, x[j] - p[j]);
+                }
+                block_reduce_t0<T, 2>(a2, S.red, [&](const double *s) {
+                    S.bc->t[0] = T((tc.V0 - S.bc->d[0] - s[1]) / s[0]);
+                });
             }
-            block_reduce_t0<T, 2>(a2, S.red, [&](const double *s) {
-                S.bc->t[0] = T((tc.V0 - S.bc->d[0] - s[1]) / s[0]);
-            });
             const T lam = S.bc->t[0];
 #pragma unroll
             for (int j = 0; j < EPT; ++j) {
@@ -426,11 +448,15 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
         elem_cv(e, nVp, v);
         if (v >= nV) continue;
         T r = x[j] - p[j];
-        en.add(T(0.5) * tc.kv * r * r);
-        al.add(tc.kv * fabs(r) * fabs(x[j]));
+        en += T(0.5) * tc.kv * r * r;
+        al += tc.kv * fabs(r) * fabs(x[j]);
         gr[j] = gsh[e] + tc.kv * r;
     }
-    Acc<T> fin[2] = {en, al};
+    Acc<T> fin[2];
+    fin[0].zero();
+    fin[1].zero();
+    fin[0].add(en);
+    fin[1].add(al);
     block_reduce_t0<T, 2>(fin, S.red, [&](const double *s) { done(s[0], 8.0 * Prec<T>::round_unit * s[1]); });
 }
 

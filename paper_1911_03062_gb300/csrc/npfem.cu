@@ -55,7 +55,8 @@ struct MeshTypeImpl {
     __nv_bfloat16 *Pinv16 = nullptr;
     double *diag = nullptr, *minv = nullptr;
     float *dhi = nullptr, *dlo = nullptr;
-    int *op = nullptr, *oj = nullptr;
+    int *op = nullptr;
+    unsigned short *oj = nullptr;
     float *ov = nullptr;
     int n_off = 0;
     // tensor-core GEMM configuration
@@ -69,7 +70,7 @@ struct MeshTypeImpl {
     void *yrel = nullptr, *delta = nullptr, *grad = nullptr, *q = nullptr, *z = nullptr;
     void *S = nullptr, *Y = nullptr, *rlo = nullptr;
     __nv_bfloat16 *q16 = nullptr;
-    double *origin = nullptr, *rho = nullptr, *alpha = nullptr, *g = nullptr, *allow = nullptr;
+    double *origin = nullptr, *rho = nullptr, *alpha = nullptr, *M = nullptr, *g = nullptr, *allow = nullptr;
     int *hcount = nullptr, *hhead = nullptr, *conv = nullptr, *fb_list = nullptr, *fb_count = nullptr;
     CUtensorMap mapQ{}, mapR{};
     int ept = 8, block = 256, stash_T = 0;
@@ -263,6 +264,7 @@ IterArgs<T> make_args(npfem_ctx *ctx, MeshTypeImpl *t) {
     a.Y = (T *)t->Y;
     a.rho = t->rho;
     a.alpha = t->alpha;
+    a.M = t->M;
     a.g = t->g;
     a.allow = t->allow;
     a.hcount = t->hcount;
@@ -388,10 +390,14 @@ void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, c
     a.conv = conv;
     a.any_active = ctx->d_any;
     a.st = ctx->d_st;
-    size_t smem = 128 * sizeof(double) + 16 + 3 * (size_t)t->nVp * sizeof(float);
+    a.n_off = t->n_off;
+    // one warp per cell, up to 8 warps per block, each warp's z in shared memory
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / (12 * (size_t)t->nVp)));
+    const size_t smem = (size_t)wpb * 3 * t->nVp * sizeof(float);
+    const int grid = std::min((rows_cells + wpb - 1) / wpb, 3 * ctx->nsm);
     prof_begin(ctx, NPFEM_K_RESIDUAL);
-    if (ctx->opt.residual_fp64) k_residual<true><<<rows_cells, 256, smem, ctx->stream>>>(a);
-    else k_residual<false><<<rows_cells, 256, smem, ctx->stream>>>(a);
+    if (ctx->opt.residual_fp64) k_residual<true><<<grid, 32 * wpb, smem, ctx->stream>>>(a);
+    else k_residual<false><<<grid, 32 * wpb, smem, ctx->stream>>>(a);
     CK(cudaGetLastError());
     prof_end(ctx);
 }
@@ -718,7 +724,7 @@ void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
 void free_cells(MeshTypeImpl *t) {
     void **bufs[] = {(void **)&t->pub_off, (void **)&t->xn, (void **)&t->vn, &t->yrel, &t->delta, &t->grad, &t->q,
                      &t->z, &t->S, &t->Y, &t->rlo, (void **)&t->q16, (void **)&t->origin, (void **)&t->rho,
-                     (void **)&t->alpha, (void **)&t->g, (void **)&t->allow, (void **)&t->hcount,
+                     (void **)&t->alpha, (void **)&t->M, (void **)&t->g, (void **)&t->allow, (void **)&t->hcount,
                      (void **)&t->hhead, (void **)&t->conv, (void **)&t->fb_list, (void **)&t->fb_count};
     for (void **b : bufs) dfree(*b);
 }
@@ -739,6 +745,7 @@ void alloc_cells(npfem_ctx *ctx, MeshTypeImpl *t, int cap) {
     t->origin = dalloc<double>(ctx, 3 * (size_t)cap);
     t->rho = dalloc<double>(ctx, m * cap);
     t->alpha = dalloc<double>(ctx, m * cap);
+    t->M = dalloc<double>(ctx, m * m * cap);
     t->g = dalloc<double>(ctx, cap);
     t->allow = dalloc<double>(ctx, cap);
     t->hcount = dalloc<int>(ctx, cap);
@@ -902,7 +909,8 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         if (mixed(ctx)) t->tc32 = upload_consts<float>(ctx, t, H, mass);
         else t->tc64 = upload_consts<double>(ctx, t, H, mass);
         std::vector<double> minv(nV), diag(nV);
-        std::vector<int> op(nV + 1, 0), oj;
+        std::vector<int> op(nV + 1, 0);
+        std::vector<unsigned short> oj;
         std::vector<float> ov;
         for (int v = 0; v < nV; ++v) {
             minv[v] = 1.0 / mass[v];
@@ -910,7 +918,7 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
             for (int u = 0; u < nV; ++u) {
                 double p = H.P[(size_t)v * nV + u];
                 if (u != v && p != 0.0) {
-                    oj.push_back(u);
+                    oj.push_back((unsigned short)u);
                     ov.push_back((float)p);
                 }
             }
@@ -937,10 +945,18 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         else t->ept = 16;
         t->block = ((n3 + t->ept - 1) / t->ept + 31) / 32 * 32;
         const size_t es = esize(ctx);
-        const size_t stash_cap = mixed(ctx) ? 16384 : 12288;
-        // the stash also holds the volume gradient (3 nVp values)
-        t->stash_T = (int)std::max<size_t>(3 * (size_t)t->nVp, std::min<size_t>(6 * (size_t)nT, stash_cap));
-        t->smem_step = smem_header_bytes() + (6 * (size_t)t->nVp + t->stash_T) * es;
+        // stash: 9 values per triangle of a chunk; as large as the shared memory left
+        // after the header and the three vectors allows (capped), and with the vectors
+        // at least the L-BFGS batch scratch ((2 m_max + 4) values per thread)
+        const size_t fixed = smem_header_bytes() + 3 * SMEM_VECS * (size_t)t->nVp * es;
+        const size_t cap = mixed(ctx) ? 16384 : 6144;
+        size_t room = (size_t)ctx->smem_optin > fixed + 1024 ? ((size_t)ctx->smem_optin - fixed - 1024) / es : 0;
+        size_t st = std::min<size_t>({9 * (size_t)nT, cap, room});
+        const size_t need = (size_t)(2 * NPFEM_MAX_HISTORY + 4) * t->block;
+        if (st + 3 * SMEM_VECS * (size_t)t->nVp < need) st = need - 3 * SMEM_VECS * (size_t)t->nVp;
+        if (st < 9) st = 9;
+        t->stash_T = (int)st;
+        t->smem_step = smem_header_bytes() + (3 * SMEM_VECS * (size_t)t->nVp + t->stash_T) * es;
         if (mixed(ctx)) {
             choose_tiles(ctx, t);
             const void *pb = bf16(ctx) ? (const void *)t->Pinv16 : (const void *)t->Pinv32;

@@ -11,6 +11,7 @@
 #pragma once
 
 #include "local.cuh"
+#include "npfem.h"
 
 namespace npfem {
 
@@ -29,6 +30,7 @@ struct IterArgs {
     __nv_bfloat16 *q_bf16;        // GEMM operand copy of q (BF16 form), or null
     T *S, *Y;                     // history [cell][m][3][nVp]
     double *rho, *alpha;          // [cell][m]
+    double *M;                    // [cell][m][m]: M[i][j] = s_i . y_j for pair i older than pair j
     double *g;                    // [cell] energy at the current iterate
     double *allow;                // [cell] rounding allowance of g (FP32 local step)
     int *hcount, *hhead;          // [cell] ring state
@@ -74,10 +76,36 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
     }
 }
 
+// Sums over the block of n per-thread partials at once (the dot products of
+// one L-BFGS pass): partials are written transposed to shared memory, warp w
+// reduces values w, w + nwarps, ... in float-float (FP64 in the FP64 path)
+// in a fixed order, and out[i] (FP64, shared memory) holds the totals for
+// every thread on return.  scratch: NMAX * blockDim.x values of T (the
+// per-cell kernels use their local-step buffers, idle outside local_eval).
+template <typename T, int NMAX>
+__device__ __forceinline__ void block_sum_many(const T (&part)[NMAX], int n1, int n2, T *scratch, double *out) {
+    // values [0, n1) and [n2, NMAX) are summed; the others are skipped
+    const int B = blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (B + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i)
+        if (i < n1 || i >= n2) scratch[i * B + threadIdx.x] = part[i];
+    __syncthreads();
+    for (int i = warp; i < NMAX; i += nw) {
+        if (i >= n1 && i < n2) continue;
+        Acc<T> acc;
+        acc.zero();
+        for (int k = lane; k < B; k += 32) acc.add(scratch[i * B + k]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc.merge_shfl(0xffffffffu, off);
+        if (lane == 0) out[i] = acc.get();
+    }
+    __syncthreads();
+}
+
 // Start of a step: y, origin (centroid of y), y_rel, delta = 0, history
 // cleared, g and grad g at x^0 = y, and q = grad g (the first apply's RHS).
 template <typename T, int EPT, int MAXB>
-__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 3 : 1) k_predict(IterArgs<T> a) {
+__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) : 1) k_predict(IterArgs<T> a) {
     const Smem<T> S = smem_layout<T>(a.tc.nVp);
     const int nVp = a.tc.nVp, n3 = 3 * nVp;
     for (int cell = blockIdx.x; cell < a.ncells; cell += gridDim.x) {
@@ -145,36 +173,69 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 3 : 1) k_predict(IterArgs<
 //   last        : x_{n+1} = y + delta, v_{n+1} = (x_{n+1} - x_n)/h  (Eq. vel)
 //   otherwise   : first loop  q = grad; for i newest -> oldest: alpha_i = rho_i s_i.q;
 //                 q -= alpha_i y_i  -> the next global step's RHS.
-// Scalars (dots, coefficients, the Armijo and curvature tests) are formed by
-// thread 0 in FP64 and broadcast through shared memory.
+// Both loops are evaluated in their dot-product form: with r_{i-1} and q_i
+// written as combinations of z (or grad) and the history vectors,
+//   y_i . r_{i-1} = y_i . z + sum_{j older than i} (alpha_j - beta_j) s_j . y_i
+//   s_i . q_i     = s_i . grad - sum_{j newer than i} alpha_j s_i . y_j,
+// so each loop needs one batched reduction (y_i . z, resp. s_i . grad) plus the
+// stored products M[i][j] = s_i . y_j (i older than j), which a new pair adds
+// in the same batch.  Scalars are formed by thread 0 in FP64 and broadcast.
+constexpr int MH = NPFEM_MAX_HISTORY;
+
 template <typename T, int EPT, int MAXB>
-__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 3 : 1) k_iterate(IterArgs<T> a, const int *list,
+__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) : 1) k_iterate(IterArgs<T> a, const int *list,
                                                                       const int *list_count) {
     const Smem<T> S = smem_layout<T>(a.tc.nVp);
     const int nVp = a.tc.nVp, n3 = 3 * nVp, m = a.m;
     const int nitems = list ? *list_count : a.ncells;
+    double *out = S.red;                       // batched sums (up to 2 MH + 4)
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int cell = list ? list[item] : item;
         const long long base = (long long)cell * n3;
         T *Sh = a.S + (long long)cell * m * n3;
         T *Yh = a.Y + (long long)cell * m * n3;
         double *rho = a.rho + (long long)cell * m, *alp = a.alpha + (long long)cell * m;
-        int cnt = a.hcount[cell], head = a.hhead[cell];
+        double *Mc = a.M + (long long)cell * m * m;
+        const int cnt = a.hcount[cell], head = a.hhead[cell];
+        auto slot = [&](int l) { return (head - cnt + l + 2 * m) % m; };   // l = 0 oldest
         T r[EPT], d[EPT], gr[EPT], dl[EPT];
         load_vec<T, EPT>(a.z + base, r, n3);
-        for (int l = cnt - 1; l >= 0; --l) {
-            const int i = ((head - 1 - l) % m + m) % m;
-            T yi[EPT], si[EPT];
-            load_vec<T, EPT>(Yh + (long long)i * n3, yi, n3);
-            load_vec<T, EPT>(Sh + (long long)i * n3, si, n3);
-            Acc<T> ac[1];
-            ac[0].zero();
+        if (cnt > 0) {
+            // second loop, pass A: y_i . z for all pairs
+            T pa[MH];
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) ac[0].add_prod(yi[j], r[j]);
-            block_reduce_t0<T, 1>(ac, S.red, [&](const double *s) { S.bc->t[0] = T(alp[i] - rho[i] * s[0]); });
-            const T coef = S.bc->t[0];
+            for (int l = 0; l < MH; ++l) {
+                pa[l] = T(0);
+                if (l < cnt) {
+                    T yi[EPT];
+                    load_vec<T, EPT>(Yh + (long long)slot(l) * n3, yi, n3);
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) r[j] += si[j] * coef;
+                    for (int j = 0; j < EPT; ++j) pa[l] += yi[j] * r[j];
+                }
+            }
+            block_sum_many<T, MH>(pa, cnt, MH, S.pos, out);
+            if (threadIdx.x == 0) {
+                double coef[MH];
+                for (int l = 0; l < cnt; ++l) {
+                    const int i = slot(l);
+                    double dot = out[l];
+                    for (int k = 0; k < l; ++k) dot += coef[k] * Mc[slot(k) * m + i];
+                    coef[l] = alp[i] - rho[i] * dot;
+                    S.bc->t[l] = T(coef[l]);
+                }
+            }
+            __syncthreads();
+            // pass B: r = z + sum_l coef_l s_l
+#pragma unroll
+            for (int l = 0; l < MH; ++l) {
+                if (l < cnt) {
+                    T si[EPT];
+                    load_vec<T, EPT>(Sh + (long long)slot(l) * n3, si, n3);
+                    const T cf = S.bc->t[l];
+#pragma unroll
+                    for (int j = 0; j < EPT; ++j) r[j] += cf * si[j];
+                }
+            }
         }
 #pragma unroll
         for (int j = 0; j < EPT; ++j) d[j] = -r[j];
@@ -228,42 +289,16 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 3 : 1) k_iterate(IterArgs<
             if (S.bc->i[3]) break;
             alpha = S.bc->t[2];
         }
-        // history pair
-        T sv[EPT], yv[EPT];
-        Acc<T> h3[3];
-        h3[0].zero(); h3[1].zero(); h3[2].zero();
-#pragma unroll
-        for (int j = 0; j < EPT; ++j) {
-            sv[j] = dt[j] - dl[j];
-            yv[j] = gt[j] - gr[j];
-            h3[0].add_prod(sv[j], yv[j]);
-            h3[1].add_prod(sv[j], sv[j]);
-            h3[2].add_prod(yv[j], yv[j]);
-        }
-        block_reduce_t0<T, 3>(h3, S.red, [&](const double *hs) {
-            const int keep = m > 0 && hs[0] > 1e-12 * sqrt(hs[1]) * sqrt(hs[2]);
-            S.bc->i[4] = keep;
-            if (keep) rho[head] = 1.0 / hs[0];
-            const double gtv = S.bc->d[3];
-            a.g[cell] = gtv;
-            a.allow[cell] = S.bc->d[4];
-            if (S.bc->i[2]) atomicAdd(&a.st->backtracks, (unsigned long long)S.bc->i[2]);
-            if (!isfinite(gtv)) dev_raise(a.st, DEV_ENONFINITE, cell);
-            if (a.last) atomicAdd(&a.st->energy_sum, gtv);
-        });
-        if (S.bc->i[4]) {
-            store_vec<T, EPT>(Sh + (long long)head * n3, sv, n3);
-            store_vec<T, EPT>(Yh + (long long)head * n3, yv, n3);
-            head = (head + 1) % m;
-            if (cnt < m) ++cnt;
-        }
         store_vec<T, EPT>(a.delta + base, dt, n3);
         store_vec<T, EPT>(a.grad + base, gt, n3);
-        if (threadIdx.x == 0) {
-            a.hcount[cell] = cnt;
-            a.hhead[cell] = head;
-        }
         if (a.last) {
+            if (threadIdx.x == 0) {
+                const double gtv = S.bc->d[3];
+                a.g[cell] = gtv;
+                if (S.bc->i[2]) atomicAdd(&a.st->backtracks, (unsigned long long)S.bc->i[2]);
+                if (!isfinite(gtv)) dev_raise(a.st, DEV_ENONFINITE, cell);
+                atomicAdd(&a.st->energy_sum, gtv);
+            }
             double y[EPT], xo[EPT];
             predictor64<T, EPT>(a, cell, y, xo);
 #pragma unroll
@@ -274,35 +309,115 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? 3 : 1) k_iterate(IterArgs<
                 a.xn[base + e] = x;
                 a.vn[base + e] = (x - xo[j]) / a.h;
             }
-        } else {
-            T qv[EPT];
+            __syncthreads();
+            continue;
+        }
+        // history pair and the first loop's dots (pass C): for every old pair
+        // s_l . grad_new and s_l . y_new; for the new pair s.y, s.s, y.y, s.grad_new
+        T sv[EPT], yv[EPT];
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) qv[j] = gt[j];
-            for (int l = 0; l < cnt; ++l) {
-                const int i = ((head - 1 - l) % m + m) % m;
-                T si[EPT], yi[EPT];
-                load_vec<T, EPT>(Sh + (long long)i * n3, si, n3);
-                load_vec<T, EPT>(Yh + (long long)i * n3, yi, n3);
-                Acc<T> ac[1];
-                ac[0].zero();
+        for (int j = 0; j < EPT; ++j) {
+            sv[j] = dt[j] - dl[j];
+            yv[j] = gt[j] - gr[j];
+        }
+        T pc[2 * MH + 4];
 #pragma unroll
-                for (int j = 0; j < EPT; ++j) ac[0].add_prod(si[j], qv[j]);
-                block_reduce_t0<T, 1>(ac, S.red, [&](const double *s) {
-                    const double al = rho[i] * s[0];
-                    alp[i] = al;
-                    S.bc->t[0] = T(al);
-                });
-                const T ca = S.bc->t[0];
+        for (int l = 0; l < MH; ++l) {
+            pc[2 * l] = T(0);
+            pc[2 * l + 1] = T(0);
+            if (l < cnt) {
+                T si[EPT];
+                load_vec<T, EPT>(Sh + (long long)slot(l) * n3, si, n3);
+#pragma unroll
+                for (int j = 0; j < EPT; ++j) {
+                    pc[2 * l] += si[j] * gt[j];
+                    pc[2 * l + 1] += si[j] * yv[j];
+                }
+            }
+        }
+        T nsy = T(0), nss = T(0), nyy = T(0), nsg = T(0);
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) {
+            nsy += sv[j] * yv[j];
+            nss += sv[j] * sv[j];
+            nyy += yv[j] * yv[j];
+            nsg += sv[j] * gt[j];
+        }
+        pc[2 * MH] = nsy;
+        pc[2 * MH + 1] = nss;
+        pc[2 * MH + 2] = nyy;
+        pc[2 * MH + 3] = nsg;
+        block_sum_many<T, 2 * MH + 4>(pc, 2 * cnt, 2 * MH, S.pos, out);
+        if (threadIdx.x == 0) {
+            const double sy = out[2 * MH], ss = out[2 * MH + 1], yy = out[2 * MH + 2], sg = out[2 * MH + 3];
+            const int keep = m > 0 && sy > 1e-12 * sqrt(ss) * sqrt(yy);
+            const double gtv = S.bc->d[3];
+            a.g[cell] = gtv;
+            a.allow[cell] = S.bc->d[4];
+            if (S.bc->i[2]) atomicAdd(&a.st->backtracks, (unsigned long long)S.bc->i[2]);
+            if (!isfinite(gtv)) dev_raise(a.st, DEV_ENONFINITE, cell);
+            // the history after this iteration, oldest first: old pairs (minus the
+            // evicted oldest when full) then the new one
+            int first_old = 0, ncnt = cnt;
+            if (keep) {
+                if (cnt == m) first_old = 1; else ncnt = cnt + 1;
+                const int ns = head;                         // the new pair's slot
+                rho[ns] = 1.0 / sy;
+                for (int l = first_old; l < cnt; ++l) Mc[slot(l) * m + ns] = out[2 * l + 1];
+            }
+            // alpha_i = rho_i (s_i . grad - sum_{j newer} alpha_j s_i . y_j), newest first
+            double al[MH + 1];
+            const int nold = cnt - first_old;
+            if (keep) al[nold] = rho[head] * sg;
+            for (int l = cnt - 1; l >= first_old; --l) {
+                const int i = slot(l), p = l - first_old;
+                double dot = out[2 * l];
+                for (int k = p + 1; k < nold; ++k) dot -= al[k] * Mc[i * m + slot(k + first_old)];
+                if (keep) dot -= al[nold] * out[2 * l + 1];
+                al[p] = rho[i] * dot;
+            }
+            for (int p = 0; p < nold; ++p) {
+                alp[slot(p + first_old)] = al[p];
+                S.bc->t[p] = T(al[p]);
+            }
+            if (keep) {
+                alp[head] = al[nold];
+                S.bc->t[nold] = T(al[nold]);
+            }
+            S.bc->i[4] = keep;
+            S.bc->i[5] = first_old;
+            a.hcount[cell] = ncnt;
+            a.hhead[cell] = keep ? (head + 1) % m : head;
+        }
+        __syncthreads();
+        const int keep = S.bc->i[4], first_old = S.bc->i[5], nold = cnt - first_old;
+        // pass D: q = grad - sum alpha_l y_l over the new history
+        T qv[EPT];
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) qv[j] = gt[j];
+#pragma unroll
+        for (int l = 0; l < MH; ++l) {
+            if (l >= first_old && l < cnt) {
+                T yi[EPT];
+                load_vec<T, EPT>(Yh + (long long)slot(l) * n3, yi, n3);
+                const T ca = S.bc->t[l - first_old];
 #pragma unroll
                 for (int j = 0; j < EPT; ++j) qv[j] -= ca * yi[j];
             }
-            store_vec<T, EPT>(a.q + base, qv, n3);
-            if (a.q_bf16) {
+        }
+        if (keep) {
+            const T ca = S.bc->t[nold];
 #pragma unroll
-                for (int j = 0; j < EPT; ++j) {
-                    int e = threadIdx.x + j * blockDim.x;
-                    if (e < n3) a.q_bf16[base + e] = __float2bfloat16_rn((float)qv[j]);
-                }
+            for (int j = 0; j < EPT; ++j) qv[j] -= ca * yv[j];
+            store_vec<T, EPT>(Sh + (long long)head * n3, sv, n3);
+            store_vec<T, EPT>(Yh + (long long)head * n3, yv, n3);
+        }
+        store_vec<T, EPT>(a.q + base, qv, n3);
+        if (a.q_bf16) {
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                int e = threadIdx.x + j * blockDim.x;
+                if (e < n3) a.q_bf16[base + e] = __float2bfloat16_rn((float)qv[j]);
             }
         }
         __syncthreads();
@@ -351,11 +466,12 @@ __global__ void k_fallback_apply(int nV, int nVp, const T *__restrict__ Pinv, co
 // their rows untouched).  final_pass: norms only, for the statistics of
 // cells that never converged.
 struct ResidArgs {
-    int ncells, nV, nVp, first, final_pass;
+    int ncells, nV, nVp, first, final_pass, n_off, stage_csr;
     double tol;
     const double *diag;      // [nV] diag(P)
     const float *dhi, *dlo;  // [nV] diag(P) = dhi + dlo (+ O(2^-48))
-    const int *op, *oj;      // off-diagonal CSR
+    const int *op;           // [nV + 1] off-diagonal CSR row starts
+    const unsigned short *oj;
     const float *ov;
     const float *q, *z;
     __nv_bfloat16 *r_bf16;   // BF16 form
@@ -365,54 +481,84 @@ struct ResidArgs {
     DevStatus *st;
 };
 
+// One warp per cell, no block-wide barriers: the warp stages its cell's z in
+// shared memory (float4 loads), then each lane evaluates all components of
+// vertices lane, lane + 32, ... from one pass over the vertex's CSR row (the
+// CSR of the type, shared by all cells, stays in L1), and the warp reduces
+// the two norms by shuffles.
 template <bool FP64R>
 __global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *red = reinterpret_cast<double *>(smem_raw);
-    float *zs = reinterpret_cast<float *>(smem_raw + 128 * sizeof(double) + 16);
-    const int nVp = a.nVp, n3 = 3 * nVp;
-    for (int cell = blockIdx.x; cell < a.ncells; cell += gridDim.x) {
+    const int nVp = a.nVp, n3 = 3 * nVp, nV = a.nV;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *zw = reinterpret_cast<float *>(smem_raw) + (size_t)warp * n3;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int cell = blockIdx.x * (blockDim.x >> 5) + warp; cell < a.ncells; cell += nwarps) {
         if (!a.first && a.conv[cell]) continue;
         const long long base = (long long)cell * n3;
-        for (int e = threadIdx.x; e < n3; e += blockDim.x) zs[e] = a.z[base + e];
-        __syncthreads();
+        {
+            const float4 *src = reinterpret_cast<const float4 *>(a.z + base);
+            float4 *dst = reinterpret_cast<float4 *>(zw);
+            for (int i = lane; i < n3 / 4; i += 32) dst[i] = __ldg(src + i);
+        }
+        __syncwarp();
         Acc<float> s[2];
         s[0].zero(); s[1].zero();
-        for (int e = threadIdx.x; e < n3; e += blockDim.x) {
-            int v, c = elem_cv(e, nVp, v);
-            float r = 0.f;
-            if (v < a.nV) {
-                const float qv = a.q[base + e], zv = zs[e];
-                float off = 0.f;
-                const float *zc = zs + c * nVp;
-                for (int k = a.op[v]; k < a.op[v + 1]; ++k) off = fmaf(a.ov[k], zc[a.oj[k]], off);
-                if (FP64R) {
-                    r = (float)(fma(-a.diag[v], (double)zv, (double)qv) - (double)off);
-                } else {
-                    r = __fmaf_rn(-a.dhi[v], zv, qv);
-                    r = __fmaf_rn(-a.dlo[v], zv, r);
-                    r = __fsub_rn(r, off);
+        for (int v = lane; v < nVp; v += 32) {
+            float r[3] = {0.f, 0.f, 0.f};
+            if (v < nV) {
+                float off[3] = {0.f, 0.f, 0.f};
+                const int kend = __ldg(a.op + v + 1);
+                for (int k = __ldg(a.op + v); k < kend; ++k) {
+                    const int u = __ldg(a.oj + k);
+                    const float w = __ldg(a.ov + k);
+                    off[0] = fmaf(w, zw[u], off[0]);
+                    off[1] = fmaf(w, zw[nVp + u], off[1]);
+                    off[2] = fmaf(w, zw[2 * nVp + u], off[2]);
                 }
-                s[0].add_prod(r, r);
-                s[1].add_prod(qv, qv);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float qv = __ldg(a.q + base + c * nVp + v), zv = zw[c * nVp + v];
+                    if (FP64R) {
+                        r[c] = (float)(fma(-a.diag[v], (double)zv, (double)qv) - (double)off[c]);
+                    } else {
+                        float t = __fmaf_rn(-__ldg(a.dhi + v), zv, qv);
+                        t = __fmaf_rn(-__ldg(a.dlo + v), zv, t);
+                        r[c] = __fsub_rn(t, off[c]);
+                    }
+                    s[0].add(r[c] * r[c]);
+                    s[1].add(qv * qv);
+                }
             }
             if (!a.final_pass) {
-                if (a.r_bf16) a.r_bf16[base + e] = __float2bfloat16_rn(r);
-                else a.r_f32[base + e] = r;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (a.r_bf16) a.r_bf16[base + c * nVp + v] = __float2bfloat16_rn(r[c]);
+                    else a.r_f32[base + c * nVp + v] = r[c];
+                }
             }
         }
-        block_reduce_t0<float, 2>(s, red, [&](const double *nr) {
-            const bool ok = nr[0] <= a.tol * a.tol * nr[1];
-            const float ratio = nr[1] > 0 ? (float)sqrt(nr[0] / nr[1]) : 0.f;
-            if (a.final_pass || ok) atomicMax(&a.st->max_resid_bits, __float_as_uint(ratio));
-            if (!a.final_pass) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            s[0].merge_shfl(0xffffffffu, off);
+            s[1].merge_shfl(0xffffffffu, off);
+        }
+        if (lane == 0) {
+            const double nr0 = s[0].get(), nr1 = s[1].get();
+            const bool ok = nr0 <= a.tol * a.tol * nr1;
+            const float ratio = nr1 > 0 ? (float)sqrt(nr0 / nr1) : 0.f;
+            if (a.final_pass) {
+                atomicMax(&a.st->max_resid_bits, __float_as_uint(ratio));
+            } else {
+                if (ok) atomicMax(&a.st->max_resid_bits, __float_as_uint(ratio));
                 a.conv[cell] = ok ? 1 : 0;
                 if (!ok) {
                     atomicOr(a.any_active, 1);
                     atomicAdd(&a.st->refine_sweeps, 1ull);
                 }
             }
-        });
+        }
+        __syncwarp();
     }
 }
 

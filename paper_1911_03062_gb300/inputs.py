@@ -235,7 +235,7 @@ def materialise(group: Group, chunk: int = 2048) -> Group:
 
 def subset(group: Group, idx) -> Group:
     """The cells ``idx`` of a materialised group (same draws)."""
-    idx = np.asarray(idx)
+    idx = np.asarray(idx, dtype=np.int64)
     g = Group(group.mtype, len(idx), group.seed, group.amp, group.shear, group.box)
     g.x0, g.v0, g.f_ext = group.x0[idx].copy(), group.v0[idx].copy(), group.f_ext[idx].copy()
     return g
