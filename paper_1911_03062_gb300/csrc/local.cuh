@@ -42,7 +42,14 @@ struct TypeConst {
     const T *mh2;           // nV: m_v / h^2
     double V0;              // rest volume
     T kb, kv;               // bending and volume weights
+    // slot-major padded copies of the incidence lists (slot q of vertex v at
+    // [q * nV + v]; unused slots carry zero weights), for one-round gathers:
+    int pad_t, pad_h;       // slots per vertex (0 = not available)
+    const int4 *vt_pad;     // (t, G0, G1, 1) as bits; padding (0, 0, 0, 0)
+    const int2 *vh_pad;     // (h, c) as bits; padding (0, 0)
 };
+
+constexpr int PAD_T = 8, PAD_H = 16;
 
 __device__ __forceinline__ int elem_cv(int e, int nVp, int &v) {
     int c = (e >= nVp) + (e >= 2 * nVp);
@@ -300,6 +307,40 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                 st[6] = N[0]; st[7] = N[1]; st[8] = N[2];
             }
             __syncthreads();
+            if (sizeof(T) == 4 && tc.pad_t && t0 == 0 && t1 == tc.nT) {
+                // whole mesh in one chunk: all slots of a vertex loaded at once (coalesced)
+                for (int v = tid; v < nV; v += B) {
+                    T g0 = T(0), g1 = T(0), g2 = T(0), n0 = T(0), n1 = T(0), n2 = T(0);
+#pragma unroll
+                    for (int q0 = 0; q0 < PAD_T; q0 += 4) {
+                        if (q0 >= tc.pad_t) break;
+                        int4 inc[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            inc[q] = q0 + q < tc.pad_t ? __ldg(tc.vt_pad + (q0 + q) * nV + v) : make_int4(0, 0, 0, 0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const T *st = stash + 9 * inc[q].x;
+                            const T G0 = __int_as_float(inc[q].y), G1 = __int_as_float(inc[q].z);
+                            const T wn = __int_as_float(inc[q].w);
+                            g0 += st[0] * G0 + st[1] * G1;
+                            g1 += st[2] * G0 + st[3] * G1;
+                            g2 += st[4] * G0 + st[5] * G1;
+                            n0 += wn * st[6];
+                            n1 += wn * st[7];
+                            n2 += wn * st[8];
+                        }
+                    }
+                    gsh[v] += g0;
+                    gsh[nVp + v] += g1;
+                    gsh[2 * nVp + v] += g2;
+                    gva[v] += n0;
+                    gva[nVp + v] += n1;
+                    gva[2 * nVp + v] += n2;
+                }
+                __syncthreads();
+                continue;
+            }
             for (int v = tid; v < nV; v += B) {
                 T g0 = T(0), g1 = T(0), g2 = T(0), n0 = T(0), n1 = T(0), n2 = T(0);
                 const int end = tc.vt_ptr[v + 1];
@@ -337,6 +378,32 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                 st[0] = R[0]; st[1] = R[1]; st[2] = R[2];
             }
             __syncthreads();
+            if (sizeof(T) == 4 && tc.pad_h && h0 == 0 && h1 == tc.nH) {
+                for (int v = tid; v < nV; v += B) {
+                    T g0 = T(0), g1 = T(0), g2 = T(0);
+#pragma unroll
+                    for (int q0 = 0; q0 < PAD_H; q0 += 4) {
+                        if (q0 >= tc.pad_h) break;
+                        int2 inc[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            inc[q] = q0 + q < tc.pad_h ? __ldg(tc.vh_pad + (q0 + q) * nV + v) : make_int2(0, 0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const T *st = stash + 3 * inc[q].x;
+                            const T c = __int_as_float(inc[q].y);
+                            g0 += c * st[0];
+                            g1 += c * st[1];
+                            g2 += c * st[2];
+                        }
+                    }
+                    gsh[v] += g0;
+                    gsh[nVp + v] += g1;
+                    gsh[2 * nVp + v] += g2;
+                }
+                __syncthreads();
+                continue;
+            }
             for (int v = tid; v < nV; v += B) {
                 T g0 = T(0), g1 = T(0), g2 = T(0);
                 const int end = tc.vh_ptr[v + 1];

@@ -667,6 +667,40 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
         vh[k].h = H.vh_inc[k] >> 2;
         vh[k].c = (T)H.vh_c[k];
     }
+    // slot-major padded incidence tables (FP32 path): a vertex's whole one-ring in one round of loads
+    int maxt = 0, maxh = 0;
+    for (int v = 0; v < t->nV; ++v) {
+        maxt = std::max(maxt, H.vt_ptr[v + 1] - H.vt_ptr[v]);
+        maxh = std::max(maxh, H.vh_ptr[v + 1] - H.vh_ptr[v]);
+    }
+    c.pad_t = (sizeof(T) == 4 && maxt <= PAD_T) ? maxt : 0;
+    c.pad_h = (sizeof(T) == 4 && maxh <= PAD_H) ? maxh : 0;
+    if (c.pad_t) {
+        std::vector<int4> vp((size_t)c.pad_t * t->nV, make_int4(0, 0, 0, 0));
+        for (int v = 0; v < t->nV; ++v)
+            for (int k = H.vt_ptr[v], q = 0; k < H.vt_ptr[v + 1]; ++k, ++q) {
+                float g0 = (float)H.vt_g[2 * k], g1 = (float)H.vt_g[2 * k + 1], one = 1.0f;
+                int4 e;
+                e.x = H.vt_inc[k] >> 2;
+                std::memcpy(&e.y, &g0, 4);
+                std::memcpy(&e.z, &g1, 4);
+                std::memcpy(&e.w, &one, 4);
+                vp[(size_t)q * t->nV + v] = e;
+            }
+        c.vt_pad = upload(ctx, vp, t->owned);
+    }
+    if (c.pad_h) {
+        std::vector<int2> hp((size_t)c.pad_h * t->nV, make_int2(0, 0));
+        for (int v = 0; v < t->nV; ++v)
+            for (int k = H.vh_ptr[v], q = 0; k < H.vh_ptr[v + 1]; ++k, ++q) {
+                float cc = (float)H.vh_c[k];
+                int2 e;
+                e.x = H.vh_inc[k] >> 2;
+                std::memcpy(&e.y, &cc, 4);
+                hp[(size_t)q * t->nV + v] = e;
+            }
+        c.vh_pad = upload(ctx, hp, t->owned);
+    }
     c.vt_ptr = upload(ctx, H.vt_ptr, t->owned);
     c.vt = upload(ctx, vt, t->owned);
     c.vh_ptr = upload(ctx, H.vh_ptr, t->owned);

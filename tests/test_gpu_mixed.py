@@ -120,3 +120,23 @@ def test_sampled_cells_at_50k_bf16():
     xo, _ = run_oracle(groups, 1, sample=sample)
     assert rel_pos_err(xg, xo, groups) <= TOL_MIXED
     assert st["max_refine_residual"] <= 1e-6
+
+
+def test_heterogeneous_twelve_types_bf16():
+    # the 12-type batch (162/642/2562-vertex meshes x k_strain {0.5,1,2,10}, dt
+    # {5e-4,1e-3}), 2 cells per type, BF16 apply + refinement, vs the oracle
+    groups = [I.materialise(g) for g in I.workload_groups("hetero20k", scale=0.0012)]
+    assert len(groups) == 12 and {g.mtype.nV for g in groups} == {162, 642, 2562}
+    xg, _, st = run_gpu(groups, 2, precision="bf16")
+    xo, _ = run_oracle(groups, 2)
+    assert rel_pos_err(xg, xo, groups) <= TOL_MIXED
+    assert st["max_refine_residual"] <= 1e-6
+
+
+def test_sampled_cells_rbc10k_plt1500_tf32():
+    # the 10000 RBC + 1500 platelet workload with the TF32 apply, 1 step, sampled cells
+    groups = [I.materialise(g) for g in I.workload_groups("rbc10k_plt1500")]
+    xg, _, st = run_gpu(groups, 1, precision="tf32")
+    xo, _ = run_oracle(groups, 1, sample=[[0, 5000, 9999], [0, 1499]])
+    assert rel_pos_err(xg, xo, groups) <= TOL_MIXED
+    assert st["max_refine_residual"] <= 1e-6
