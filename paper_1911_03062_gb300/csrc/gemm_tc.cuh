@@ -26,7 +26,7 @@ namespace tc {
 
 constexpr int BM = 128;          // rows of Q per tile (= TMEM lanes)
 constexpr int KB_BYTES = 128;    // bytes of K per stage row (one 128B swizzle atom)
-constexpr long long WAIT_LIMIT = 1ll << 24;
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -53,10 +53,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: false after WAIT_NS of wall time (the longest legitimate wait
+// in these kernels is one tile's work, microseconds).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (long long i = 0; i < WAIT_LIMIT; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > WAIT_NS) return false;
+    }
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {

@@ -19,6 +19,8 @@
 
 #include "npfem.h"
 #include "npfem_internal.h"
+#include <fstream>
+#include <sstream>
 
 using namespace npfem;
 
@@ -316,10 +318,11 @@ void run_iterate(npfem_ctx *ctx, MeshTypeImpl *t, int last, bool fallback) {
     else DISPATCH_EPT(double, run_iterate_t, ctx, t, last, fallback);
 }
 
-// --- global step: z = P^{-1} q for all rows of a type
-size_t gemm_smem(const MeshTypeImpl *t) {
-    return 1024 + (size_t)t->stages * (tc::BM + t->n_tile) * tc::KB_BYTES + (2 * t->stages + 2) * 8;
+// --- global step: z = P^{-1} q for the stacked rows of every type (one grouped launch)
+size_t grouped_smem(int stages, int max_ntile) {
+    return 1024 + (size_t)stages * (tc::BM + max_ntile) * tc::KB_BYTES + (2 * stages + 4) * 8 + 16;
 }
+size_t gemm_smem(const MeshTypeImpl *t) { return grouped_smem(t->stages, t->n_tile); }
 
 // Kernel attributes are set at set-up time (never inside a stream capture),
 // to the device's opt-in maximum so that every type's request fits.
@@ -335,8 +338,8 @@ void set_kernel_attrs(npfem_ctx *ctx) {
         all(k_predict<float, 4, 256>); all(k_predict<float, 8, 256>); all(k_predict<float, 16, 512>);
         all(k_iterate<float, 4, 256>); all(k_iterate<float, 8, 256>); all(k_iterate<float, 16, 512>);
         all(k_fallback_apply<float>);
-        all(tc::k_gemm_tc<false>);
-        all(tc::k_gemm_tc<true>);
+        all(tc::k_gemm_grouped<false>);
+        all(tc::k_gemm_grouped<true>);
     } else {
         all(k_predict<double, 4, 256>); all(k_predict<double, 8, 256>); all(k_predict<double, 16, 512>);
         all(k_iterate<double, 4, 256>); all(k_iterate<double, 8, 256>); all(k_iterate<double, 16, 512>);
@@ -347,25 +350,61 @@ void set_kernel_attrs(npfem_ctx *ctx) {
     ctx->smem_optin = mx;
 }
 
+struct GemmItem {
+    const MeshTypeImpl *t;
+    const CUtensorMap *mapQ;
+    int rows;
+    float *Z;
+    const int *conv;
+};
+
+// One persistent launch (per MAXG items) over every item's (row tile, N tile) units.
+void gemm_group(npfem_ctx *ctx, const std::vector<GemmItem> &items, int accumulate) {
+    for (size_t i0 = 0; i0 < items.size(); i0 += tc::MAXG) {
+        const size_t i1 = std::min(items.size(), i0 + tc::MAXG);
+        tc::GroupArgs g{};
+        tc::GroupMaps maps;
+        int max_nt = 16, stages = 0, best_rows = -1, units = 0;
+        for (size_t i = i0; i < i1; ++i) {
+            const GemmItem &it = items[i];
+            tc::GroupProblem &P = g.pr[g.nprob];
+            P.rows = it.rows;
+            P.nV = it.t->nV;
+            P.nVp = it.t->nVp;
+            P.n_tile = it.t->n_tile;
+            P.n_ntiles = (it.t->nV + it.t->n_tile - 1) / it.t->n_tile;
+            P.m_tiles = (it.rows + tc::BM - 1) / tc::BM;
+            P.kblocks = (it.t->nV * (bf16(ctx) ? 2 : 4) + tc::KB_BYTES - 1) / tc::KB_BYTES;
+            P.unit_begin = units;
+            P.Z = it.Z;
+            P.conv = it.conv;
+            units += P.m_tiles * P.n_ntiles;
+            maps.q[g.nprob] = *it.mapQ;
+            maps.p[g.nprob] = it.t->mapP;
+            max_nt = std::max(max_nt, it.t->n_tile);
+            if (it.rows > best_rows) { best_rows = it.rows; stages = it.t->stages; }
+            ++g.nprob;
+        }
+        if (!units) continue;
+        while (stages > 2 && grouped_smem(stages, max_nt) + 2048 > (size_t)ctx->smem_optin) --stages;
+        g.total_units = units;
+        g.stages = stages;
+        g.accumulate = accumulate;
+        g.stage_bytes_b = max_nt * tc::KB_BYTES;
+        g.st = ctx->d_st;
+        const int grid = std::min(units, ctx->nsm);
+        const size_t smem = grouped_smem(stages, max_nt);
+        prof_begin(ctx, accumulate ? NPFEM_K_GEMM_REFINE : NPFEM_K_GEMM);
+        if (bf16(ctx)) tc::k_gemm_grouped<false><<<grid, 192, smem, ctx->stream>>>(maps, g);
+        else tc::k_gemm_grouped<true><<<grid, 192, smem, ctx->stream>>>(maps, g);
+        CK(cudaGetLastError());
+        prof_end(ctx);
+    }
+}
+
 void gemm_tc(npfem_ctx *ctx, MeshTypeImpl *t, const CUtensorMap &mapQ, int rows, float *Z, int accumulate,
              const int *conv) {
-    tc::GemmArgs g{};
-    g.rows = rows;
-    g.nV = t->nV;
-    g.nVp = t->nVp;
-    g.n_tile = t->n_tile;
-    g.stages = t->stages;
-    g.accumulate = accumulate;
-    g.conv = conv;
-    g.Z = Z;
-    g.st = ctx->d_st;
-    dim3 grid((t->nV + t->n_tile - 1) / t->n_tile, (rows + tc::BM - 1) / tc::BM);
-    const size_t smem = gemm_smem(t);
-    prof_begin(ctx, accumulate ? NPFEM_K_GEMM_REFINE : NPFEM_K_GEMM);
-    if (bf16(ctx)) tc::k_gemm_tc<false><<<grid, 128, smem, ctx->stream>>>(mapQ, t->mapP, g);
-    else tc::k_gemm_tc<true><<<grid, 128, smem, ctx->stream>>>(mapQ, t->mapP, g);
-    CK(cudaGetLastError());
-    prof_end(ctx);
+    gemm_group(ctx, {GemmItem{t, &mapQ, rows, Z, conv}}, accumulate);
 }
 
 void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, const float *z, void *r,
@@ -402,25 +441,40 @@ void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, c
     prof_end(ctx);
 }
 
-// z = P^{-1} q for the `cells` cells stored in the type's q / z buffers.
-void apply_type(npfem_ctx *ctx, MeshTypeImpl *t) {
-    const int rows = 3 * t->ncells;
+// z = P^{-1} q for every cell of every type (q / z buffers of the types):
+// FP64 form: one SIMT GEMM per type; mixed forms: grouped tensor-core applies
+// and refinement sweeps (a residual per type between grouped corrections).
+void apply_all(npfem_ctx *ctx) {
     if (!mixed(ctx)) {
-        dim3 grid((t->nV + SG_T - 1) / SG_T, (rows + SG_T - 1) / SG_T);
-        prof_begin(ctx, NPFEM_K_GEMM);
-        k_gemm_simt<double><<<grid, 256, 0, ctx->stream>>>(rows, t->nV, t->nVp, (const double *)t->q, t->Pinv64,
-                                                           (double *)t->z);
-        CK(cudaGetLastError());
-        prof_end(ctx);
+        for (auto *t : ctx->types) {
+            if (!t->ncells) continue;
+            const int rows = 3 * t->ncells;
+            dim3 grid((t->nV + SG_T - 1) / SG_T, (rows + SG_T - 1) / SG_T);
+            prof_begin(ctx, NPFEM_K_GEMM);
+            k_gemm_simt<double><<<grid, 256, 0, ctx->stream>>>(rows, t->nV, t->nVp, (const double *)t->q,
+                                                               t->Pinv64, (double *)t->z);
+            CK(cudaGetLastError());
+            prof_end(ctx);
+        }
         return;
     }
-    gemm_tc(ctx, t, t->mapQ, rows, (float *)t->z, 0, nullptr);
-    for (int s = 0; s < ctx->opt.refine_max; ++s) {
-        residual(ctx, t, t->ncells, (const float *)t->q, (const float *)t->z, t->rlo, t->conv, s == 0, 0);
-        gemm_tc(ctx, t, t->mapR, rows, (float *)t->z, 1, t->conv);
+    std::vector<GemmItem> first, corr;
+    for (auto *t : ctx->types) {
+        if (!t->ncells) continue;
+        first.push_back(GemmItem{t, &t->mapQ, 3 * t->ncells, (float *)t->z, nullptr});
+        corr.push_back(GemmItem{t, &t->mapR, 3 * t->ncells, (float *)t->z, t->conv});
     }
-    residual(ctx, t, t->ncells, (const float *)t->q, (const float *)t->z, nullptr, t->conv,
-             ctx->opt.refine_max == 0, 1);
+    gemm_group(ctx, first, 0);
+    for (int s = 0; s < ctx->opt.refine_max; ++s) {
+        for (auto *t : ctx->types)
+            if (t->ncells)
+                residual(ctx, t, t->ncells, (const float *)t->q, (const float *)t->z, t->rlo, t->conv, s == 0, 0);
+        gemm_group(ctx, corr, 1);
+    }
+    for (auto *t : ctx->types)
+        if (t->ncells)
+            residual(ctx, t, t->ncells, (const float *)t->q, (const float *)t->z, nullptr, t->conv,
+                     ctx->opt.refine_max == 0, 1);
 }
 
 void fallback_apply(npfem_ctx *ctx, MeshTypeImpl *t) {
@@ -448,9 +502,9 @@ void enqueue_step(npfem_ctx *ctx) {
     const int K = ctx->opt.iters;
     for (int k = 0; k < K; ++k) {
         const int last = (k == K - 1);
+        apply_all(ctx);
         for (auto *t : ctx->types) {
             if (!t->ncells) continue;
-            apply_type(ctx, t);
             CK(cudaMemsetAsync(t->fb_count, 0, sizeof(int), ctx->stream));
             run_iterate(ctx, t, last, false);
             fallback_apply(ctx, t);
@@ -745,14 +799,98 @@ void invert_on_gpu(npfem_ctx *ctx, MeshTypeImpl *t, const std::vector<double> &P
     for (void *p : tmp) cudaFree(p);
 }
 
+// GEMM tile autotuner: for each (device, nV, operand type) time the grouped
+// tensor-core apply on 24576 right-hand-side rows for the N-tile widths that
+// cover nV with the fewest (and one more) tiles and 2..6 pipeline stages, and
+// keep the fastest.  Results are cached per process and, when
+// npfem_options.autotune_cache names a file, read from / appended to it
+// ("key n_tile stages microseconds" lines).
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tuned;
+
+std::string tune_key(npfem_ctx *ctx, int nV) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) prop.name[0] = 0;
+    std::string name(prop.name);
+    for (char &c : name)
+        if (c == ' ') c = '_';
+    return name + "|nV=" + std::to_string(nV) + "|" + (bf16(ctx) ? "bf16" : "tf32");
+}
+
 void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
-    const int ntiles = (t->nV + 255) / 256;
-    int nt = (t->nV + ntiles - 1) / ntiles;
-    nt = (nt + 15) / 16 * 16;
-    t->n_tile = nt;
-    const size_t stage = (size_t)(tc::BM + nt) * tc::KB_BYTES;
-    t->stages = (int)std::min<size_t>(4, (200 * 1024) / stage);
-    (void)ctx;
+    const void *pb = bf16(ctx) ? (const void *)t->Pinv16 : (const void *)t->Pinv32;
+    const std::string key = tune_key(ctx, t->nV);
+    auto use = [&](int nt, int st) {
+        t->n_tile = nt;
+        t->stages = st;
+        t->mapP = make_map(ctx, pb, bf16(ctx), t->nV, t->nV, t->nVp, nt);
+    };
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) { use(it->second.first, it->second.second); return; }
+        if (ctx->opt.autotune_cache) {
+            std::ifstream f(ctx->opt.autotune_cache);
+            std::string line;
+            while (std::getline(f, line)) {
+                std::istringstream ls(line);
+                std::string k;
+                int nt = 0, st = 0;
+                if (ls >> k >> nt >> st && k == key && nt >= 16 && nt <= 256 && nt % 16 == 0 && st >= 2 && st <= 8) {
+                    g_tuned[key] = {nt, st};
+                    use(nt, st);
+                    return;
+                }
+            }
+        }
+    }
+    const int rows = 3 * 8192;
+    std::vector<void *> tmp;
+    float best = 1e30f;
+    int best_nt = 0, best_st = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    try {
+        void *Q = dalloc<unsigned char>(ctx, (size_t)rows * t->nVp * (bf16(ctx) ? 2 : 4), &tmp);
+        float *Z = dalloc<float>(ctx, (size_t)rows * t->nVp, &tmp);
+        CUtensorMap mq = make_map(ctx, Q, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        const int base_tiles = (t->nV + 255) / 256;
+        for (int ntiles = base_tiles; ntiles <= base_tiles + 1; ++ntiles) {
+            int nt = ((t->nV + ntiles - 1) / ntiles + 15) / 16 * 16;
+            if (nt > 256 || nt < 16) continue;
+            for (int st = 2; st <= 6; ++st) {
+                if (grouped_smem(st, nt) + 2048 > (size_t)ctx->smem_optin) continue;
+                use(nt, st);
+                gemm_tc(ctx, t, mq, rows, Z, 0, nullptr);
+                CK(cudaEventRecord(e0, ctx->stream));
+                for (int r = 0; r < 5; ++r) gemm_tc(ctx, t, mq, rows, Z, 0, nullptr);
+                CK(cudaEventRecord(e1, ctx->stream));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; best_nt = nt; best_st = st; }
+            }
+        }
+    } catch (...) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaStreamSynchronize(ctx->stream);
+        for (void *p : tmp) cudaFree(p);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (void *p : tmp) cudaFree(p);
+    if (!best_nt) fail(ctx, NPFEM_EINVAL, "no GEMM tile configuration fits nV = %d", t->nV);
+    use(best_nt, best_st);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = {best_nt, best_st};
+    if (ctx->opt.autotune_cache) {
+        std::ofstream f(ctx->opt.autotune_cache, std::ios::app);
+        f << key << " " << best_nt << " " << best_st << " " << (best * 1000.0f / 5.0f) << "\n";
+    }
 }
 
 void free_cells(MeshTypeImpl *t) {
@@ -991,11 +1129,7 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         if (st < 9) st = 9;
         t->stash_T = (int)st;
         t->smem_step = smem_header_bytes() + (3 * SMEM_VECS * (size_t)t->nVp + t->stash_T) * es;
-        if (mixed(ctx)) {
-            choose_tiles(ctx, t);
-            const void *pb = bf16(ctx) ? (const void *)t->Pinv16 : (const void *)t->Pinv32;
-            t->mapP = make_map(ctx, pb, bf16(ctx), nV, nV, t->nVp, t->n_tile);
-        }
+        if (mixed(ctx)) choose_tiles(ctx, t);
         if (t->smem_step > (size_t)ctx->smem_optin || gemm_smem(t) + 2048 > (size_t)ctx->smem_optin)
             fail(ctx, NPFEM_EINVAL, "mesh type needs more shared memory than the device offers");
         CK(cudaStreamSynchronize(ctx->stream));

@@ -6,3 +6,4 @@
 #include "step_kernels.cuh"
 #include "gemm_simt.cuh"
 #include "gemm_tc.cuh"
+#include "gemm_grouped.cuh"
