@@ -58,8 +58,7 @@ struct MeshTypeImpl {
     double *diag = nullptr, *minv = nullptr;
     float *dhi = nullptr, *dlo = nullptr;
     int *op = nullptr;
-    unsigned short *oj = nullptr;
-    float *ov = nullptr;
+    int2 *oe = nullptr;
     int n_off = 0;
     // tensor-core GEMM configuration
     int n_tile = 0, stages = 0;
@@ -420,8 +419,7 @@ void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, c
     a.dhi = t->dhi;
     a.dlo = t->dlo;
     a.op = t->op;
-    a.oj = t->oj;
-    a.ov = t->ov;
+    a.oe = t->oe;
     a.q = q;
     a.z = z;
     a.r_bf16 = bf16(ctx) ? (__nv_bfloat16 *)r : nullptr;
@@ -1082,19 +1080,20 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         else t->tc64 = upload_consts<double>(ctx, t, H, mass);
         std::vector<double> minv(nV), diag(nV);
         std::vector<int> op(nV + 1, 0);
-        std::vector<unsigned short> oj;
-        std::vector<float> ov;
+        std::vector<int2> oe;
         for (int v = 0; v < nV; ++v) {
             minv[v] = 1.0 / mass[v];
             diag[v] = H.P[(size_t)v * nV + v];
             for (int u = 0; u < nV; ++u) {
                 double p = H.P[(size_t)v * nV + u];
                 if (u != v && p != 0.0) {
-                    oj.push_back((unsigned short)u);
-                    ov.push_back((float)p);
+                    const float pf = (float)p;
+                    int bits;
+                    std::memcpy(&bits, &pf, 4);
+                    oe.push_back(make_int2(u, bits));
                 }
             }
-            op[v + 1] = (int)oj.size();
+            op[v + 1] = (int)oe.size();
         }
         t->minv = upload(ctx, minv, t->owned);
         t->diag = upload(ctx, diag, t->owned);
@@ -1106,9 +1105,8 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         t->dhi = upload(ctx, dhi, t->owned);
         t->dlo = upload(ctx, dlo, t->owned);
         t->op = upload(ctx, op, t->owned);
-        t->oj = upload(ctx, oj, t->owned);
-        t->ov = upload(ctx, ov, t->owned);
-        t->n_off = (int)oj.size();
+        t->oe = upload(ctx, oe, t->owned);
+        t->n_off = (int)oe.size();
         invert_on_gpu(ctx, t, H.P);
         // per-cell kernel shape: EPT elements per thread, block <= 256 (<= 512 for big meshes)
         const int n3 = 3 * t->nVp;

@@ -466,13 +466,12 @@ __global__ void k_fallback_apply(int nV, int nVp, const T *__restrict__ Pinv, co
 // their rows untouched).  final_pass: norms only, for the statistics of
 // cells that never converged.
 struct ResidArgs {
-    int ncells, nV, nVp, first, final_pass, n_off, stage_csr;
+    int ncells, nV, nVp, first, final_pass, n_off;
     double tol;
     const double *diag;      // [nV] diag(P)
     const float *dhi, *dlo;  // [nV] diag(P) = dhi + dlo (+ O(2^-48))
     const int *op;           // [nV + 1] off-diagonal CSR row starts
-    const unsigned short *oj;
-    const float *ov;
+    const int2 *oe;          // (column, value bits) per off-diagonal entry
     const float *q, *z;
     __nv_bfloat16 *r_bf16;   // BF16 form
     float *r_f32;            // TF32 form
@@ -502,16 +501,18 @@ __global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
             for (int i = lane; i < n3 / 4; i += 32) dst[i] = __ldg(src + i);
         }
         __syncwarp();
-        Acc<float> s[2];
-        s[0].zero(); s[1].zero();
+        // squared norms for the convergence test (|r| <= tol |q| needs ~1% accuracy):
+        // FP32 per lane, float-float across the warp
+        float nr = 0.f, nq = 0.f;
         for (int v = lane; v < nVp; v += 32) {
             float r[3] = {0.f, 0.f, 0.f};
             if (v < nV) {
                 float off[3] = {0.f, 0.f, 0.f};
                 const int kend = __ldg(a.op + v + 1);
                 for (int k = __ldg(a.op + v); k < kend; ++k) {
-                    const int u = __ldg(a.oj + k);
-                    const float w = __ldg(a.ov + k);
+                    const int2 e = __ldg(a.oe + k);          // (column, value bits)
+                    const int u = e.x;
+                    const float w = __int_as_float(e.y);
                     off[0] = fmaf(w, zw[u], off[0]);
                     off[1] = fmaf(w, zw[nVp + u], off[1]);
                     off[2] = fmaf(w, zw[2 * nVp + u], off[2]);
@@ -526,8 +527,8 @@ __global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
                         t = __fmaf_rn(-__ldg(a.dlo + v), zv, t);
                         r[c] = __fsub_rn(t, off[c]);
                     }
-                    s[0].add(r[c] * r[c]);
-                    s[1].add(qv * qv);
+                    nr = fmaf(r[c], r[c], nr);
+                    nq = fmaf(qv, qv, nq);
                 }
             }
             if (!a.final_pass) {
@@ -538,6 +539,11 @@ __global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
                 }
             }
         }
+        Acc<float> s[2];
+        s[0].zero();
+        s[1].zero();
+        s[0].add(nr);
+        s[1].add(nq);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             s[0].merge_shfl(0xffffffffu, off);
