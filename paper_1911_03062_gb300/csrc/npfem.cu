@@ -60,6 +60,11 @@ struct MeshTypeImpl {
     int *op = nullptr;
     int2 *oe = nullptr;
     int n_off = 0;
+    // fixed-width row table of the off-diagonal entries for the block-per-cell
+    // residual (ell_W = 0: rows too long or too many vertices, CSR kernel)
+    unsigned short *ell_col = nullptr;
+    float *ell_val = nullptr;
+    int ell_W = 0, ell_KR = 0, ell_nt = 0, ell_grid = 0;
     // tensor-core GEMM configuration
     int n_tile = 0, stages = 0;
     CUtensorMap mapP{};
@@ -325,6 +330,24 @@ size_t gemm_smem(const MeshTypeImpl *t) { return grouped_smem(t->stages, t->n_ti
 
 // Kernel attributes are set at set-up time (never inside a stream capture),
 // to the device's opt-in maximum so that every type's request fits.
+using ResidEllFn = void (*)(ResidEllArgs);
+
+ResidEllFn resid_ell_fn(int W, int KR) {
+    switch (W * 10 + KR) {
+    case 121: return k_residual_ell<12, 1>;
+    case 122: return k_residual_ell<12, 2>;
+    case 123: return k_residual_ell<12, 3>;
+    case 124: return k_residual_ell<12, 4>;
+    case 161: return k_residual_ell<16, 1>;
+    case 162: return k_residual_ell<16, 2>;
+    case 163: return k_residual_ell<16, 3>;
+    case 164: return k_residual_ell<16, 4>;
+    default: return nullptr;
+    }
+}
+
+size_t resid_ell_smem(int nVp) { return (size_t)RESID_STAGES * 2 * 3 * nVp * sizeof(float); }
+
 void set_kernel_attrs(npfem_ctx *ctx) {
     int mx = 0;
     CK(cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
@@ -346,6 +369,8 @@ void set_kernel_attrs(npfem_ctx *ctx) {
     }
     all(k_residual<false>);
     all(k_residual<true>);
+    for (int W : {12, 16})
+        for (int KR = 1; KR <= 4; ++KR) all(resid_ell_fn(W, KR));
     ctx->smem_optin = mx;
 }
 
@@ -428,6 +453,32 @@ void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, c
     a.any_active = ctx->d_any;
     a.st = ctx->d_st;
     a.n_off = t->n_off;
+    if (t->ell_W && !ctx->opt.residual_fp64) {
+        ResidEllArgs e{};
+        e.ncells = rows_cells;
+        e.nV = t->nV;
+        e.nVp = t->nVp;
+        e.first = first;
+        e.final_pass = final_pass;
+        e.tol2 = (float)(ctx->opt.refine_tol * ctx->opt.refine_tol);
+        e.dhi = t->dhi;
+        e.dlo = t->dlo;
+        e.ell_col = t->ell_col;
+        e.ell_val = t->ell_val;
+        e.q = q;
+        e.z = z;
+        e.r_bf16 = a.r_bf16;
+        e.r_f32 = a.r_f32;
+        e.conv = conv;
+        e.any_active = ctx->d_any;
+        e.st = ctx->d_st;
+        const int grid = std::min(rows_cells, t->ell_grid);
+        prof_begin(ctx, NPFEM_K_RESIDUAL);
+        resid_ell_fn(t->ell_W, t->ell_KR)<<<grid, t->ell_nt, resid_ell_smem(t->nVp), ctx->stream>>>(e);
+        CK(cudaGetLastError());
+        prof_end(ctx);
+        return;
+    }
     // one warp per cell, up to 8 warps per block, each warp's z in shared memory
     const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / (12 * (size_t)t->nVp)));
     const size_t smem = (size_t)wpb * 3 * t->nVp * sizeof(float);
@@ -1097,7 +1148,7 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         }
         t->minv = upload(ctx, minv, t->owned);
         t->diag = upload(ctx, diag, t->owned);
-        std::vector<float> dhi(nV), dlo(nV);
+        std::vector<float> dhi(t->nVp, 0.f), dlo(t->nVp, 0.f);
         for (int v = 0; v < nV; ++v) {
             dhi[v] = (float)diag[v];
             dlo[v] = (float)(diag[v] - (double)dhi[v]);
@@ -1107,6 +1158,33 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         t->op = upload(ctx, op, t->owned);
         t->oe = upload(ctx, oe, t->owned);
         t->n_off = (int)oe.size();
+        if (mixed(ctx)) {
+            int wmax = 0;
+            for (int v = 0; v < nV; ++v) wmax = std::max(wmax, op[v + 1] - op[v]);
+            const int KR = (t->nVp + RESID_MAX_THREADS - 1) / RESID_MAX_THREADS;
+            if (wmax <= 16 && KR <= 4 && nV < 65536) {
+                const int W = wmax <= 12 ? 12 : 16;
+                const int nVp = t->nVp;
+                std::vector<unsigned short> col((size_t)W * nVp, 0);
+                std::vector<float> val((size_t)W * nVp, 0.f);
+                for (int v = 0; v < nV; ++v)
+                    for (int k = op[v]; k < op[v + 1]; ++k) {
+                        const int w = k - op[v];
+                        col[(size_t)w * nVp + v] = (unsigned short)oe[k].x;
+                        std::memcpy(&val[(size_t)w * nVp + v], &oe[k].y, 4);
+                    }
+                t->ell_col = upload(ctx, col, t->owned);
+                t->ell_val = upload(ctx, val, t->owned);
+                t->ell_W = W;
+                t->ell_KR = KR;
+                t->ell_nt = ((nVp + KR - 1) / KR + 31) / 32 * 32;
+                int nb = 0;
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, resid_ell_fn(W, KR), t->ell_nt,
+                                                                 resid_ell_smem(nVp)));
+                if (nb < 1) fail(ctx, NPFEM_ECUDA, "residual kernel does not fit on an SM");
+                t->ell_grid = nb * ctx->nsm;
+            }
+        }
         invert_on_gpu(ctx, t, H.P);
         // per-cell kernel shape: EPT elements per thread, block <= 256 (<= 512 for big meshes)
         const int n3 = 3 * t->nVp;

@@ -7,3 +7,4 @@
 #include "gemm_simt.cuh"
 #include "gemm_tc.cuh"
 #include "gemm_grouped.cuh"
+#include "residual_ell.cuh"
