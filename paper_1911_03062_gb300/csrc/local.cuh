@@ -41,6 +41,7 @@ struct TypeConst {
     const HingeInc<T> *vh;
     const T *mh2;           // nV: m_v / h^2
     double V0;              // rest volume
+    double V0x6, vtol6;     // 6 V0 and 6 tol |V0| (the volume sums give 6 V)
     T kb, kv;               // bending and volume weights
     // slot-major padded copies of the incidence lists (slot q of vertex v at
     // [q * nV + v]; unused slots carry zero weights), for one-round gathers:
@@ -440,10 +441,11 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
             int e = tid + j * B;
             if (e < n3) a1[1].add_prod(gva[e], gva[e]);    // zero on padding
         }
+        // thread 0 works with 6 V (the sums' own scale): no FP64 division
         block_reduce_t0<T, 2>(a1, S.red, [&](const double *s) {
-            const double V = s[0] / 6.0;
-            S.bc->i[0] = fabs(V - tc.V0) <= Prec<T>::vol_tol * fabs(tc.V0);
-            S.bc->t[0] = T((tc.V0 - V) / s[1]);            // p_0 = x: gV.(x - p_0) = 0
+            const double r6 = tc.V0x6 - s[0];               // 6 (V0 - V)
+            S.bc->i[0] = fabs(r6) <= tc.vtol6;
+            S.bc->t[0] = T(r6) / T(6.0 * s[1]);             // p_0 = x: gV.(x - p_0) = 0
         });
         T *gV = gva;
         for (int it = 0; !S.bc->i[0]; ++it) {
@@ -482,7 +484,7 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                     a2[1].add_prod(gv, x[j] - p[j]);
                 }
                 block_reduce_t0<T, 2>(a2, S.red, [&](const double *s) {
-                    S.bc->t[0] = T((tc.V0 - S.bc->d[0] - s[1]) / s[0]);
+                    S.bc->t[0] = T(tc.V0x6 - S.bc->d[0] - 6.0 * s[1]) / T(6.0 * s[0]);
                 });
             }
             const T lam = S.bc->t[0];
@@ -500,9 +502,8 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
             a3[0].zero();
             volume_pass(tc, pos, nVp, a3[0]);
             block_reduce_t0<T, 1>(a3, S.red, [&](const double *s) {
-                const double V = s[0] / 6.0;
-                S.bc->d[0] = V;
-                S.bc->i[0] = fabs(V - tc.V0) <= Prec<T>::vol_tol * fabs(tc.V0) || it == 7;
+                S.bc->d[0] = s[0];                           // 6 V(p)
+                S.bc->i[0] = fabs(tc.V0x6 - s[0]) <= tc.vtol6 || it == 7;
             });
         }
     }

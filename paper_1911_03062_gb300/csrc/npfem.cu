@@ -253,6 +253,7 @@ IterArgs<T> make_args(npfem_ctx *ctx, MeshTypeImpl *t) {
     a.use_allow = mixed(ctx) ? 1 : 0;
     a.stash_T = t->stash_T;
     a.h = t->h;
+    a.inv_h = 1.0 / t->h;
     a.c1 = ctx->opt.armijo_c1;
     a.xn = t->xn;
     a.vn = t->vn;
@@ -810,6 +811,8 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
     c.vh = upload(ctx, vh, t->owned);
     c.mh2 = upload(ctx, cvt<T>(mh2), t->owned);
     c.V0 = H.V0;
+    c.V0x6 = 6.0 * H.V0;
+    c.vtol6 = 6.0 * Prec<T>::vol_tol * std::fabs(H.V0);
     c.kb = (T)t->kb;
     c.kv = (T)t->kv;
     return c;

@@ -19,7 +19,7 @@ template <typename T>
 struct IterArgs {
     TypeConst<T> tc;
     int ncells, m, max_bt, last, use_allow, stash_T;
-    double h, c1;
+    double h, inv_h, c1;
     double *xn, *vn;              // state, FP64 SoA
     const double *const *fptr;    // device slot holding the f_ext base (public layout)
     const long long *pub_off;     // [cell] offset of the cell in the public arrays (doubles)
@@ -124,8 +124,11 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             s[c].add(y[j]);
         }
         block_reduce_t0<double, 3>(s, S.red, [&](const double *o) {
+            // origin of the FP32 offsets: the centroid up to ~1e-7 relative (any fixed
+            // point serves; it is stored and y is re-formed in FP64 at the end)
+            const double inv_n = (double)(1.0f / (float)a.tc.nV);
             for (int c = 0; c < 3; ++c) {
-                S.bc->d[c] = o[c] / a.tc.nV;
+                S.bc->d[c] = o[c] * inv_n;
                 a.origin[3 * cell + c] = S.bc->d[c];
             }
         });
@@ -198,6 +201,18 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         double *Mc = a.M + (long long)cell * m * m;
         const int cnt = a.hcount[cell], head = a.hhead[cell];
         auto slot = [&](int l) { return (head - cnt + l + 2 * m) % m; };   // l = 0 oldest
+        // the cell's scalars that thread 0 uses between barriers, fetched up front into
+        // shared memory (red[32 ..), above every reduction's scratch): M, rho, alpha, g, allow
+        double *sM = S.red + 32, *srho = sM + MH * MH, *salp = srho + MH;
+        for (int i = threadIdx.x; i < m * m + 2 * m; i += blockDim.x) {
+            if (i < m * m) sM[i] = Mc[i];
+            else if (i < m * m + m) srho[i - m * m] = rho[i - m * m];
+            else salp[i - m * m - m] = alp[i - m * m - m];
+        }
+        if (threadIdx.x == 0) {
+            S.bc->d[5] = a.g[cell];
+            S.bc->d[6] = a.allow[cell];
+        }
         T r[EPT], d[EPT], gr[EPT], dl[EPT];
         load_vec<T, EPT>(a.z + base, r, n3);
         if (cnt > 0) {
@@ -219,8 +234,8 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
                 for (int l = 0; l < cnt; ++l) {
                     const int i = slot(l);
                     double dot = out[l];
-                    for (int k = 0; k < l; ++k) dot += coef[k] * Mc[slot(k) * m + i];
-                    coef[l] = alp[i] - rho[i] * dot;
+                    for (int k = 0; k < l; ++k) dot += coef[k] * sM[slot(k) * m + i];
+                    coef[l] = salp[i] - srho[i] * dot;
                     S.bc->t[l] = T(coef[l]);
                 }
             }
@@ -271,10 +286,10 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             for (int j = 0; j < EPT; ++j) dt[j] = dl[j] + alpha * d[j];
             local_eval<T, EPT>(a.tc, a.yrel + base, dt, gt, S, a.stash_T, [&](double g, double allow) {
                 const double al = S.bc->d[2], gd = S.bc->d[1];
-                const double slack = a.use_allow ? (a.allow[cell] + allow) : 0.0;
+                const double slack = a.use_allow ? (S.bc->d[6] + allow) : 0.0;
                 S.bc->d[3] = g;
                 S.bc->d[4] = allow;
-                if (g <= a.g[cell] + a.c1 * al * gd + slack) {
+                if (g <= S.bc->d[5] + a.c1 * al * gd + slack) {
                     S.bc->i[3] = 1;
                 } else if (S.bc->i[2] == a.max_bt) {
                     S.bc->i[3] = 2;
@@ -307,7 +322,7 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
                 if (e >= n3) continue;
                 double x = y[j] + (double)dt[j];
                 a.xn[base + e] = x;
-                a.vn[base + e] = (x - xo[j]) / a.h;
+                a.vn[base + e] = (x - xo[j]) * a.inv_h;
             }
             __syncthreads();
             continue;
@@ -350,7 +365,8 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         block_sum_many<T, 2 * MH + 4>(pc, 2 * cnt, 2 * MH, S.pos, out);
         if (threadIdx.x == 0) {
             const double sy = out[2 * MH], ss = out[2 * MH + 1], yy = out[2 * MH + 2], sg = out[2 * MH + 3];
-            const int keep = m > 0 && sy > 1e-12 * sqrt(ss) * sqrt(yy);
+            // curvature test sy > 1e-12 |s| |y|, squared (no FP64 square roots)
+            const int keep = m > 0 && sy > 0.0 && sy * sy > 1e-24 * ss * yy;
             const double gtv = S.bc->d[3];
             a.g[cell] = gtv;
             a.allow[cell] = S.bc->d[4];
@@ -362,19 +378,31 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             if (keep) {
                 if (cnt == m) first_old = 1; else ncnt = cnt + 1;
                 const int ns = head;                         // the new pair's slot
-                rho[ns] = 1.0 / sy;
-                for (int l = first_old; l < cnt; ++l) Mc[slot(l) * m + ns] = out[2 * l + 1];
+                double rr;
+                if (sizeof(T) == 4 && sy > 1e-30 && sy < 1e30) {
+                    // FP32 reciprocal + one Newton step in FP64: ~1e-14 relative
+                    const double r0 = (double)(1.0f / (float)sy);
+                    rr = r0 * (2.0 - sy * r0);
+                } else {
+                    rr = 1.0 / sy;
+                }
+                rho[ns] = rr;
+                srho[ns] = rr;
+                for (int l = first_old; l < cnt; ++l) {
+                    Mc[slot(l) * m + ns] = out[2 * l + 1];
+                    sM[slot(l) * m + ns] = out[2 * l + 1];
+                }
             }
             // alpha_i = rho_i (s_i . grad - sum_{j newer} alpha_j s_i . y_j), newest first
             double al[MH + 1];
             const int nold = cnt - first_old;
-            if (keep) al[nold] = rho[head] * sg;
+            if (keep) al[nold] = srho[head] * sg;
             for (int l = cnt - 1; l >= first_old; --l) {
                 const int i = slot(l), p = l - first_old;
                 double dot = out[2 * l];
-                for (int k = p + 1; k < nold; ++k) dot -= al[k] * Mc[i * m + slot(k + first_old)];
+                for (int k = p + 1; k < nold; ++k) dot -= al[k] * sM[i * m + slot(k + first_old)];
                 if (keep) dot -= al[nold] * out[2 * l + 1];
-                al[p] = rho[i] * dot;
+                al[p] = srho[i] * dot;
             }
             for (int p = 0; p < nold; ++p) {
                 alp[slot(p + first_old)] = al[p];
