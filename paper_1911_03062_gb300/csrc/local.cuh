@@ -52,6 +52,30 @@ struct TypeConst {
 
 constexpr int PAD_T = 8, PAD_H = 16;
 
+// Elements of a per-cell vector owned by the calling thread: EPT / 4 granules
+// of 4 consecutive elements, granule g at 4 (tid + g B), so vector loads and
+// stores are 16 bytes (FP32) wide and a warp's granules are contiguous.
+// Element j is lane j % 4 of granule j / 4; a granule lies in one component
+// (nVp is a multiple of 8).
+__device__ __forceinline__ int elem_of(int j) { return 4 * (threadIdx.x + (j >> 2) * blockDim.x) + (j & 3); }
+
+// 4 consecutive values at p (16-byte aligned for FP32, 32-byte for FP64)
+__device__ __forceinline__ void ld4(const float *p, float (&r)[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&r)[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, const float (&r)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(r[0], r[1], r[2], r[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&r)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(r[0], r[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(r[2], r[3]);
+}
+
 __device__ __forceinline__ int elem_cv(int e, int nVp, int &v) {
     int c = (e >= nVp) + (e >= 2 * nVp);
     v = e - c * nVp;
@@ -274,20 +298,33 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
     T en = T(0), al = T(0);      // energy and allowance partials (per thread: a handful of terms)
     // 1. positions; gradient buffer starts with the inertia term M/h^2 (x - y)
 #pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-        int e = tid + j * B, v;
-        x[j] = T(0);
-        if (e >= n3) continue;
-        elem_cv(e, nVp, v);
-        gva[e] = T(0);
-        if (v >= nV) { gsh[e] = T(0); continue; }
-        x[j] = yrel[e] + dt[j];
-        pos[e] = x[j];
-        T mh = tc.mh2[v];
-        gsh[e] = mh * dt[j];
-        T q = T(0.5) * mh * dt[j] * dt[j];
-        en += q;
-        al += q;
+    for (int g4 = 0; g4 < EPT / 4; ++g4) {
+        const int e0 = 4 * (tid + g4 * B);
+        T xv[4] = {T(0), T(0), T(0), T(0)}, gv[4] = {T(0), T(0), T(0), T(0)};
+        if (e0 < n3) {
+            int v0;
+            elem_cv(e0, nVp, v0);
+            T yr4[4], mh4[4];
+            ld4(yrel + e0, yr4);
+            ld4(tc.mh2 + v0, mh4);                      // zero beyond nV
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const T dj = dt[4 * g4 + i];
+                if (v0 + i < nV) {
+                    xv[i] = yr4[i] + dj;
+                    gv[i] = mh4[i] * dj;
+                    T q = T(0.5) * mh4[i] * dj * dj;
+                    en += q;
+                    al += q;
+                }
+            }
+            const T zero4[4] = {T(0), T(0), T(0), T(0)};
+            st4(pos + e0, xv);
+            st4(gsh + e0, gv);
+            st4(gva + e0, zero4);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[4 * g4 + i] = xv[i];
     }
     __syncthreads();
     Acc<T> aV;
@@ -437,9 +474,13 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
         a1[0] = aV;
         a1[1].zero();
 #pragma unroll
-        for (int j = 0; j < EPT; ++j) {
-            int e = tid + j * B;
-            if (e < n3) a1[1].add_prod(gva[e], gva[e]);    // zero on padding
+        for (int g4 = 0; g4 < EPT / 4; ++g4) {
+            const int e0 = 4 * (tid + g4 * B);
+            if (e0 >= n3) continue;
+            T gv[4];
+            ld4(gva + e0, gv);                              // zero on padding
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a1[1].add_prod(gv[i], gv[i]);
         }
         // thread 0 works with 6 V (the sums' own scale): no FP64 division
         block_reduce_t0<T, 2>(a1, S.red, [&](const double *s) {
@@ -474,14 +515,19 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                 a2[0].zero();
                 a2[1].zero();
 #pragma unroll
-                for (int j = 0; j < EPT; ++j) {
-                    int e = tid + j * B, v;
-                    if (e >= n3) continue;
-                    elem_cv(e, nVp, v);
-                    if (v >= nV) continue;
-                    T gv = gV[e];
-                    a2[0].add_prod(gv, gv);
-                    a2[1].add_prod(gv, x[j] - p[j]);
+                for (int g4 = 0; g4 < EPT / 4; ++g4) {
+                    const int e0 = 4 * (tid + g4 * B);
+                    if (e0 >= n3) continue;
+                    int v0;
+                    elem_cv(e0, nVp, v0);
+                    T gv[4];
+                    ld4(gV + e0, gv);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (v0 + i >= nV) continue;
+                        a2[0].add_prod(gv[i], gv[i]);
+                        a2[1].add_prod(gv[i], x[4 * g4 + i] - p[4 * g4 + i]);
+                    }
                 }
                 block_reduce_t0<T, 2>(a2, S.red, [&](const double *s) {
                     S.bc->t[0] = T(tc.V0x6 - S.bc->d[0] - 6.0 * s[1]) / T(6.0 * s[0]);
@@ -489,13 +535,20 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
             }
             const T lam = S.bc->t[0];
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                int e = tid + j * B, v;
-                if (e >= n3) continue;
-                elem_cv(e, nVp, v);
-                if (v >= nV) continue;
-                p[j] = x[j] + lam * gV[e];
-                pos[e] = p[j];
+            for (int g4 = 0; g4 < EPT / 4; ++g4) {
+                const int e0 = 4 * (tid + g4 * B);
+                if (e0 >= n3) continue;
+                int v0;
+                elem_cv(e0, nVp, v0);
+                T gv[4], pv[4];
+                ld4(gV + e0, gv);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int j = 4 * g4 + i;
+                    if (v0 + i < nV) p[j] = x[j] + lam * gv[i];
+                    pv[i] = p[j];
+                }
+                st4(pos + e0, pv);
             }
             __syncthreads();
             Acc<T> a3[1];
@@ -509,16 +562,24 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
     }
     // 5. gradient to registers (+ volume term), energy
 #pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-        int e = tid + j * B, v;
-        gr[j] = T(0);
-        if (e >= n3) continue;
-        elem_cv(e, nVp, v);
-        if (v >= nV) continue;
-        T r = x[j] - p[j];
-        en += T(0.5) * tc.kv * r * r;
-        al += tc.kv * fabs(r) * fabs(x[j]);
-        gr[j] = gsh[e] + tc.kv * r;
+    for (int g4 = 0; g4 < EPT / 4; ++g4) {
+        const int e0 = 4 * (tid + g4 * B);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) gr[4 * g4 + i] = T(0);
+        if (e0 >= n3) continue;
+        int v0;
+        elem_cv(e0, nVp, v0);
+        T gs[4];
+        ld4(gsh + e0, gs);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (v0 + i >= nV) continue;
+            const int j = 4 * g4 + i;
+            T r = x[j] - p[j];
+            en += T(0.5) * tc.kv * r * r;
+            al += tc.kv * fabs(r) * fabs(x[j]);
+            gr[j] = gs[i] + tc.kv * r;
+        }
     }
     Acc<T> fin[2];
     fin[0].zero();

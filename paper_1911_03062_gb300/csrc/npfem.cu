@@ -745,7 +745,7 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
     std::vector<int4> tri(t->nT), hv(t->nH);
     for (int i = 0; i < t->nT; ++i) tri[i] = make_int4(H.tri[3 * i], H.tri[3 * i + 1], H.tri[3 * i + 2], 0);
     for (int i = 0; i < t->nH; ++i) hv[i] = make_int4(H.hv[4 * i], H.hv[4 * i + 1], H.hv[4 * i + 2], H.hv[4 * i + 3]);
-    std::vector<double> wtri(2 * t->nT), mh2(t->nV);
+    std::vector<double> wtri(2 * t->nT), mh2(t->nVp, 0.0);   // mh2 zero-padded for 4-wide loads
     for (int i = 0; i < t->nT; ++i) {
         wtri[2 * i] = t->ks * H.area[i];
         wtri[2 * i + 1] = t->ka * H.area[i];

@@ -38,21 +38,43 @@ struct IterArgs {
     DevStatus *st;
 };
 
+// this thread's elements (granules of 4, see elem_of) of a per-cell vector
 template <typename T, int EPT>
 __device__ __forceinline__ void load_vec(const T *__restrict__ p, T (&r)[EPT], int n3) {
 #pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-        int e = threadIdx.x + j * blockDim.x;
-        r[j] = e < n3 ? p[e] : T(0);
+    for (int g = 0; g < EPT / 4; ++g) {
+        const int e0 = 4 * (threadIdx.x + g * blockDim.x);
+        T v[4] = {T(0), T(0), T(0), T(0)};
+        if (e0 < n3) ld4(p + e0, v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) r[4 * g + i] = v[i];
     }
 }
 
 template <typename T, int EPT>
 __device__ __forceinline__ void store_vec(T *__restrict__ p, const T (&r)[EPT], int n3) {
 #pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-        int e = threadIdx.x + j * blockDim.x;
-        if (e < n3) p[e] = r[j];
+    for (int g = 0; g < EPT / 4; ++g) {
+        const int e0 = 4 * (threadIdx.x + g * blockDim.x);
+        if (e0 >= n3) continue;
+        const T v[4] = {r[4 * g], r[4 * g + 1], r[4 * g + 2], r[4 * g + 3]};
+        st4(p + e0, v);
+    }
+}
+
+// BF16 copy of this thread's elements (the GEMM operand of q)
+template <typename T, int EPT>
+__device__ __forceinline__ void store_vec_bf16(__nv_bfloat16 *__restrict__ p, const T (&r)[EPT], int n3) {
+#pragma unroll
+    for (int g = 0; g < EPT / 4; ++g) {
+        const int e0 = 4 * (threadIdx.x + g * blockDim.x);
+        if (e0 >= n3) continue;
+        __nv_bfloat162 lo = __floats2bfloat162_rn((float)r[4 * g], (float)r[4 * g + 1]);
+        __nv_bfloat162 hi = __floats2bfloat162_rn((float)r[4 * g + 2], (float)r[4 * g + 3]);
+        uint2 u;
+        u.x = *reinterpret_cast<unsigned *>(&lo);
+        u.y = *reinterpret_cast<unsigned *>(&hi);
+        *reinterpret_cast<uint2 *>(p + e0) = u;
     }
 }
 
@@ -63,16 +85,26 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
     const double *f = *a.fptr + a.pub_off[cell];
     const long long base = (long long)cell * n3;
 #pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-        int e = threadIdx.x + j * blockDim.x, v;
-        y[j] = 0.0;
-        xo[j] = 0.0;
-        if (e >= n3) continue;
-        int c = elem_cv(e, nVp, v);
-        if (v >= nV) continue;
-        double x = a.xn[base + e];
-        xo[j] = x;
-        y[j] = x + a.h * a.vn[base + e] + a.h * a.h * a.minv[v] * f[3 * v + c];
+    for (int g = 0; g < EPT / 4; ++g) {
+        const int e0 = 4 * (threadIdx.x + g * blockDim.x);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            y[4 * g + i] = 0.0;
+            xo[4 * g + i] = 0.0;
+        }
+        if (e0 >= n3) continue;
+        int v0;
+        const int c = elem_cv(e0, nVp, v0);
+        double xv[4], vv[4];
+        ld4(a.xn + base + e0, xv);
+        ld4(a.vn + base + e0, vv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int v = v0 + i;
+            if (v >= nV) continue;
+            xo[4 * g + i] = xv[i];
+            y[4 * g + i] = xv[i] + a.h * vv[i] + a.h * a.h * a.minv[v] * f[3 * v + c];
+        }
     }
 }
 
@@ -117,7 +149,7 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         s[0].zero(); s[1].zero(); s[2].zero();
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
-            int e = threadIdx.x + j * blockDim.x, v;
+            int e = elem_of(j), v;
             if (e >= n3) continue;
             int c = elem_cv(e, nVp, v);
             if (v >= a.tc.nV) continue;
@@ -135,7 +167,7 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         T yr[EPT], dl[EPT], gr[EPT];
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
-            int e = threadIdx.x + j * blockDim.x, v;
+            int e = elem_of(j), v;
             yr[j] = T(0);
             dl[j] = T(0);
             if (e >= n3) continue;
@@ -155,13 +187,7 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         });
         store_vec<T, EPT>(a.grad + base, gr, n3);
         store_vec<T, EPT>(a.q + base, gr, n3);
-        if (a.q_bf16) {
-#pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                int e = threadIdx.x + j * blockDim.x;
-                if (e < n3) a.q_bf16[base + e] = __float2bfloat16_rn((float)gr[j]);
-            }
-        }
+        if (a.q_bf16) store_vec_bf16<T, EPT>(a.q_bf16 + base, gr, n3);
     }
 }
 
@@ -317,12 +343,18 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             double y[EPT], xo[EPT];
             predictor64<T, EPT>(a, cell, y, xo);
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                int e = threadIdx.x + j * blockDim.x;
-                if (e >= n3) continue;
-                double x = y[j] + (double)dt[j];
-                a.xn[base + e] = x;
-                a.vn[base + e] = (x - xo[j]) * a.inv_h;
+            for (int g = 0; g < EPT / 4; ++g) {
+                const int e0 = 4 * (threadIdx.x + g * blockDim.x);
+                if (e0 >= n3) continue;
+                double xv[4], vv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int j = 4 * g + i;
+                    xv[i] = y[j] + (double)dt[j];
+                    vv[i] = (xv[i] - xo[j]) * a.inv_h;
+                }
+                st4(a.xn + base + e0, xv);
+                st4(a.vn + base + e0, vv);
             }
             __syncthreads();
             continue;
@@ -441,13 +473,7 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             store_vec<T, EPT>(Yh + (long long)head * n3, yv, n3);
         }
         store_vec<T, EPT>(a.q + base, qv, n3);
-        if (a.q_bf16) {
-#pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                int e = threadIdx.x + j * blockDim.x;
-                if (e < n3) a.q_bf16[base + e] = __float2bfloat16_rn((float)qv[j]);
-            }
-        }
+        if (a.q_bf16) store_vec_bf16<T, EPT>(a.q_bf16 + base, qv, n3);
         __syncthreads();
     }
 }
