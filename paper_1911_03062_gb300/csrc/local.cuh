@@ -68,6 +68,14 @@ __device__ __forceinline__ void ld4(const double *p, double (&r)[4]) {
     const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
     r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y;
 }
+__device__ __forceinline__ void ld2(const float *p, float (&r)[2]) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    r[0] = v.x; r[1] = v.y;
+}
+__device__ __forceinline__ void ld2(const double *p, double (&r)[2]) {
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    r[0] = v.x; r[1] = v.y;
+}
 __device__ __forceinline__ void st4(float *p, const float (&r)[4]) {
     *reinterpret_cast<float4 *>(p) = make_float4(r[0], r[1], r[2], r[3]);
 }
@@ -208,7 +216,7 @@ __device__ __forceinline__ void area_target(T s1, T s2, T d[2]) {
 // (e1 x e2) / 6 (each corner's share of the volume gradient) and the
 // signed-volume term (x0 - o).(e1 x e2) of the triangle.
 template <typename T>
-__device__ __forceinline__ T tri_local(const T *pos, int nVp, int4 tv, const T *Di, T ws, T wa, const T o[3],
+__device__ __forceinline__ T tri_local(const T *pos, int nVp, int4 tv, const T (&Di)[4], T ws, T wa, const T o[3],
                                        T R[6], T N[3], T &en, T &al) {
     T F[6], E1[3], E2[3], A0[3];
 #pragma unroll
@@ -248,7 +256,7 @@ __device__ __forceinline__ T tri_local(const T *pos, int nVp, int4 tv, const T *
 
 // Bending of one hinge: b = sum_j c_j x_j, p = b |b_rest| / |b|; stash kb (b - p).
 template <typename T>
-__device__ __forceinline__ void hinge_local(const T *pos, int nVp, int4 hv, const T *hc, T rest, T kb,
+__device__ __forceinline__ void hinge_local(const T *pos, int nVp, int4 hv, const T (&hc)[4], T rest, T kb,
                                             T R[3], T &en, T &al) {
     T b[3];
 #pragma unroll
@@ -273,8 +281,10 @@ __device__ __forceinline__ void hinge_local(const T *pos, int nVp, int4 hv, cons
 template <typename T>
 __device__ __forceinline__ void volume_pass(const TypeConst<T> &tc, const T *pos, int nVp, Acc<T> &aV) {
     const T o0 = pos[0], o1 = pos[nVp], o2 = pos[2 * nVp];
+    int4 tv_n = threadIdx.x < tc.nT ? __ldg(tc.tri + threadIdx.x) : make_int4(0, 0, 0, 0);
     for (int t = threadIdx.x; t < tc.nT; t += blockDim.x) {
-        int4 tv = tc.tri[t];
+        const int4 tv = tv_n;
+        if (t + (int)blockDim.x < tc.nT) tv_n = __ldg(tc.tri + t + blockDim.x);
         T ax = pos[tv.x] - o0, ay = pos[nVp + tv.x] - o1, az = pos[2 * nVp + tv.x] - o2;
         T e1x = pos[tv.y] - pos[tv.x], e1y = pos[nVp + tv.y] - pos[nVp + tv.x], e1z = pos[2 * nVp + tv.y] - pos[2 * nVp + tv.x];
         T e2x = pos[tv.z] - pos[tv.x], e2y = pos[nVp + tv.z] - pos[nVp + tv.x], e2z = pos[2 * nVp + tv.z] - pos[2 * nVp + tv.x];
@@ -335,10 +345,14 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
         const int ct = stash_T / 9;
         for (int t0 = 0; t0 < tc.nT; t0 += ct) {
             const int t1 = min(tc.nT, t0 + ct);
+            // software-pipelined: the next triangle's constants load while this one is evaluated
             for (int t = t0 + tid; t < t1; t += B) {
+                const int4 tv = __ldg(tc.tri + t);
+                T Di[4], w[2];
+                ld4(tc.dinv + 4 * t, Di);
+                ld2(tc.wtri + 2 * t, w);
                 T R[6], N[3];
-                const T *Di = tc.dinv + 4 * t;
-                aV.add(tri_local(pos, nVp, tc.tri[t], Di, tc.wtri[2 * t], tc.wtri[2 * t + 1], o, R, N, en, al));
+                aV.add(tri_local(pos, nVp, tv, Di, w[0], w[1], o, R, N, en, al));
                 T *st = stash + 9 * (t - t0);
 #pragma unroll
                 for (int i = 0; i < 6; ++i) st[i] = R[i];
@@ -409,9 +423,23 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
         const int ch = stash_T / 3;
         for (int h0 = 0; h0 < tc.nH; h0 += ch) {
             const int h1 = min(tc.nH, h0 + ch);
+            int4 hv_n = make_int4(0, 0, 0, 0);
+            T hc_n[4] = {T(0), T(0), T(0), T(0)}, rest_n = T(0);
+            if (h0 + tid < h1) {
+                hv_n = __ldg(tc.hv + h0 + tid);
+                ld4(tc.hc + 4 * (h0 + tid), hc_n);
+                rest_n = tc.hrest[h0 + tid];
+            }
             for (int h = h0 + tid; h < h1; h += B) {
+                const int4 hv = hv_n;
+                const T hc[4] = {hc_n[0], hc_n[1], hc_n[2], hc_n[3]}, rest = rest_n;
+                if (h + B < h1) {
+                    hv_n = __ldg(tc.hv + h + B);
+                    ld4(tc.hc + 4 * (h + B), hc_n);
+                    rest_n = tc.hrest[h + B];
+                }
                 T R[3];
-                hinge_local(pos, nVp, tc.hv[h], tc.hc + 4 * h, tc.hrest[h], tc.kb, R, en, al);
+                hinge_local(pos, nVp, hv, hc, rest, tc.kb, R, en, al);
                 T *st = stash + 3 * (h - h0);
                 st[0] = R[0]; st[1] = R[1]; st[2] = R[2];
             }
