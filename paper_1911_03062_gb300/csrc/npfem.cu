@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -60,6 +61,8 @@ struct MeshTypeImpl {
     int *op = nullptr;
     int2 *oe = nullptr;
     int n_off = 0;
+    // vertex numbering: vpub[i] = caller's index of internal vertex i, vint its inverse
+    int *vpub = nullptr, *vint = nullptr;
     // fixed-width row table of the off-diagonal entries for the block-per-cell
     // residual (ell_W = 0: rows too long or too many vertices, CSR kernel)
     unsigned short *ell_col = nullptr;
@@ -259,6 +262,7 @@ IterArgs<T> make_args(npfem_ctx *ctx, MeshTypeImpl *t) {
     a.vn = t->vn;
     a.fptr = ctx->d_fslot;
     a.pub_off = t->pub_off;
+    a.vpub = t->vpub;
     a.minv = t->minv;
     a.yrel = (T *)t->yrel;
     a.origin = t->origin;
@@ -587,6 +591,64 @@ struct HostType {
     double V0 = 0;
 };
 
+// Internal vertex numbering: reverse Cuthill-McKee order of the vertex graph
+// (bandwidth-reducing), so the vertices a warp touches in the element loops
+// and vertex gathers have nearby indices, i.e. mostly distinct shared-memory
+// banks.  Start of each component: a pseudo-peripheral vertex (two rounds of
+// "minimum degree in the last BFS level"); ties by degree, then index.
+// Returns pub[i] = caller's index of internal vertex i.
+std::vector<int> rcm_order(int nV, int nT, const int32_t *tris) {
+    std::vector<std::vector<int>> adj(nV);
+    for (int t = 0; t < nT; ++t)
+        for (int k = 0; k < 3; ++k) {
+            const int a = tris[3 * t + k], b = tris[3 * t + (k + 1) % 3];
+            adj[a].push_back(b);
+            adj[b].push_back(a);
+        }
+    for (auto &l : adj) {
+        std::sort(l.begin(), l.end());
+        l.erase(std::unique(l.begin(), l.end()), l.end());
+    }
+    auto deg = [&](int v) { return (int)adj[v].size(); };
+    auto by_degree = [&](int a, int b) { return deg(a) != deg(b) ? deg(a) < deg(b) : a < b; };
+    std::vector<int> order, level(nV, -1);
+    order.reserve(nV);
+    std::vector<char> placed(nV, 0);
+    std::vector<int> q;
+    auto bfs_last_level_min = [&](int s) {
+        std::fill(level.begin(), level.end(), -1);
+        q.assign(1, s);
+        level[s] = 0;
+        for (size_t i = 0; i < q.size(); ++i)
+            for (int u : adj[q[i]])
+                if (level[u] < 0) { level[u] = level[q[i]] + 1; q.push_back(u); }
+        const int last = level[q.back()];
+        int best = -1;
+        for (int v : q)
+            if (level[v] == last && (best < 0 || by_degree(v, best))) best = v;
+        return best;
+    };
+    for (;;) {
+        int s = -1;
+        for (int v = 0; v < nV; ++v)
+            if (!placed[v] && (s < 0 || by_degree(v, s))) s = v;
+        if (s < 0) break;
+        s = bfs_last_level_min(bfs_last_level_min(s));
+        const size_t first = order.size();
+        order.push_back(s);
+        placed[s] = 1;
+        for (size_t i = first; i < order.size(); ++i) {
+            std::vector<int> nb;
+            for (int u : adj[order[i]])
+                if (!placed[u]) nb.push_back(u);
+            std::sort(nb.begin(), nb.end(), by_degree);
+            for (int u : nb) { placed[u] = 1; order.push_back(u); }
+        }
+    }
+    std::reverse(order.begin(), order.end());
+    return order;
+}
+
 // Validate the mesh and build the element constants:
 //   triangles: D_m^{-1} in the triangle's rest frame, rest area;
 //   hinges   : every edge shared by t1 = (a, b, c) and t2 = (b, a, d):
@@ -594,14 +656,16 @@ struct HostType {
 //              sqrt(3 / (A1 + A2)), rest |b|;
 //   incidence lists per vertex (sorted by element), rest volume, dense P.
 void build_host_type(npfem_ctx *ctx, int nV, const double *X, int nT, const int32_t *tris, const double *mass,
-                     const npfem_material &m, HostType &H) {
+                     const npfem_material &m, const int *vpub, const int *tpub, HostType &H) {
+    // vpub / tpub: the caller's number of each (internal) vertex / triangle, for messages
     auto P3 = [&](int i) { return V3{X[3 * i], X[3 * i + 1], X[3 * i + 2]}; };
     H.tri.assign(tris, tris + 3 * nT);
     for (int i = 0; i < 3 * nT; ++i)
         if (tris[i] < 0 || tris[i] >= nV) fail(ctx, NPFEM_EINVAL, "triangle index %d out of range", tris[i]);
     for (int t = 0; t < nT; ++t) {
         const int *v = &H.tri[3 * t];
-        if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2]) fail(ctx, NPFEM_EINVAL, "triangle %d repeats a vertex", t);
+        if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2])
+            fail(ctx, NPFEM_EINVAL, "triangle %d repeats a vertex", tpub[t]);
     }
     // half-edge twins
     std::unordered_map<long long, int> he;
@@ -610,11 +674,12 @@ void build_host_type(npfem_ctx *ctx, int nV, const double *X, int nT, const int3
         for (int k = 0; k < 3; ++k) {
             long long a = H.tri[3 * t + k], b = H.tri[3 * t + (k + 1) % 3];
             if (!he.emplace(a * nV + b, 3 * t + k).second)
-                fail(ctx, NPFEM_EINVAL, "edge (%lld,%lld) used twice with the same orientation", a, b);
+                fail(ctx, NPFEM_EINVAL, "edge (%d,%d) used twice with the same orientation", vpub[a], vpub[b]);
         }
     for (auto &kv : he) {
         long long a = kv.first / nV, b = kv.first % nV;
-        if (!he.count(b * nV + a)) fail(ctx, NPFEM_EINVAL, "open or inconsistently oriented mesh at edge (%lld,%lld)", a, b);
+        if (!he.count(b * nV + a))
+            fail(ctx, NPFEM_EINVAL, "open or inconsistently oriented mesh at edge (%d,%d)", vpub[a], vpub[b]);
     }
     // triangle constants
     H.dinv.resize(4 * nT);
@@ -624,7 +689,7 @@ void build_host_type(npfem_ctx *ctx, int nV, const double *X, int nT, const int3
         V3 E1 = sub(P3(v[1]), P3(v[0])), E2 = sub(P3(v[2]), P3(v[0]));
         V3 n = crs(E1, E2);
         double nn = nrm(n), l1 = nrm(E1), l2 = nrm(E2);
-        if (!(nn > 1e-14 * l1 * l2)) fail(ctx, NPFEM_EINVAL, "degenerate triangle %d", t);
+        if (!(nn > 1e-14 * l1 * l2)) fail(ctx, NPFEM_EINVAL, "degenerate triangle %d", tpub[t]);
         V3 u = {E1.x / l1, E1.y / l1, E1.z / l1};
         V3 nh = {n.x / nn, n.y / nn, n.z / nn};
         V3 w = crs(nh, u);
@@ -1118,8 +1183,35 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         }
         for (int i = 0; i < 3 * nV; ++i)
             if (!std::isfinite(rest_xyz[i])) fail(ctx, NPFEM_ENONFINITE, "non-finite rest position");
+        for (int i = 0; i < 3 * nT; ++i)
+            if (tris[i] < 0 || tris[i] >= nV) fail(ctx, NPFEM_EINVAL, "triangle index %d out of range", tris[i]);
+        // internal numbering: RCM vertex order; each triangle rotated (orientation kept)
+        // to start at its smallest internal index, triangles sorted by their indices
+        const std::vector<int> vpub = rcm_order(nV, nT, tris);
+        std::vector<int> intl(nV);
+        for (int i = 0; i < nV; ++i) intl[vpub[i]] = i;
+        std::vector<double> rest_i(3 * (size_t)nV), mass_i(nV);
+        for (int i = 0; i < nV; ++i) {
+            for (int c = 0; c < 3; ++c) rest_i[3 * i + c] = rest_xyz[3 * vpub[i] + c];
+            mass_i[i] = mass[vpub[i]];
+        }
+        std::vector<std::array<int, 3>> tr(nT);
+        for (int k = 0; k < nT; ++k) {
+            std::array<int, 3> a = {intl[tris[3 * k]], intl[tris[3 * k + 1]], intl[tris[3 * k + 2]]};
+            for (int r = 0; r < 2 && (a[0] > a[1] || a[0] > a[2]); ++r) a = {a[1], a[2], a[0]};
+            tr[k] = a;
+        }
+        std::vector<int> tpub(nT);
+        for (int k = 0; k < nT; ++k) tpub[k] = k;
+        std::stable_sort(tpub.begin(), tpub.end(), [&](int x, int y) { return tr[x] < tr[y]; });
+        std::vector<int32_t> tris_i(3 * (size_t)nT);
+        for (int k = 0; k < nT; ++k)
+            for (int j = 0; j < 3; ++j) tris_i[3 * k + j] = tr[tpub[k]][j];
+        mass.swap(mass_i);
         HostType H;
-        build_host_type(ctx, nV, rest_xyz, nT, tris, mass.data(), *mat, H);
+        build_host_type(ctx, nV, rest_i.data(), nT, tris_i.data(), mass.data(), *mat, vpub.data(), tpub.data(), H);
+        t->vpub = upload(ctx, vpub, t->owned);
+        t->vint = upload(ctx, intl, t->owned);
         t->nV = nV;
         t->nVp = (nV + 7) / 8 * 8;
         t->nT = nT;
@@ -1256,9 +1348,9 @@ int npfem_add_cells(npfem_ctx *ctx, int type_id, int n_cells, const double *x0, 
             if (v0) CK(cudaMemcpyAsync(sv, v0, total * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
             const long long n3 = 3ll * t->nVp;
             k_pub_to_soa<<<grid_for(n_cells * n3, 256, 8192), 256, 0, ctx->stream>>>(n_cells, t->nV, t->nVp, offs, sx,
-                                                                                   t->xn + t->ncells * n3);
+                                                                                   t->xn + t->ncells * n3, t->vpub);
             k_pub_to_soa<<<grid_for(n_cells * n3, 256, 8192), 256, 0, ctx->stream>>>(
-                n_cells, t->nV, t->nVp, offs, v0 ? sv : nullptr, t->vn + t->ncells * n3);
+                n_cells, t->nV, t->nVp, offs, v0 ? sv : nullptr, t->vn + t->ncells * n3, t->vpub);
             CK(cudaGetLastError());
             CK(cudaStreamSynchronize(ctx->stream));
         } catch (...) {
@@ -1334,7 +1426,7 @@ static int get_state(npfem_ctx *ctx, bool pos, double *out, size_t n, int on_dev
             if (!t->ncells) continue;
             long long tot = 3ll * t->nV * t->ncells;
             k_soa_to_pub<<<grid_for(tot, 256, 8192), 256, 0, ctx->stream>>>(t->ncells, t->nV, t->nVp, t->pub_off,
-                                                                            pos ? t->xn : t->vn, dst);
+                                                                            pos ? t->xn : t->vn, dst, t->vint);
         }
         CK(cudaGetLastError());
         if (!on_device) CK(cudaMemcpyAsync(out, ctx->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1364,7 +1456,7 @@ int npfem_set_state(npfem_ctx *ctx, const double *x, const double *v, size_t n) 
                 if (!t->ncells) continue;
                 long long tot = 3ll * t->nVp * t->ncells;
                 k_pub_to_soa<<<grid_for(tot, 256, 8192), 256, 0, ctx->stream>>>(
-                    t->ncells, t->nV, t->nVp, t->pub_off, src ? ctx->d_stage : nullptr, pass == 0 ? t->xn : t->vn);
+                    t->ncells, t->nV, t->nVp, t->pub_off, src ? ctx->d_stage : nullptr, pass == 0 ? t->xn : t->vn, t->vpub);
             }
             CK(cudaGetLastError());
             CK(cudaStreamSynchronize(ctx->stream));
@@ -1428,17 +1520,17 @@ int npfem_apply_pinv(npfem_ctx *ctx, int type_id, const double *q, double *z, in
         try {
             if (!mixed(ctx)) {
                 double *qi = dalloc<double>(ctx, nvec, &tmp), *zi = dalloc<double>(ctx, nvec, &tmp);
-                k_cols_in<double><<<grid_for(nvec, 256, 8192), 256, 0, ctx->stream>>>(n_cols, t->nV, t->nVp, q, qi, nullptr);
+                k_cols_in<double><<<grid_for(nvec, 256, 8192), 256, 0, ctx->stream>>>(n_cols, t->nV, t->nVp, q, qi, nullptr, t->vpub);
                 dim3 grid((t->nV + SG_T - 1) / SG_T, (rows + SG_T - 1) / SG_T);
                 k_gemm_simt<double><<<grid, 256, 0, ctx->stream>>>(rows, t->nV, t->nVp, qi, t->Pinv64, zi);
                 k_cols_out<double><<<grid_for((long long)n_cols * t->nV, 256, 8192), 256, 0, ctx->stream>>>(
-                    n_cols, t->nV, t->nVp, zi, z);
+                    n_cols, t->nV, t->nVp, zi, z, t->vint);
             } else {
                 float *qi = dalloc<float>(ctx, nvec, &tmp), *zi = dalloc<float>(ctx, nvec, &tmp);
                 __nv_bfloat16 *q16 = bf16(ctx) ? dalloc<__nv_bfloat16>(ctx, nvec, &tmp) : nullptr;
                 void *rl = dalloc<unsigned char>(ctx, nvec * (bf16(ctx) ? 2 : 4), &tmp);
                 int *conv = dalloc<int>(ctx, ncell, &tmp);
-                k_cols_in<float><<<grid_for(nvec, 256, 8192), 256, 0, ctx->stream>>>(n_cols, t->nV, t->nVp, q, qi, q16);
+                k_cols_in<float><<<grid_for(nvec, 256, 8192), 256, 0, ctx->stream>>>(n_cols, t->nV, t->nVp, q, qi, q16, t->vpub);
                 CUtensorMap mq = make_map(ctx, bf16(ctx) ? (const void *)q16 : qi, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
                 CUtensorMap mr = make_map(ctx, rl, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
                 gemm_tc(ctx, t, mq, rows, zi, 0, nullptr);
@@ -1448,7 +1540,7 @@ int npfem_apply_pinv(npfem_ctx *ctx, int type_id, const double *q, double *z, in
                 }
                 residual(ctx, t, ncell, qi, zi, nullptr, conv, ctx->opt.refine_max == 0, 1);
                 k_cols_out<float><<<grid_for((long long)n_cols * t->nV, 256, 8192), 256, 0, ctx->stream>>>(
-                    n_cols, t->nV, t->nVp, zi, z);
+                    n_cols, t->nV, t->nVp, zi, z, t->vint);
             }
             CK(cudaGetLastError());
             pending_error(ctx);
@@ -1531,15 +1623,15 @@ extern "C" int npfem_apply_pinv_noalloc(npfem_ctx *ctx, int type_id, const doubl
         }
         if (!mixed(ctx)) {
             k_cols_in<double><<<grid_for(nvec, 256, 8192), 256, 0, ctx->stream>>>(n_cols, t->nV, t->nVp, q,
-                                                                                (double *)qi, nullptr);
+                                                                                (double *)qi, nullptr, t->vpub);
             dim3 grid((t->nV + SG_T - 1) / SG_T, (rows + SG_T - 1) / SG_T);
             k_gemm_simt<double><<<grid, 256, 0, ctx->stream>>>(rows, t->nV, t->nVp, (const double *)qi, t->Pinv64,
                                                                (double *)zi);
             k_cols_out<double><<<grid_for((long long)n_cols * t->nV, 256, 8192), 256, 0, ctx->stream>>>(
-                n_cols, t->nV, t->nVp, (const double *)zi, z);
+                n_cols, t->nV, t->nVp, (const double *)zi, z, t->vint);
         } else {
             k_cols_in<float><<<grid_for(nvec, 256, 8192), 256, 0, ctx->stream>>>(n_cols, t->nV, t->nVp, q,
-                                                                               (float *)qi, q16);
+                                                                               (float *)qi, q16, t->vpub);
             CUtensorMap mq = make_map(ctx, bf16(ctx) ? (const void *)q16 : qi, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
             CUtensorMap mr = make_map(ctx, rl, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
             gemm_tc(ctx, t, mq, rows, (float *)zi, 0, nullptr);
@@ -1549,7 +1641,7 @@ extern "C" int npfem_apply_pinv_noalloc(npfem_ctx *ctx, int type_id, const doubl
             }
             residual(ctx, t, ncell, (const float *)qi, (const float *)zi, nullptr, conv, ctx->opt.refine_max == 0, 1);
             k_cols_out<float><<<grid_for((long long)n_cols * t->nV, 256, 8192), 256, 0, ctx->stream>>>(
-                n_cols, t->nV, t->nVp, (const float *)zi, z);
+                n_cols, t->nV, t->nVp, (const float *)zi, z, t->vint);
         }
         CK(cudaGetLastError());
         pending_error(ctx);

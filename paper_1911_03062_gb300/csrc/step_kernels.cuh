@@ -23,6 +23,7 @@ struct IterArgs {
     double *xn, *vn;              // state, FP64 SoA
     const double *const *fptr;    // device slot holding the f_ext base (public layout)
     const long long *pub_off;     // [cell] offset of the cell in the public arrays (doubles)
+    const int *vpub;              // [nV] the caller's index of internal vertex v
     const double *minv;           // [nV] 1 / m_v
     T *yrel;                      // y - origin
     double *origin;               // [cell][3]
@@ -103,7 +104,7 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
             const int v = v0 + i;
             if (v >= nV) continue;
             xo[4 * g + i] = xv[i];
-            y[4 * g + i] = xv[i] + a.h * vv[i] + a.h * a.h * a.minv[v] * f[3 * v + c];
+            y[4 * g + i] = xv[i] + a.h * vv[i] + a.h * a.h * a.minv[v] * f[3 * a.vpub[v] + c];
         }
     }
 }
@@ -633,49 +634,51 @@ __global__ void k_axpy_unconverged(int ncells, int n3, float *z, const float *dz
 }
 
 // public [cell][nV][3] (FP64) <-> internal SoA [cell][3][nVp]
+// vpub[v]: the caller's index of internal vertex v (vint: the inverse)
 __global__ void k_pub_to_soa(int ncells, int nV, int nVp, const long long *pub_off, const double *src,
-                             double *dst) {
+                             double *dst, const int *vpub) {
     const int n3 = 3 * nVp;
     long long total = (long long)ncells * n3;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         int cell = (int)(i / n3), e = (int)(i - (long long)cell * n3), v;
         int c = elem_cv(e, nVp, v);
-        dst[i] = v < nV ? (src ? src[pub_off[cell] + 3 * v + c] : 0.0) : 0.0;
+        dst[i] = v < nV ? (src ? src[pub_off[cell] + 3 * vpub[v] + c] : 0.0) : 0.0;
     }
 }
 
 __global__ void k_soa_to_pub(int ncells, int nV, int nVp, const long long *pub_off, const double *src,
-                             double *dst) {
+                             double *dst, const int *vint) {
     long long total = (long long)ncells * nV * 3;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         int cell = (int)(i / (3 * nV)), k = (int)(i - (long long)cell * 3 * nV);
         int v = k / 3, c = k - 3 * v;
-        dst[pub_off[cell] + k] = src[(long long)cell * 3 * nVp + c * nVp + v];
+        dst[pub_off[cell] + k] = src[(long long)cell * 3 * nVp + c * nVp + vint[v]];
     }
 }
 
 // internal SoA (T) [rows][nVp] <-> FP64 column block [rows][nV] (apply entry)
 template <typename T>
-__global__ void k_cols_in(int rows, int nV, int nVp, const double *src, T *dst, __nv_bfloat16 *dst16) {
+__global__ void k_cols_in(int rows, int nV, int nVp, const double *src, T *dst, __nv_bfloat16 *dst16,
+                          const int *vpub) {
     long long total = (long long)rows * nVp;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         int r = (int)(i / nVp), v = (int)(i - (long long)r * nVp);
-        double x = v < nV ? src[(long long)r * nV + v] : 0.0;
+        double x = v < nV ? src[(long long)r * nV + vpub[v]] : 0.0;
         dst[i] = T(x);
         if (dst16) dst16[i] = __float2bfloat16_rn((float)x);
     }
 }
 
 template <typename T>
-__global__ void k_cols_out(int rows, int nV, int nVp, const T *src, double *dst) {
+__global__ void k_cols_out(int rows, int nV, int nVp, const T *src, double *dst, const int *vint) {
     long long total = (long long)rows * nV;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         int r = (int)(i / nV), v = (int)(i - (long long)r * nV);
-        dst[i] = (double)src[(long long)r * nVp + v];
+        dst[i] = (double)src[(long long)r * nVp + vint[v]];
     }
 }
 

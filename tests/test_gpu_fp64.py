@@ -151,3 +151,25 @@ def test_errors():
     with pytest.raises(NpfemError) as e:
         s.add_cells(tid, np.full((1, 4, 3), np.inf))
     assert e.value.code == ENONFINITE
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_vertex_numbering_is_internal(precision):
+    # the library renumbers vertices internally; a caller's relabelling of the
+    # same cells (vertices shuffled, triangles rotated and reordered) gives the
+    # same public result up to rounding
+    rng = np.random.default_rng(7)
+    base = I.rbc_type()
+    g = I.materialise(I.Group(base, 5, seed=11, amp=0.3))
+    perm = rng.permutation(base.nV)                        # new label k <- old vertex perm[k]
+    new_of_old = np.empty_like(perm)
+    new_of_old[perm] = np.arange(base.nV)
+    tris = new_of_old[base.tris]
+    tris = np.roll(tris, 1, axis=1)[rng.permutation(len(tris))].astype(np.int32)
+    relabelled = I.MeshType("rbc_relabelled", base.rest[perm], tris, base.material, base.radius)
+    g2 = I.Group(relabelled, 5, seed=11, amp=0.3)
+    g2.x0, g2.v0, g2.f_ext = g.x0[:, perm], g.v0[:, perm], g.f_ext[:, perm]
+    xa, _, _ = run_gpu([g], 3, precision=precision)
+    xb, _, _ = run_gpu([g2], 3, precision=precision)
+    err = np.abs(xa[0] - xb[0][:, new_of_old]).max() / base.radius
+    assert err <= (1e-12 if precision == "fp64" else 1e-6)
