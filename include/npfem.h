@@ -73,6 +73,11 @@ typedef struct {
     int residual_fp64;      /* mixed forms: refinement residual with FP64 arithmetic (1) or with exact
                                FP32 fused multiply-adds on a float-pair diagonal (0, default); both
                                evaluate q - diag(P) z without cancellation error */
+    int refine_split;       /* BF16 form: refinement corrections with P^{-1} and r each split into
+                               a BF16 high part and a BF16 low part, three tensor-core products
+                               (r_hi P_hi + r_lo P_hi + r_hi P_lo) accumulated in FP32, so one
+                               correction reduces the residual ~100x further than a plain BF16
+                               one (1, default); plain BF16 corrections (0) */
 } npfem_options;
 
 /* Material and time step of one mesh type.  Element weights follow the

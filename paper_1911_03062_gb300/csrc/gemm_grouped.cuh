@@ -2,6 +2,10 @@
 // tcgen05 launch:  Z_p[r][v] (+)= sum_k Q_p[r][k] * Pinv_p[v][k]  for every
 // problem p (one mesh type: its stacked right-hand sides and its inverse).
 //
+// Split form (BF16): each stage also carries the low parts of both operands
+// and the accumulator takes Q_hi P_hi + Q_lo P_hi + Q_hi P_lo (~16-bit
+// operands, FP32 accumulation) for the refinement corrections.
+//
 // Work units are (problem, 128-row tile, N tile) triples, numbered problem by
 // problem; each block (one per SM) takes units blockIdx.x, + gridDim.x, ...
 // Roles (192 threads): warp 0 issues TMA loads of both operands through an
@@ -32,10 +36,13 @@ struct GroupProblem {
 struct GroupMaps {
     CUtensorMap q[MAXG];
     CUtensorMap p[MAXG];
+    CUtensorMap q_lo[MAXG];   // split products only: low BF16 parts of Q and P^{-1}
+    CUtensorMap p_lo[MAXG];
 };
 
 struct GroupArgs {
     int nprob, total_units, stages, accumulate, stage_bytes_b;   // B-tile bytes per stage (max n_tile)
+    int split;   // 1: Z (+)= Q_hi P_hi + Q_lo P_hi + Q_hi P_lo (BF16 parts, FP32 accumulation)
     GroupProblem pr[MAXG];
     DevStatus *st;
 };
@@ -77,8 +84,10 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped(const __grid_constant__
     uint32_t base = smem_u32(smem_g);
     uint32_t pad = ((base + 1023u) & ~1023u) - base;
     uint8_t *tiles = smem_g + pad;
+    // stage: A_hi | B_hi (| A_lo | B_lo when split); every tile 1024-byte aligned
     const uint32_t a_bytes = BM * KB_BYTES;
-    const uint32_t stage_bytes = a_bytes + (uint32_t)a.stage_bytes_b;
+    const uint32_t half_bytes = a_bytes + (uint32_t)a.stage_bytes_b;
+    const uint32_t stage_bytes = half_bytes * (a.split ? 2u : 1u);
     uint64_t *full = reinterpret_cast<uint64_t *>(tiles + (size_t)a.stages * stage_bytes);
     uint64_t *empty = full + a.stages;
     uint64_t *tfull = empty + a.stages;      // [2]
@@ -110,7 +119,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped(const __grid_constant__
                 const Unit w = decode_unit(a, u);
                 if (unit_skipped(a, w)) continue;
                 const GroupProblem &P = a.pr[w.p];
-                const uint32_t bytes = a_bytes + (uint32_t)P.n_tile * KB_BYTES;
+                const uint32_t bytes = (a_bytes + (uint32_t)P.n_tile * KB_BYTES) * (a.split ? 2u : 1u);
                 for (int kb = 0; kb < P.kblocks; ++kb, ++it) {
                     const int s = (int)(it % a.stages);
                     const uint32_t round = (uint32_t)(it / a.stages);
@@ -123,6 +132,11 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped(const __grid_constant__
                     mbar_expect_tx(&full[s], bytes);
                     tma_load_2d(sa, &maps.q[w.p], &full[s], kb * k_per_block, w.mt * BM);
                     tma_load_2d(sa + a_bytes, &maps.p[w.p], &full[s], kb * k_per_block, w.nt * P.n_tile);
+                    if (a.split) {
+                        tma_load_2d(sa + half_bytes, &maps.q_lo[w.p], &full[s], kb * k_per_block, w.mt * BM);
+                        tma_load_2d(sa + half_bytes + a_bytes, &maps.p_lo[w.p], &full[s], kb * k_per_block,
+                                    w.nt * P.n_tile);
+                    }
                     last_phase[s] = round & 1;
                 }
             }
@@ -163,6 +177,14 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped(const __grid_constant__
                     for (int k = 0; k < 4; ++k)
                         mma<TF32>(d_tmem, desc_sw128(sa + 32 * k), desc_sw128(sb + 32 * k), idesc,
                                   (kb > 0 || k > 0) ? 1u : 0u);
+                    if (a.split) {
+                        const uint32_t sal = sa + half_bytes, sbl = sal + a_bytes;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            mma<TF32>(d_tmem, desc_sw128(sal + 32 * k), desc_sw128(sb + 32 * k), idesc, 1u);
+                            mma<TF32>(d_tmem, desc_sw128(sa + 32 * k), desc_sw128(sbl + 32 * k), idesc, 1u);
+                        }
+                    }
                     mma_commit(&empty[s]);
                 }
                 if (!ok) break;

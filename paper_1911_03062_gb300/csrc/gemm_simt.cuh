@@ -5,7 +5,7 @@
 //   * k_gj_*      : in-place Gauss-Jordan inversion of the SPD matrix P in FP64,
 //                   one pivot per launch pair (no pivoting: P is SPD and strongly
 //                   diagonally dominant through M/h^2);
-//   * k_convert_pinv : FP64 inverse -> FP32 / BF16 operand copies.
+//   * k_convert_pinv : FP64 inverse -> FP32 / BF16 (high and low part) operand copies.
 #pragma once
 
 #include "common.cuh"
@@ -89,7 +89,8 @@ __global__ void k_gj_update(int n, int k, double *A, const double *rowk, const d
 }
 
 // dense n x n FP64 -> padded [n][nVp] copies (FP64, FP32, BF16; null = skip)
-__global__ void k_convert_pinv(int n, int nVp, const double *A, double *P64, float *P32, __nv_bfloat16 *P16) {
+__global__ void k_convert_pinv(int n, int nVp, const double *A, double *P64, float *P32, __nv_bfloat16 *P16,
+                               __nv_bfloat16 *P16lo) {
     long long total = (long long)n * nVp;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -98,6 +99,10 @@ __global__ void k_convert_pinv(int n, int nVp, const double *A, double *P64, flo
         if (P64) P64[idx] = v;
         if (P32) P32[idx] = (float)v;
         if (P16) P16[idx] = __float2bfloat16_rn((float)v);
+        if (P16lo) {   // low part: v - hi, rounded to BF16 (hi + lo carries ~16 bits)
+            const double hi = (double)__bfloat162float(__float2bfloat16_rn((float)v));
+            P16lo[idx] = __float2bfloat16_rn((float)(v - hi));
+        }
     }
 }
 

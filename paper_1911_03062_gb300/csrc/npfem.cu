@@ -56,6 +56,7 @@ struct MeshTypeImpl {
     double *Pinv64 = nullptr;
     float *Pinv32 = nullptr;
     __nv_bfloat16 *Pinv16 = nullptr;
+    __nv_bfloat16 *Pinv16lo = nullptr;          // split corrections: BF16 low part of P^{-1}
     double *diag = nullptr, *minv = nullptr;
     float *dhi = nullptr, *dlo = nullptr;
     int *op = nullptr;
@@ -70,7 +71,7 @@ struct MeshTypeImpl {
     int ell_W = 0, ell_KR = 0, ell_nt = 0, ell_grid = 0;
     // tensor-core GEMM configuration
     int n_tile = 0, stages = 0;
-    CUtensorMap mapP{};
+    CUtensorMap mapP{}, mapPlo{};
     // cells
     int ncells = 0, cap = 0;
     std::vector<long long> pub_off_h;
@@ -78,10 +79,11 @@ struct MeshTypeImpl {
     double *xn = nullptr, *vn = nullptr;        // state SoA FP64
     void *yrel = nullptr, *delta = nullptr, *grad = nullptr, *q = nullptr, *z = nullptr;
     void *S = nullptr, *Y = nullptr, *rlo = nullptr;
+    __nv_bfloat16 *rlo_lo = nullptr;             // split corrections: BF16 low part of r
     __nv_bfloat16 *q16 = nullptr;
     double *origin = nullptr, *rho = nullptr, *alpha = nullptr, *M = nullptr, *g = nullptr, *allow = nullptr;
     int *hcount = nullptr, *hhead = nullptr, *conv = nullptr, *fb_list = nullptr, *fb_count = nullptr;
-    CUtensorMap mapQ{}, mapR{};
+    CUtensorMap mapQ{}, mapR{}, mapRlo{};
     int ept = 8, block = 256, stash_T = 0;
     size_t smem_step = 0;
 };
@@ -328,8 +330,8 @@ void run_iterate(npfem_ctx *ctx, MeshTypeImpl *t, int last, bool fallback) {
 }
 
 // --- global step: z = P^{-1} q for the stacked rows of every type (one grouped launch)
-size_t grouped_smem(int stages, int max_ntile) {
-    return 1024 + (size_t)stages * (tc::BM + max_ntile) * tc::KB_BYTES + (2 * stages + 4) * 8 + 16;
+size_t grouped_smem(int stages, int max_ntile, bool split = false) {
+    return 1024 + (size_t)stages * (tc::BM + max_ntile) * tc::KB_BYTES * (split ? 2 : 1) + (2 * stages + 4) * 8 + 16;
 }
 size_t gemm_smem(const MeshTypeImpl *t) { return grouped_smem(t->stages, t->n_tile); }
 
@@ -352,6 +354,8 @@ ResidEllFn resid_ell_fn(int W, int KR) {
 }
 
 size_t resid_ell_smem(int nVp) { return (size_t)RESID_STAGES * 2 * 3 * nVp * sizeof(float); }
+
+bool split(const npfem_ctx *ctx) { return bf16(ctx) && ctx->opt.refine_split; }
 
 void set_kernel_attrs(npfem_ctx *ctx) {
     int mx = 0;
@@ -385,10 +389,11 @@ struct GemmItem {
     int rows;
     float *Z;
     const int *conv;
+    const CUtensorMap *mapQlo = nullptr;   // split form: low part of Q (P's low part from the type)
 };
 
 // One persistent launch (per MAXG items) over every item's (row tile, N tile) units.
-void gemm_group(npfem_ctx *ctx, const std::vector<GemmItem> &items, int accumulate) {
+void gemm_group(npfem_ctx *ctx, const std::vector<GemmItem> &items, int accumulate, bool split_form = false) {
     for (size_t i0 = 0; i0 < items.size(); i0 += tc::MAXG) {
         const size_t i1 = std::min(items.size(), i0 + tc::MAXG);
         tc::GroupArgs g{};
@@ -410,19 +415,24 @@ void gemm_group(npfem_ctx *ctx, const std::vector<GemmItem> &items, int accumula
             units += P.m_tiles * P.n_ntiles;
             maps.q[g.nprob] = *it.mapQ;
             maps.p[g.nprob] = it.t->mapP;
+            if (split_form) {
+                maps.q_lo[g.nprob] = *it.mapQlo;
+                maps.p_lo[g.nprob] = it.t->mapPlo;
+            }
             max_nt = std::max(max_nt, it.t->n_tile);
             if (it.rows > best_rows) { best_rows = it.rows; stages = it.t->stages; }
             ++g.nprob;
         }
         if (!units) continue;
-        while (stages > 2 && grouped_smem(stages, max_nt) + 2048 > (size_t)ctx->smem_optin) --stages;
+        while (stages > 2 && grouped_smem(stages, max_nt, split_form) + 2048 > (size_t)ctx->smem_optin) --stages;
         g.total_units = units;
         g.stages = stages;
         g.accumulate = accumulate;
+        g.split = split_form ? 1 : 0;
         g.stage_bytes_b = max_nt * tc::KB_BYTES;
         g.st = ctx->d_st;
         const int grid = std::min(units, ctx->nsm);
-        const size_t smem = grouped_smem(stages, max_nt);
+        const size_t smem = grouped_smem(stages, max_nt, split_form);
         prof_begin(ctx, accumulate ? NPFEM_K_GEMM_REFINE : NPFEM_K_GEMM);
         if (bf16(ctx)) tc::k_gemm_grouped<false><<<grid, 192, smem, ctx->stream>>>(maps, g);
         else tc::k_gemm_grouped<true><<<grid, 192, smem, ctx->stream>>>(maps, g);
@@ -432,12 +442,12 @@ void gemm_group(npfem_ctx *ctx, const std::vector<GemmItem> &items, int accumula
 }
 
 void gemm_tc(npfem_ctx *ctx, MeshTypeImpl *t, const CUtensorMap &mapQ, int rows, float *Z, int accumulate,
-             const int *conv) {
-    gemm_group(ctx, {GemmItem{t, &mapQ, rows, Z, conv}}, accumulate);
+             const int *conv, const CUtensorMap *mapQlo = nullptr) {
+    gemm_group(ctx, {GemmItem{t, &mapQ, rows, Z, conv, mapQlo}}, accumulate, mapQlo != nullptr);
 }
 
 void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, const float *z, void *r,
-              int *conv, int first, int final_pass) {
+              int *conv, int first, int final_pass, __nv_bfloat16 *r_lo = nullptr) {
     ResidArgs a{};
     a.ncells = rows_cells;
     a.nV = t->nV;
@@ -454,6 +464,7 @@ void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, c
     a.z = z;
     a.r_bf16 = bf16(ctx) ? (__nv_bfloat16 *)r : nullptr;
     a.r_f32 = bf16(ctx) ? nullptr : (float *)r;
+    a.r_lo = r_lo;
     a.conv = conv;
     a.any_active = ctx->d_any;
     a.st = ctx->d_st;
@@ -474,6 +485,7 @@ void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, c
         e.z = z;
         e.r_bf16 = a.r_bf16;
         e.r_f32 = a.r_f32;
+        e.r_lo = r_lo;
         e.conv = conv;
         e.any_active = ctx->d_any;
         e.st = ctx->d_st;
@@ -516,14 +528,15 @@ void apply_all(npfem_ctx *ctx) {
     for (auto *t : ctx->types) {
         if (!t->ncells) continue;
         first.push_back(GemmItem{t, &t->mapQ, 3 * t->ncells, (float *)t->z, nullptr});
-        corr.push_back(GemmItem{t, &t->mapR, 3 * t->ncells, (float *)t->z, t->conv});
+        corr.push_back(GemmItem{t, &t->mapR, 3 * t->ncells, (float *)t->z, t->conv, split(ctx) ? &t->mapRlo : nullptr});
     }
     gemm_group(ctx, first, 0);
     for (int s = 0; s < ctx->opt.refine_max; ++s) {
         for (auto *t : ctx->types)
             if (t->ncells)
-                residual(ctx, t, t->ncells, (const float *)t->q, (const float *)t->z, t->rlo, t->conv, s == 0, 0);
-        gemm_group(ctx, corr, 1);
+                residual(ctx, t, t->ncells, (const float *)t->q, (const float *)t->z, t->rlo, t->conv, s == 0, 0,
+                         t->rlo_lo);
+        gemm_group(ctx, corr, 1, split(ctx));
     }
     for (auto *t : ctx->types)
         if (t->ncells)
@@ -905,8 +918,10 @@ void invert_on_gpu(npfem_ctx *ctx, MeshTypeImpl *t, const std::vector<double> &P
         t->Pinv64 = dalloc<double>(ctx, (size_t)n * t->nVp, &t->owned);
         if (mixed(ctx)) t->Pinv32 = dalloc<float>(ctx, (size_t)n * t->nVp, &t->owned);
         if (bf16(ctx)) t->Pinv16 = dalloc<__nv_bfloat16>(ctx, (size_t)n * t->nVp, &t->owned);
+        if (split(ctx)) t->Pinv16lo = dalloc<__nv_bfloat16>(ctx, (size_t)n * t->nVp, &t->owned);
         k_convert_pinv<<<grid_for((long long)n * t->nVp, 256, 4096), 256, 0, ctx->stream>>>(n, t->nVp, A, t->Pinv64,
-                                                                                          t->Pinv32, t->Pinv16);
+                                                                                          t->Pinv32, t->Pinv16,
+                                                                                          t->Pinv16lo);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(ctx->stream));
     } catch (...) {
@@ -941,6 +956,7 @@ void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
         t->n_tile = nt;
         t->stages = st;
         t->mapP = make_map(ctx, pb, bf16(ctx), t->nV, t->nV, t->nVp, nt);
+        if (t->Pinv16lo) t->mapPlo = make_map(ctx, t->Pinv16lo, true, t->nV, t->nV, t->nVp, nt);
     };
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1012,7 +1028,7 @@ void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
 
 void free_cells(MeshTypeImpl *t) {
     void **bufs[] = {(void **)&t->pub_off, (void **)&t->xn, (void **)&t->vn, &t->yrel, &t->delta, &t->grad, &t->q,
-                     &t->z, &t->S, &t->Y, &t->rlo, (void **)&t->q16, (void **)&t->origin, (void **)&t->rho,
+                     &t->z, &t->S, &t->Y, &t->rlo, (void **)&t->rlo_lo, (void **)&t->q16, (void **)&t->origin, (void **)&t->rho,
                      (void **)&t->alpha, (void **)&t->M, (void **)&t->g, (void **)&t->allow, (void **)&t->hcount,
                      (void **)&t->hhead, (void **)&t->conv, (void **)&t->fb_list, (void **)&t->fb_count};
     for (void **b : bufs) dfree(*b);
@@ -1031,6 +1047,7 @@ void alloc_cells(npfem_ctx *ctx, MeshTypeImpl *t, int cap) {
     t->Y = dalloc<unsigned char>(ctx, cap * n3 * es * m);
     t->q16 = bf16(ctx) ? dalloc<__nv_bfloat16>(ctx, cap * n3) : nullptr;
     t->rlo = mixed(ctx) ? dalloc<unsigned char>(ctx, cap * n3 * (bf16(ctx) ? 2 : 4)) : nullptr;
+    t->rlo_lo = split(ctx) ? dalloc<__nv_bfloat16>(ctx, cap * n3) : nullptr;
     t->origin = dalloc<double>(ctx, 3 * (size_t)cap);
     t->rho = dalloc<double>(ctx, m * cap);
     t->alpha = dalloc<double>(ctx, m * cap);
@@ -1052,6 +1069,7 @@ void alloc_cells(npfem_ctx *ctx, MeshTypeImpl *t, int cap) {
     if (mixed(ctx)) {
         t->mapQ = make_map(ctx, bf16(ctx) ? (const void *)t->q16 : t->q, bf16(ctx), t->nV, 3ll * cap, t->nVp, tc::BM);
         t->mapR = make_map(ctx, t->rlo, bf16(ctx), t->nV, 3ll * cap, t->nVp, tc::BM);
+        if (split(ctx)) t->mapRlo = make_map(ctx, t->rlo_lo, true, t->nV, 3ll * cap, t->nVp, tc::BM);
     }
 }
 
@@ -1098,6 +1116,7 @@ void npfem_default_options(npfem_options *o) {
     o->cuda_stream = nullptr;
     o->autotune_cache = nullptr;
     o->residual_fp64 = 0;
+    o->refine_split = 1;
 }
 
 int npfem_create(const npfem_options *opt, npfem_ctx **out) {
@@ -1529,14 +1548,17 @@ int npfem_apply_pinv(npfem_ctx *ctx, int type_id, const double *q, double *z, in
                 float *qi = dalloc<float>(ctx, nvec, &tmp), *zi = dalloc<float>(ctx, nvec, &tmp);
                 __nv_bfloat16 *q16 = bf16(ctx) ? dalloc<__nv_bfloat16>(ctx, nvec, &tmp) : nullptr;
                 void *rl = dalloc<unsigned char>(ctx, nvec * (bf16(ctx) ? 2 : 4), &tmp);
+                __nv_bfloat16 *rlo = split(ctx) ? dalloc<__nv_bfloat16>(ctx, nvec, &tmp) : nullptr;
                 int *conv = dalloc<int>(ctx, ncell, &tmp);
                 k_cols_in<float><<<grid_for(nvec, 256, 8192), 256, 0, ctx->stream>>>(n_cols, t->nV, t->nVp, q, qi, q16, t->vpub);
                 CUtensorMap mq = make_map(ctx, bf16(ctx) ? (const void *)q16 : qi, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
                 CUtensorMap mr = make_map(ctx, rl, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
+                CUtensorMap mrl{};
+                if (rlo) mrl = make_map(ctx, rlo, true, t->nV, rows, t->nVp, tc::BM);
                 gemm_tc(ctx, t, mq, rows, zi, 0, nullptr);
                 for (int s = 0; s < ctx->opt.refine_max; ++s) {
-                    residual(ctx, t, ncell, qi, zi, rl, conv, s == 0, 0);
-                    gemm_tc(ctx, t, mr, rows, zi, 1, conv);
+                    residual(ctx, t, ncell, qi, zi, rl, conv, s == 0, 0, rlo);
+                    gemm_tc(ctx, t, mr, rows, zi, 1, conv, rlo ? &mrl : nullptr);
                 }
                 residual(ctx, t, ncell, qi, zi, nullptr, conv, ctx->opt.refine_max == 0, 1);
                 k_cols_out<float><<<grid_for((long long)n_cols * t->nV, 256, 8192), 256, 0, ctx->stream>>>(
@@ -1600,16 +1622,18 @@ extern "C" int npfem_apply_pinv_noalloc(npfem_ctx *ctx, int type_id, const doubl
                  n_cols, t->nV, nvec, t->nVp, (int)NPFEM_NOALLOC_MAX_ELEMS);
         unsigned char *base = (unsigned char *)noalloc_scratch(ctx);
         const size_t es = esize(ctx);
-        // carve: q, z (solver type), then the BF16 copy of q and the refinement operand, then flags
+        // carve: q, z (solver type), then the BF16 copy of q, the refinement operand (and its
+        // low part for split corrections), then flags: at most 16 bytes per element
         size_t off = 0;
         void *qi = base + off;  off += up256(nvec * es);
         void *zi = base + off;  off += up256(nvec * es);
-        __nv_bfloat16 *q16 = nullptr;
+        __nv_bfloat16 *q16 = nullptr, *rlo = nullptr;
         void *rl = nullptr;
         int *conv = nullptr;
         if (mixed(ctx)) {
             if (bf16(ctx)) { q16 = (__nv_bfloat16 *)(base + off); off += up256(nvec * 2); }
             rl = base + off;  off += up256(nvec * (bf16(ctx) ? 2 : 4));
+            if (split(ctx)) { rlo = (__nv_bfloat16 *)(base + off); off += up256(nvec * 2); }
             conv = (int *)(base + off);  off += up256((size_t)ncell * sizeof(int));
         }
         if (off > NPFEM_NOALLOC_SCRATCH_BYTES) fail(ctx, NPFEM_EINVAL, "scratch layout overflow");
@@ -1634,10 +1658,12 @@ extern "C" int npfem_apply_pinv_noalloc(npfem_ctx *ctx, int type_id, const doubl
                                                                                (float *)qi, q16, t->vpub);
             CUtensorMap mq = make_map(ctx, bf16(ctx) ? (const void *)q16 : qi, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
             CUtensorMap mr = make_map(ctx, rl, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
+            CUtensorMap mrl{};
+            if (rlo) mrl = make_map(ctx, rlo, true, t->nV, rows, t->nVp, tc::BM);
             gemm_tc(ctx, t, mq, rows, (float *)zi, 0, nullptr);
             for (int s = 0; s < ctx->opt.refine_max; ++s) {
-                residual(ctx, t, ncell, (const float *)qi, (const float *)zi, rl, conv, s == 0, 0);
-                gemm_tc(ctx, t, mr, rows, (float *)zi, 1, conv);
+                residual(ctx, t, ncell, (const float *)qi, (const float *)zi, rl, conv, s == 0, 0, rlo);
+                gemm_tc(ctx, t, mr, rows, (float *)zi, 1, conv, rlo ? &mrl : nullptr);
             }
             residual(ctx, t, ncell, (const float *)qi, (const float *)zi, nullptr, conv, ctx->opt.refine_max == 0, 1);
             k_cols_out<float><<<grid_for((long long)n_cols * t->nV, 256, 8192), 256, 0, ctx->stream>>>(

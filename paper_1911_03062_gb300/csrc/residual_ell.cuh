@@ -32,7 +32,8 @@ struct ResidEllArgs {
     const unsigned short *ell_col;   // [W][nVp] column of slot w of row v
     const float *ell_val;            // [W][nVp] value of slot w of row v
     const float *q, *z;              // [cell][3][nVp]
-    __nv_bfloat16 *r_bf16;           // BF16 form
+    __nv_bfloat16 *r_bf16;           // BF16 form (high part when r_lo is set)
+    __nv_bfloat16 *r_lo;             // split corrections: r - r_hi in BF16, or null
     float *r_f32;                    // TF32 form
     int *conv;                       // [cell]
     int *any_active;
@@ -146,8 +147,13 @@ __global__ void __launch_bounds__(RESID_MAX_THREADS, (KR * W <= 24) ? 3 : 2) k_r
             if (!a.final_pass) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    if (a.r_bf16) a.r_bf16[base + c * nVp + v] = __float2bfloat16_rn(r[c]);
-                    else a.r_f32[base + c * nVp + v] = r[c];
+                    if (a.r_bf16) {
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(r[c]);
+                        a.r_bf16[base + c * nVp + v] = hi;
+                        if (a.r_lo) a.r_lo[base + c * nVp + v] = __float2bfloat16_rn(r[c] - __bfloat162float(hi));
+                    } else {
+                        a.r_f32[base + c * nVp + v] = r[c];
+                    }
                 }
             }
         }

@@ -38,7 +38,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("iters", C.c_int), ("history", C.c_int),
                 ("armijo_c1", C.c_double), ("max_backtracks", C.c_int), ("refine_tol", C.c_double),
                 ("refine_max", C.c_int), ("use_graph", C.c_int), ("device", C.c_int),
-                ("cuda_stream", C.c_void_p), ("autotune_cache", C.c_char_p), ("residual_fp64", C.c_int)]
+                ("cuda_stream", C.c_void_p), ("autotune_cache", C.c_char_p), ("residual_fp64", C.c_int),
+                ("refine_split", C.c_int)]
 
 
 class Material(C.Structure):
@@ -132,7 +133,8 @@ class Solver:
     """One npFEM context: mesh types, cells, and the time step on one GPU."""
 
     def __init__(self, precision="fp64", iters=10, history=5, armijo_c1=1e-4, max_backtracks=8,
-                 refine_tol=1e-6, refine_max=3, use_graph=True, device=0, stream=None, residual_fp64=False):
+                 refine_tol=1e-6, refine_max=3, use_graph=True, device=0, stream=None, residual_fp64=False,
+                 refine_split=True):
         self._L = load()
         o = default_options()
         o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -140,6 +142,7 @@ class Solver:
         o.max_backtracks, o.refine_tol, o.refine_max = max_backtracks, refine_tol, refine_max
         o.use_graph, o.device = int(bool(use_graph)), device
         o.residual_fp64 = int(bool(residual_fp64))
+        o.refine_split = int(bool(refine_split))
         if stream is not None:
             o.cuda_stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         self.precision = o.precision

@@ -19,15 +19,22 @@ def built():
     G.build()
 
 
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def _solver(prec, **kw):
+    # "bf16-plain": BF16 form with plain (unsplit) refinement corrections
+    from paper_1911_03062_gb300.npfem import Solver
+    if prec == "bf16-plain":
+        return Solver(precision="bf16", refine_split=False, **kw)
+    return Solver(precision=prec, **kw)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16-plain", "tf32"])
 def test_apply_pinv_tensor_cores(prec):
     # z = P^{-1} q on tcgen05 + refinement vs the exact FP64 solve; 131 columns
     # (two 128-row tiles, ragged), both mesh sizes (three 224-wide N tiles / one)
     import torch
     from oracle import oracle as O
-    from paper_1911_03062_gb300.npfem import Solver
     for mt in (I.rbc_type(), I.plt_type()):
-        s = Solver(precision=prec)
+        s = _solver(prec)
         tid = s.create_type(mt)
         P = O.OracleType.from_mesh_type(mt).P_dense()
         q = np.random.default_rng(7).standard_normal((131, mt.nV))
@@ -60,10 +67,32 @@ def test_unrefined_apply_is_low_precision(prec):
     assert 1e-6 < resid < (2e-2 if prec == "bf16" else 5e-3), resid
 
 
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_split_correction_gains_two_orders():
+    # one refinement sweep: the split BF16 correction (hi/lo parts of r and
+    # P^{-1}, three products) leaves a residual far below the plain one's
+    import torch
+    from oracle import oracle as O
+    mt = I.rbc_type()
+    P = O.OracleType.from_mesh_type(mt).P_dense()
+    q = np.random.default_rng(9).standard_normal((96, mt.nV))
+    res = {}
+    for prec in ("bf16", "bf16-plain"):
+        s = _solver(prec, refine_max=1)
+        tid = s.create_type(mt)
+        z = s.apply_pinv(tid, torch.tensor(q, device="cuda"),
+                         torch.empty((96, mt.nV), dtype=torch.float64, device="cuda")).cpu().numpy()
+        res[prec] = (np.linalg.norm(q - z @ P, axis=1) / np.linalg.norm(q, axis=1)).max()
+        s.close()
+    assert res["bf16"] <= 1e-5 and res["bf16"] * 20 <= res["bf16-plain"], res
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16-plain", "tf32"])
 def test_two_types_ragged_tiles(prec):
     groups = make_groups([(I.rbc_type(), 50, 0.3), (I.plt_type(), 7, 0.3)])
-    xg, _, st = run_gpu(groups, 3, precision=prec)
+    if prec == "bf16-plain":
+        xg, _, st = run_gpu(groups, 3, precision="bf16", refine_split=False)
+    else:
+        xg, _, st = run_gpu(groups, 3, precision=prec)
     xo, _ = run_oracle(groups, 3)
     assert rel_pos_err(xg, xo, groups) <= TOL_MIXED
     assert st["max_refine_residual"] <= 1e-6
