@@ -35,6 +35,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+PARITY_CELLS = 16        # cells per mesh type compared with the oracle (evenly spaced)
 METRIC = "cell-iterations/sec at 50k cells, mixed vs FP64 GPU at ≤1e-6 rel pos error"
 UNIT = "cell-iterations/s"
 
@@ -280,6 +281,11 @@ def main():
     value = world * ncells * K * args.steps / t
     st = s.stats()
     launches = st["launches_per_step"] * args.steps
+    ci = max(1, st["cell_iterations"])
+    solver = {"backtracks_per_cell_iteration": st["backtracks"] / ci,
+              "refine_sweeps_per_cell_iteration": st["refine_sweeps"] / ci,
+              "max_refine_residual": st["max_refine_residual"], "fallbacks": st["fallbacks"],
+              "capped_searches": st["capped_searches"], "of_step": "last timed step"}
 
     # ---- parity of the timed trajectory on sampled cells vs the FP64 oracle
     total_steps = args.warmup + args.steps
@@ -292,13 +298,13 @@ def main():
             n = g.n_cells * g.mtype.nV * 3
             xg = x[off:off + n].reshape(g.n_cells, g.mtype.nV, 3)
             off += n
-            idx = np.unique(np.linspace(0, g.n_cells - 1, 3).astype(int))
+            idx = np.unique(np.linspace(0, g.n_cells - 1, PARITY_CELLS).astype(int))
             T = O.OracleType.from_mesh_type(g.mtype)
             xo, vo = g.x0[idx].copy(), g.v0[idx].copy()
             for _ in range(total_steps):
-                xo, vo = T.step_cells(xo, vo, g.f_ext[idx], K=K, m=5, threads=4)
+                xo, vo = T.step_cells(xo, vo, g.f_ext[idx], K=K, m=5, threads=os.cpu_count() or 4)
             errs.append(float(np.linalg.norm(xg[idx] - xo, axis=2).max() / g.mtype.radius))
-        parity = {"rel_pos_err": max(errs), "sampled_cells": 3 * len(groups), "steps": total_steps,
+        parity = {"rel_pos_err": max(errs), "sampled_cells": PARITY_CELLS * len(groups), "steps": total_steps,
                   "tolerance": 1e-6 if precision != "fp64" else 1e-10}
 
     # ---- per-kernel CUDA-event times (same steps, events around every launch)
@@ -407,7 +413,7 @@ def main():
                        "l2": "inputs larger than L2 (state + forces ~1.6 GB), no flush",
                        "parallelism": f"{world} independent ranks" if world > 1 else "1 GPU"},
             "clocks": clk, "gpu_launches": launches, "parity": parity, "fp64_gpu": fp64, "e2e": e2e,
-            "roofline": roof, "kernels": kernels}
+            "roofline": roof, "kernels": kernels, "solver": solver}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line), flush=True)

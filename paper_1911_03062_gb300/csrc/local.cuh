@@ -99,7 +99,13 @@ struct Bcast {
 };
 
 // Shared-memory layout of the per-cell kernels:
-//   red[128] doubles | Bcast | pos[3 nVp] | grad[3 nVp] | gva[3 nVp] | stash[stash_T]
+//   red[RED_DOUBLES] | Bcast | pos[3 nVp] | grad[3 nVp] | gva[3 nVp] | stash[stash_T]
+// red: [0, 64) reduction scratch (block_reduce_t0 of up to 4 values over up to
+// 16 warps; the batched L-BFGS sums), [64, 64 + 80) the iteration's per-cell
+// L-BFGS scalars (k_iterate).
+constexpr int RED_DOUBLES = 160;
+constexpr int RED_SCALARS = 64;   // first double of the per-cell L-BFGS scalars
+
 template <typename T>
 struct Smem {
     double *red;
@@ -112,15 +118,15 @@ __device__ __forceinline__ Smem<T> smem_layout(int nVp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<T> s;
     s.red = reinterpret_cast<double *>(smem_raw);
-    s.bc = reinterpret_cast<Bcast<T> *>(smem_raw + 128 * sizeof(double));
-    s.pos = reinterpret_cast<T *>(smem_raw + 128 * sizeof(double) + sizeof(Bcast<double>) + 64);
+    s.bc = reinterpret_cast<Bcast<T> *>(smem_raw + RED_DOUBLES * sizeof(double));
+    s.pos = reinterpret_cast<T *>(smem_raw + RED_DOUBLES * sizeof(double) + sizeof(Bcast<double>) + 64);
     s.gsh = s.pos + 3 * nVp;
     s.gva = s.gsh + 3 * nVp;
     s.stash = s.gva + 3 * nVp;
     return s;
 }
 
-__host__ __device__ constexpr size_t smem_header_bytes() { return 128 * sizeof(double) + sizeof(Bcast<double>) + 64; }
+__host__ __device__ constexpr size_t smem_header_bytes() { return RED_DOUBLES * sizeof(double) + sizeof(Bcast<double>) + 64; }
 constexpr int SMEM_VECS = 3;   // pos, grad, gva: 3 nVp values each
 
 // ---------------------------------------------------------------- 3x2 SVD

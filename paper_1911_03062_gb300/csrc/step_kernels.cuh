@@ -229,8 +229,9 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         const int cnt = a.hcount[cell], head = a.hhead[cell];
         auto slot = [&](int l) { return (head - cnt + l + 2 * m) % m; };   // l = 0 oldest
         // the cell's scalars that thread 0 uses between barriers, fetched up front into
-        // shared memory (red[32 ..), above every reduction's scratch): M, rho, alpha, g, allow
-        double *sM = S.red + 32, *srho = sM + MH * MH, *salp = srho + MH;
+        // shared memory (red[RED_SCALARS ..), above every reduction's scratch): M, rho, alpha, g, allow
+        double *sM = S.red + RED_SCALARS, *srho = sM + MH * MH, *salp = srho + MH;
+        static_assert(RED_SCALARS + MH * MH + 2 * MH <= RED_DOUBLES, "L-BFGS scalars exceed the reduction area");
         for (int i = threadIdx.x; i < m * m + 2 * m; i += blockDim.x) {
             if (i < m * m) sM[i] = Mc[i];
             else if (i < m * m + m) srho[i - m * m] = rho[i - m * m];
