@@ -35,6 +35,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) per k_iterate launch on rbc50k_plt5k in the BF16 form,
+# averaged over the RBC and platelet launches of one step, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, one pass, launches of one timed step).
+# Set to None whenever k_iterate changes until it is captured again.
+ITERATE_TRAFFIC = 2.1875e9
 PARITY_CELLS = 16        # cells per mesh type compared with the oracle (evenly spaced)
 METRIC = "cell-iterations/sec at 50k cells, mixed vs FP64 GPU at ≤1e-6 rel pos error"
 UNIT = "cell-iterations/s"
@@ -197,7 +202,7 @@ def cpu_baseline(workload, n_rbc=768, n_plt=96):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="rbc50k_plt5k")
@@ -391,8 +396,10 @@ def main():
         avg_ms = prof[dom][0] / prof[dom][1]
         per_launch = byts / (launches_per_step if launches_per_step else 1)
         ach = per_launch / (avg_ms / 1e3) / 1e9
+        traffic = ITERATE_TRAFFIC if (args.workload == "rbc50k_plt5k" and precision == "bf16") else None
         roof = {"kernel": "k_iterate", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": peak_src}
+                "frac": ach / hbm, "traffic": traffic, "traffic_unit": "bytes per launch",
+                "peak_source": peak_src}
     elif dom in ("gemm", "gemm_refine"):
         byts = K * sum(algorithmic_gemm(g.mtype.nV, g.n_cells, bf16)[0] for g in groups)
         launches_per_step = prof[dom][1] / args.steps
