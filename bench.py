@@ -292,24 +292,32 @@ def main():
               "max_refine_residual": st["max_refine_residual"], "fallbacks": st["fallbacks"],
               "capped_searches": st["capped_searches"], "of_step": "last timed step"}
 
-    # ---- parity of the timed trajectory on sampled cells vs the FP64 oracle
+    # ---- parity: one step from the state the timed trajectory reached (after
+    # warm-up + timed steps, large deformation), on the GPU and in the FP64 oracle
+    # from the same positions and velocities, sampled cells.  The step map is what
+    # the implementation computes; two trajectories integrated independently drift
+    # apart by rounding amplification of the dynamics (~1.16x per step on this
+    # workload, the oracle against itself included), so they are not compared.
     total_steps = args.warmup + args.steps
     parity = None
     if rank == 0:
         from oracle import oracle as O
-        x = s.positions()
+        xn, vn = s.positions(), s.velocities()
+        s.step(f_dev)
+        s.sync()
+        x1 = s.positions()
         errs, off = [], 0
         for g in groups:
             n = g.n_cells * g.mtype.nV * 3
-            xg = x[off:off + n].reshape(g.n_cells, g.mtype.nV, 3)
-            off += n
+            shape = (g.n_cells, g.mtype.nV, 3)
             idx = np.unique(np.linspace(0, g.n_cells - 1, PARITY_CELLS).astype(int))
             T = O.OracleType.from_mesh_type(g.mtype)
-            xo, vo = g.x0[idx].copy(), g.v0[idx].copy()
-            for _ in range(total_steps):
-                xo, vo = T.step_cells(xo, vo, g.f_ext[idx], K=K, m=5, threads=os.cpu_count() or 4)
-            errs.append(float(np.linalg.norm(xg[idx] - xo, axis=2).max() / g.mtype.radius))
-        parity = {"rel_pos_err": max(errs), "sampled_cells": PARITY_CELLS * len(groups), "steps": total_steps,
+            xo, _ = T.step_cells(xn[off:off + n].reshape(shape)[idx].copy(), vn[off:off + n].reshape(shape)[idx].copy(),
+                                 g.f_ext[idx], K=K, m=5, threads=os.cpu_count() or 4)
+            errs.append(float(np.linalg.norm(x1[off:off + n].reshape(shape)[idx] - xo, axis=2).max() / g.mtype.radius))
+            off += n
+        parity = {"rel_pos_err": max(errs), "sampled_cells": PARITY_CELLS * len(groups),
+                  "measure": f"one step from the GPU state after {total_steps} steps, GPU vs FP64 oracle",
                   "tolerance": 1e-6 if precision != "fp64" else 1e-10}
 
     # ---- per-kernel CUDA-event times (same steps, events around every launch)
@@ -373,6 +381,7 @@ def main():
                     xo, vo = T.step_cells(xo, vo, g.f_ext[idx], K=K, m=5, threads=2)
                 errs.append(float(np.linalg.norm(xg[idx] - xo, axis=2).max() / g.mtype.radius))
             fp64["rel_pos_err"] = max(errs)
+            fp64["measure"] = f"trajectory of {1 + args.fp64_steps} steps from the initial state, 2 cells per type"
             fp64["mixed_over_fp64"] = value / fp64["value"]
         s64.close()
 

@@ -38,7 +38,11 @@ struct GroupMaps {
     CUtensorMap p[MAXG];
     CUtensorMap q_lo[MAXG];   // split products only: low BF16 parts of Q and P^{-1}
     CUtensorMap p_lo[MAXG];
+    CUtensorMap z[MAXG];      // Z (FP32, width nV, box 32 x 32, 128-byte swizzle): epilogue stores
 };
+
+constexpr uint32_t EPI_BOX_BYTES = 32 * 32 * 4;   // one epilogue warp's 32 rows x 32 columns
+constexpr uint32_t EPI_SMEM = 4 * 2 * EPI_BOX_BYTES;   // 4 warps x double buffer
 
 struct GroupArgs {
     int nprob, total_units, stages, accumulate, stage_bytes_b;   // B-tile bytes per stage (max n_tile)
@@ -88,7 +92,8 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped(const __grid_constant__
     const uint32_t a_bytes = BM * KB_BYTES;
     const uint32_t half_bytes = a_bytes + (uint32_t)a.stage_bytes_b;
     const uint32_t stage_bytes = half_bytes * (a.split ? 2u : 1u);
-    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + (size_t)a.stages * stage_bytes);
+    uint8_t *epi = tiles + (size_t)a.stages * stage_bytes;   // epilogue staging, 1024-byte aligned
+    uint64_t *full = reinterpret_cast<uint64_t *>(epi + EPI_SMEM);
     uint64_t *empty = full + a.stages;
     uint64_t *tfull = empty + a.stages;      // [2]
     uint64_t *tempty = tfull + 2;            // [2]
@@ -193,9 +198,15 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped(const __grid_constant__
             }
         }
     } else {
-        // ---------------- epilogue: warps 2..5 own TMEM lane quadrants (warp % 4)
+        // ---------------- epilogue: warps 2..5 own TMEM lane quadrants (warp % 4).
+        // Each 32-column chunk of the warp's 32 rows goes through a 128-byte-swizzled
+        // shared box (chunk j of row r at 16-byte slot j ^ (r & 7): conflict-free) and
+        // leaves by one TMA tile store (apply) or TMA reduce-add into Z (corrections:
+        // the add happens at L2, no read of Z here); rows of converged cells are
+        // staged as zeros.  Two boxes per warp alternate.
         const int quad = warp & 3;
-        int tcount = 0;
+        const uint32_t box0 = smem_u32(epi) + (uint32_t)quad * 2u * EPI_BOX_BYTES;
+        int tcount = 0, sb = 0;
         for (int u = blockIdx.x; u < a.total_units; u += gridDim.x) {
             const Unit w = decode_unit(a, u);
             if (unit_skipped(a, w)) continue;
@@ -210,33 +221,35 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped(const __grid_constant__
             fence_after();
             const int row = w.mt * BM + quad * 32 + lane;
             const int n0 = w.nt * P.n_tile;
-            const bool live = row < P.rows && !(a.accumulate && P.conv && P.conv[row / 3]);
+            const bool zero_row = a.accumulate && (row >= P.rows || (P.conv && P.conv[row / 3]));
             for (int c0 = 0; c0 < P.n_tile; c0 += 32) {
                 float v[32];
                 tmem_ld32(tmem + (uint32_t)(buf * 256) + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
-                if (!live) continue;
-                float *zr = P.Z + (long long)row * P.nVp + n0 + c0;
-                const int lim = min(min(32, P.n_tile - c0), P.nV - (n0 + c0));
-                if (lim == 32) {
-                    float4 *z4 = reinterpret_cast<float4 *>(zr);
+                if (lane == 0) bulk_wait_read_1();          // this box's previous store has read it
+                __syncwarp();
+                const uint32_t box = box0 + (uint32_t)sb * EPI_BOX_BYTES;
+                const uint32_t rbase = box + (uint32_t)lane * 128u;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        float4 o = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                        if (a.accumulate) {
-                            float4 p = z4[i];
-                            o.x += p.x; o.y += p.y; o.z += p.z; o.w += p.w;
-                        }
-                        z4[i] = o;
-                    }
-                } else {
-                    for (int i = 0; i < lim; ++i) zr[i] = a.accumulate ? zr[i] + v[i] : v[i];
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t a16 = rbase + ((uint32_t)(j ^ (lane & 7)) << 4);
+                    if (zero_row) st_shared_v4(a16, 0.f, 0.f, 0.f, 0.f);
+                    else st_shared_v4(a16, v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    if (a.accumulate) tma_reduce_add_2d(&maps.z[w.p], box, n0 + c0, w.mt * BM + quad * 32);
+                    else tma_store_2d(&maps.z[w.p], box, n0 + c0, w.mt * BM + quad * 32);
+                    bulk_commit();
+                }
+                sb ^= 1;
             }
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[buf]);
             ++tcount;
         }
+        if (lane == 0) bulk_wait_all();
     }
     fence_before();
     __syncthreads();

@@ -83,7 +83,7 @@ struct MeshTypeImpl {
     __nv_bfloat16 *q16 = nullptr;
     double *origin = nullptr, *rho = nullptr, *alpha = nullptr, *M = nullptr, *g = nullptr, *allow = nullptr;
     int *hcount = nullptr, *hhead = nullptr, *conv = nullptr, *fb_list = nullptr, *fb_count = nullptr;
-    CUtensorMap mapQ{}, mapR{}, mapRlo{};
+    CUtensorMap mapQ{}, mapR{}, mapRlo{}, mapZ{};
     int ept = 8, block = 256, stash_T = 0;
     size_t smem_step = 0;
 };
@@ -331,7 +331,8 @@ void run_iterate(npfem_ctx *ctx, MeshTypeImpl *t, int last, bool fallback) {
 
 // --- global step: z = P^{-1} q for the stacked rows of every type (one grouped launch)
 size_t grouped_smem(int stages, int max_ntile, bool split = false) {
-    return 1024 + (size_t)stages * (tc::BM + max_ntile) * tc::KB_BYTES * (split ? 2 : 1) + (2 * stages + 4) * 8 + 16;
+    return 1024 + (size_t)stages * (tc::BM + max_ntile) * tc::KB_BYTES * (split ? 2 : 1) + tc::EPI_SMEM +
+           (2 * stages + 4) * 8 + 16;
 }
 size_t gemm_smem(const MeshTypeImpl *t) { return grouped_smem(t->stages, t->n_tile); }
 
@@ -387,7 +388,7 @@ struct GemmItem {
     const MeshTypeImpl *t;
     const CUtensorMap *mapQ;
     int rows;
-    float *Z;
+    const CUtensorMap *mapZ;               // Z (FP32, width nV, 32 x 32 boxes)
     const int *conv;
     const CUtensorMap *mapQlo = nullptr;   // split form: low part of Q (P's low part from the type)
 };
@@ -410,11 +411,12 @@ void gemm_group(npfem_ctx *ctx, const std::vector<GemmItem> &items, int accumula
             P.m_tiles = (it.rows + tc::BM - 1) / tc::BM;
             P.kblocks = (it.t->nV * (bf16(ctx) ? 2 : 4) + tc::KB_BYTES - 1) / tc::KB_BYTES;
             P.unit_begin = units;
-            P.Z = it.Z;
+            P.Z = nullptr;
             P.conv = it.conv;
             units += P.m_tiles * P.n_ntiles;
             maps.q[g.nprob] = *it.mapQ;
             maps.p[g.nprob] = it.t->mapP;
+            maps.z[g.nprob] = *it.mapZ;
             if (split_form) {
                 maps.q_lo[g.nprob] = *it.mapQlo;
                 maps.p_lo[g.nprob] = it.t->mapPlo;
@@ -441,9 +443,9 @@ void gemm_group(npfem_ctx *ctx, const std::vector<GemmItem> &items, int accumula
     }
 }
 
-void gemm_tc(npfem_ctx *ctx, MeshTypeImpl *t, const CUtensorMap &mapQ, int rows, float *Z, int accumulate,
-             const int *conv, const CUtensorMap *mapQlo = nullptr) {
-    gemm_group(ctx, {GemmItem{t, &mapQ, rows, Z, conv, mapQlo}}, accumulate, mapQlo != nullptr);
+void gemm_tc(npfem_ctx *ctx, MeshTypeImpl *t, const CUtensorMap &mapQ, int rows, const CUtensorMap &mapZ,
+             int accumulate, const int *conv, const CUtensorMap *mapQlo = nullptr) {
+    gemm_group(ctx, {GemmItem{t, &mapQ, rows, &mapZ, conv, mapQlo}}, accumulate, mapQlo != nullptr);
 }
 
 void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, const float *z, void *r,
@@ -527,8 +529,8 @@ void apply_all(npfem_ctx *ctx) {
     std::vector<GemmItem> first, corr;
     for (auto *t : ctx->types) {
         if (!t->ncells) continue;
-        first.push_back(GemmItem{t, &t->mapQ, 3 * t->ncells, (float *)t->z, nullptr});
-        corr.push_back(GemmItem{t, &t->mapR, 3 * t->ncells, (float *)t->z, t->conv, split(ctx) ? &t->mapRlo : nullptr});
+        first.push_back(GemmItem{t, &t->mapQ, 3 * t->ncells, &t->mapZ, nullptr});
+        corr.push_back(GemmItem{t, &t->mapR, 3 * t->ncells, &t->mapZ, t->conv, split(ctx) ? &t->mapRlo : nullptr});
     }
     gemm_group(ctx, first, 0);
     for (int s = 0; s < ctx->opt.refine_max; ++s) {
@@ -969,7 +971,7 @@ void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
                 std::istringstream ls(line);
                 std::string k;
                 int nt = 0, st = 0;
-                if (ls >> k >> nt >> st && k == key && nt >= 16 && nt <= 256 && nt % 16 == 0 && st >= 2 && st <= 8) {
+                if (ls >> k >> nt >> st && k == key && nt >= 32 && nt <= 256 && nt % 32 == 0 && st >= 2 && st <= 8) {
                     g_tuned[key] = {nt, st};
                     use(nt, st);
                     return;
@@ -986,18 +988,20 @@ void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
         void *Q = dalloc<unsigned char>(ctx, (size_t)rows * t->nVp * (bf16(ctx) ? 2 : 4), &tmp);
         float *Z = dalloc<float>(ctx, (size_t)rows * t->nVp, &tmp);
         CUtensorMap mq = make_map(ctx, Q, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
+        CUtensorMap mz = make_map(ctx, Z, false, t->nV, rows, t->nVp, 32);
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         const int base_tiles = (t->nV + 255) / 256;
         for (int ntiles = base_tiles; ntiles <= base_tiles + 1; ++ntiles) {
-            int nt = ((t->nV + ntiles - 1) / ntiles + 15) / 16 * 16;
+            // N tile: a multiple of 32 (the epilogue's store box width), at most 256
+            int nt = ((t->nV + ntiles - 1) / ntiles + 31) / 32 * 32;
             if (nt > 256 || nt < 16) continue;
             for (int st = 2; st <= 6; ++st) {
                 if (grouped_smem(st, nt) + 2048 > (size_t)ctx->smem_optin) continue;
                 use(nt, st);
-                gemm_tc(ctx, t, mq, rows, Z, 0, nullptr);
+                gemm_tc(ctx, t, mq, rows, mz, 0, nullptr);
                 CK(cudaEventRecord(e0, ctx->stream));
-                for (int r = 0; r < 5; ++r) gemm_tc(ctx, t, mq, rows, Z, 0, nullptr);
+                for (int r = 0; r < 5; ++r) gemm_tc(ctx, t, mq, rows, mz, 0, nullptr);
                 CK(cudaEventRecord(e1, ctx->stream));
                 CK(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -1070,6 +1074,7 @@ void alloc_cells(npfem_ctx *ctx, MeshTypeImpl *t, int cap) {
         t->mapQ = make_map(ctx, bf16(ctx) ? (const void *)t->q16 : t->q, bf16(ctx), t->nV, 3ll * cap, t->nVp, tc::BM);
         t->mapR = make_map(ctx, t->rlo, bf16(ctx), t->nV, 3ll * cap, t->nVp, tc::BM);
         if (split(ctx)) t->mapRlo = make_map(ctx, t->rlo_lo, true, t->nV, 3ll * cap, t->nVp, tc::BM);
+        t->mapZ = make_map(ctx, t->z, false, t->nV, 3ll * cap, t->nVp, 32);
     }
 }
 
@@ -1555,10 +1560,11 @@ int npfem_apply_pinv(npfem_ctx *ctx, int type_id, const double *q, double *z, in
                 CUtensorMap mr = make_map(ctx, rl, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
                 CUtensorMap mrl{};
                 if (rlo) mrl = make_map(ctx, rlo, true, t->nV, rows, t->nVp, tc::BM);
-                gemm_tc(ctx, t, mq, rows, zi, 0, nullptr);
+                const CUtensorMap mz = make_map(ctx, zi, false, t->nV, rows, t->nVp, 32);
+                gemm_tc(ctx, t, mq, rows, mz, 0, nullptr);
                 for (int s = 0; s < ctx->opt.refine_max; ++s) {
                     residual(ctx, t, ncell, qi, zi, rl, conv, s == 0, 0, rlo);
-                    gemm_tc(ctx, t, mr, rows, zi, 1, conv, rlo ? &mrl : nullptr);
+                    gemm_tc(ctx, t, mr, rows, mz, 1, conv, rlo ? &mrl : nullptr);
                 }
                 residual(ctx, t, ncell, qi, zi, nullptr, conv, ctx->opt.refine_max == 0, 1);
                 k_cols_out<float><<<grid_for((long long)n_cols * t->nV, 256, 8192), 256, 0, ctx->stream>>>(
@@ -1660,10 +1666,11 @@ extern "C" int npfem_apply_pinv_noalloc(npfem_ctx *ctx, int type_id, const doubl
             CUtensorMap mr = make_map(ctx, rl, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
             CUtensorMap mrl{};
             if (rlo) mrl = make_map(ctx, rlo, true, t->nV, rows, t->nVp, tc::BM);
-            gemm_tc(ctx, t, mq, rows, (float *)zi, 0, nullptr);
+            const CUtensorMap mz = make_map(ctx, zi, false, t->nV, rows, t->nVp, 32);
+            gemm_tc(ctx, t, mq, rows, mz, 0, nullptr);
             for (int s = 0; s < ctx->opt.refine_max; ++s) {
                 residual(ctx, t, ncell, (const float *)qi, (const float *)zi, rl, conv, s == 0, 0, rlo);
-                gemm_tc(ctx, t, mr, rows, (float *)zi, 1, conv, rlo ? &mrl : nullptr);
+                gemm_tc(ctx, t, mr, rows, mz, 1, conv, rlo ? &mrl : nullptr);
             }
             residual(ctx, t, ncell, (const float *)qi, (const float *)zi, nullptr, conv, ctx->opt.refine_max == 0, 1);
             k_cols_out<float><<<grid_for((long long)n_cols * t->nV, 256, 8192), 256, 0, ctx->stream>>>(

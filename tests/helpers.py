@@ -64,3 +64,34 @@ def rel_pos_err(xg_groups, xo_groups, groups):
         d = np.linalg.norm(xg[idx] - xo, axis=2).max() / g.mtype.radius
         err = max(err, float(d))
     return err
+
+
+def one_step_parity(groups, steps_before, sample, precision="fp64", **opts):
+    """Advance all cells `steps_before` steps on the GPU, then one more step on the
+    GPU and, from the same GPU state (positions and velocities), one oracle step for
+    the sampled cells; returns the relative position error of that step.
+
+    The cell dynamics amplify any difference in rounding order (the oracle against
+    itself with a 1e-12 perturbation grows ~1.16x per step on the amplitude-0.3
+    workloads), so parity after many steps is measured on the step map from a shared
+    state rather than on two independently integrated trajectories."""
+    from oracle import oracle as O
+    from paper_1911_03062_gb300.npfem import Solver
+    s = Solver(precision=precision, **opts)
+    for g in groups:
+        s.add_cells(s.create_type(g.mtype), g.x0, g.v0)
+    f = public(groups, "f_ext")
+    for _ in range(steps_before):
+        s.step(f)
+    xn, vn = split(s.positions(), groups), split(s.velocities(), groups)
+    s.step(f)
+    x1 = split(s.positions(), groups)
+    st = s.stats()
+    s.close()
+    err = 0.0
+    for gi, g in enumerate(groups):
+        idx = np.asarray(sample[gi])
+        T = O.OracleType.from_mesh_type(g.mtype)
+        xo, _ = T.step_cells(xn[gi][idx].copy(), vn[gi][idx].copy(), g.f_ext[idx], K=10, m=5, threads=4)
+        err = max(err, float(np.linalg.norm(x1[gi][idx] - xo, axis=2).max() / g.mtype.radius))
+    return err, st

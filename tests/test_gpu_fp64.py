@@ -6,7 +6,7 @@ import pytest
 
 from paper_1911_03062_gb300 import inputs as I
 
-from helpers import make_groups, public, rel_pos_err, run_gpu, run_oracle, split
+from helpers import make_groups, one_step_parity, public, rel_pos_err, run_gpu, run_oracle, split
 
 pytestmark = pytest.mark.gpu
 
@@ -64,6 +64,15 @@ def test_sampled_cells_at_4096():
     sample = [[0, 1, 2047, 4000, 4095]]
     xo, _ = run_oracle([g], 2, sample=sample)
     assert rel_pos_err(xg, xo, [g]) <= TOL64
+
+
+def test_late_state_step_at_4096():
+    # 4096 RBC after 20 steps: one FP64 GPU step from its own state vs the oracle's
+    # step from the same state (trajectories themselves drift apart by rounding
+    # amplification, ~1.2x per step)
+    groups = [I.materialise(g) for g in I.workload_groups("rbc4096")]
+    err, _ = one_step_parity(groups, 20, [[0, 1000, 2048, 4095]], precision="fp64")
+    assert err <= TOL64, err
 
 
 def test_rest_state_stays_at_rest():

@@ -6,7 +6,7 @@ import pytest
 
 from paper_1911_03062_gb300 import inputs as I
 
-from helpers import make_groups, public, rel_pos_err, run_gpu, run_oracle
+from helpers import make_groups, one_step_parity, public, rel_pos_err, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -148,6 +148,15 @@ def test_sampled_cells_at_50k_bf16():
     sample = [[0, 1, 25000, 49999], [0, 2500, 4999]]
     xo, _ = run_oracle(groups, 1, sample=sample)
     assert rel_pos_err(xg, xo, groups) <= TOL_MIXED
+    assert st["max_refine_residual"] <= 1e-6
+
+
+def test_late_state_step_at_50k_bf16():
+    # the bench workload after 30 steps (large deformation): one step from the GPU's
+    # state, sampled cells vs the oracle's step from the same state
+    groups = [I.materialise(g) for g in I.workload_groups("rbc50k_plt5k")]
+    err, st = one_step_parity(groups, 30, [[0, 7, 12345, 31000, 49999], [0, 1234, 4999]], precision="bf16")
+    assert err <= TOL_MIXED, err
     assert st["max_refine_residual"] <= 1e-6
 
 
