@@ -86,6 +86,7 @@ struct MeshTypeImpl {
     CUtensorMap mapQ{}, mapR{}, mapRlo{}, mapZ{};
     int ept = 8, block = 256, stash_T = 0;
     size_t smem_step = 0;
+    int pf_iter = 0, pf_pred = 0;                // L2 prefetch distance: resident blocks of the kernel
 };
 
 struct npfem_ctx {
@@ -288,9 +289,23 @@ IterArgs<T> make_args(npfem_ctx *ctx, MeshTypeImpl *t) {
     return a;
 }
 
+// Resident blocks of the per-cell kernels (blocks per SM x SMs): a k_predict block
+// prefetches into L2 the state and forces of the cell that many blocks ahead, which
+// starts about when it ends.  (In k_iterate the same prefetch of the next wave's
+// vectors evicted the history pairs the running blocks re-read from L2: +15 %.)
+template <typename T, int EPT, int MAXB>
+void prefetch_distance_t(npfem_ctx *ctx, MeshTypeImpl *t) {
+    int bi = 0, bp = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bi, k_iterate<T, EPT, MAXB>, t->block, t->smem_step));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bp, k_predict<T, EPT, MAXB>, t->block, t->smem_step));
+    t->pf_iter = bi * ctx->nsm;
+    t->pf_pred = bp * ctx->nsm;
+}
+
 template <typename T, int EPT, int MAXB>
 void run_predict_t(npfem_ctx *ctx, MeshTypeImpl *t) {
     IterArgs<T> a = make_args<T>(ctx, t);
+    a.pf_dist = t->pf_pred;
     prof_begin(ctx, NPFEM_K_PREDICT);
     k_predict<T, EPT, MAXB><<<t->ncells, t->block, t->smem_step, ctx->stream>>>(a);
     CK(cudaGetLastError());
@@ -327,6 +342,11 @@ void run_predict(npfem_ctx *ctx, MeshTypeImpl *t) {
 void run_iterate(npfem_ctx *ctx, MeshTypeImpl *t, int last, bool fallback) {
     if (mixed(ctx)) DISPATCH_EPT(float, run_iterate_t, ctx, t, last, fallback);
     else DISPATCH_EPT(double, run_iterate_t, ctx, t, last, fallback);
+}
+
+void set_prefetch_distance(npfem_ctx *ctx, MeshTypeImpl *t) {
+    if (mixed(ctx)) DISPATCH_EPT(float, prefetch_distance_t, ctx, t);
+    else DISPATCH_EPT(double, prefetch_distance_t, ctx, t);
 }
 
 // --- global step: z = P^{-1} q for the stacked rows of every type (one grouped launch)
@@ -1327,6 +1347,7 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         if (mixed(ctx)) choose_tiles(ctx, t);
         if (t->smem_step > (size_t)ctx->smem_optin || gemm_smem(t) + 2048 > (size_t)ctx->smem_optin)
             fail(ctx, NPFEM_EINVAL, "mesh type needs more shared memory than the device offers");
+        set_prefetch_distance(ctx, t);
         CK(cudaStreamSynchronize(ctx->stream));
         ctx->types.push_back(t);
         invalidate_graph(ctx);

@@ -19,6 +19,7 @@ template <typename T>
 struct IterArgs {
     TypeConst<T> tc;
     int ncells, m, max_bt, last, use_allow, stash_T;
+    int pf_dist;                  // k_predict: L2 prefetch of cell + pf_dist (one resident wave ahead), 0: off
     double h, inv_h, c1;
     double *xn, *vn;              // state, FP64 SoA
     const double *const *fptr;    // device slot holding the f_ext base (public layout)
@@ -109,6 +110,14 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
     }
 }
 
+// L2 prefetch hint of n bytes at p (rounded down to 16-byte multiples; p must be
+// 16-byte aligned): cp.async.bulk.prefetch, no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t n) {
+    const uint32_t b = (uint32_t)(n & ~(size_t)15);
+    if (b && !(reinterpret_cast<uintptr_t>(p) & 15))
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p)), "r"(b) : "memory");
+}
+
 // Sums over the block of n per-thread partials at once (the dot products of
 // one L-BFGS pass): partials are written transposed to shared memory, warp w
 // reduces values w, w + nwarps, ... in float-float (FP64 in the FP64 path)
@@ -143,6 +152,15 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
     const int nVp = a.tc.nVp, n3 = 3 * nVp;
     for (int cell = blockIdx.x; cell < a.ncells; cell += gridDim.x) {
         const long long base = (long long)cell * n3;
+        if (a.pf_dist && threadIdx.x < 3) {
+            const int fut = cell + a.pf_dist;        // one resident wave ahead
+            if (fut < a.ncells) {
+                const size_t vb = (size_t)n3 * sizeof(double);
+                if (threadIdx.x == 0) prefetch_l2(a.xn + (long long)fut * n3, vb);
+                else if (threadIdx.x == 1) prefetch_l2(a.vn + (long long)fut * n3, vb);
+                else prefetch_l2(*a.fptr + a.pub_off[fut], (size_t)3 * a.tc.nV * sizeof(double));
+            }
+        }
         double y[EPT], xo[EPT];
         predictor64<T, EPT>(a, cell, y, xo);
         // centroid of y, per component
