@@ -789,6 +789,70 @@ int orc_step(const orc_type *T, const double *xn, const double *vn, const double
     return caps;
 }
 
+/* ------------------------------------------------ pre- and post-step filters
+ * One-ring median filter of the external forces (paper Sec. 2.2: a median in the
+ * one-ring neighbourhood of every Lagrangian point attenuates force spikes).
+ * Reading: the force of vertex v becomes, component by component, the median of
+ * the forces of v and of the vertices sharing an edge with v; for an even count
+ * the mean of the two middle values.  f, out: [nV][3]. */
+static int dbl_cmp(const void *a, const void *b) {
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+int orc_force_median(const orc_type *T, const double *f, double *out) {
+    int nV = T->nV, nT = T->nT;
+    int *deg = (int *)calloc((size_t)nV + 1, sizeof(int));
+    int *nb = (int *)malloc(sizeof(int) * 6 * (size_t)nT);
+    double *val = (double *)malloc(sizeof(double) * ((size_t)nV + 1));
+    int *start = (int *)malloc(sizeof(int) * ((size_t)nV + 1));
+    if (!deg || !nb || !val || !start) { free(deg); free(nb); free(val); free(start); return ORC_ENOMEM; }
+    /* directed edges (each triangle edge both ways), bucketed by source vertex */
+    for (int t = 0; t < nT; ++t)
+        for (int k = 0; k < 3; ++k) { deg[T->tri[3*t+k]] += 2; }
+    start[0] = 0;
+    for (int v = 0; v < nV; ++v) start[v+1] = start[v] + deg[v];
+    for (int v = 0; v < nV; ++v) deg[v] = 0;
+    for (int t = 0; t < nT; ++t)
+        for (int k = 0; k < 3; ++k) {
+            int a = T->tri[3*t+k], b = T->tri[3*t+(k+1)%3];
+            nb[start[a] + deg[a]++] = b;
+            nb[start[b] + deg[b]++] = a;
+        }
+    for (int v = 0; v < nV; ++v) {
+        int *l = nb + start[v], n = deg[v], u = 0;
+        /* unique neighbours (each appears twice in a closed manifold mesh) */
+        for (int i = 0; i < n; ++i) {
+            int dup = 0;
+            for (int j = 0; j < u; ++j) if (l[j] == l[i]) { dup = 1; break; }
+            if (!dup) l[u++] = l[i];
+        }
+        for (int c = 0; c < 3; ++c) {
+            int cnt = 0;
+            val[cnt++] = f[3*v + c];
+            for (int i = 0; i < u; ++i) val[cnt++] = f[3*l[i] + c];
+            qsort(val, (size_t)cnt, sizeof(double), dbl_cmp);
+            out[3*v + c] = (cnt & 1) ? val[cnt/2] : 0.5 * (val[cnt/2 - 1] + val[cnt/2]);
+        }
+    }
+    free(deg); free(nb); free(val); free(start);
+    return ORC_OK;
+}
+
+/* Velocity cap (paper Sec. 2.2: an npFEM vertex velocity above U*_max is
+ * truncated towards the threshold).  Reading: |v| > umax -> v * umax / |v|,
+ * direction kept.  v: [nV][3], in place. */
+void orc_velocity_cap(int nV, double *v, double umax) {
+    for (int i = 0; i < nV; ++i) {
+        double *w = v + 3*i;
+        double n = sqrt(w[0]*w[0] + w[1]*w[1] + w[2]*w[2]);
+        if (n > umax) {
+            double sc = umax / n;
+            w[0] *= sc; w[1] *= sc; w[2] *= sc;
+        }
+    }
+}
+
 /* n cells of one type, one after another (arrays: [n][nV][3]). */
 int orc_step_cells(const orc_type *T, int n, const double *xn, const double *vn, const double *f,
                    int K, int m, double c1, int max_bt, double *x_out, double *v_out) {

@@ -69,6 +69,9 @@ def lib():
             L.orc_step_cells.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, C.c_int, C.c_double,
                                          C.c_int, vp, vp]
             L.orc_step_cells.restype = C.c_int
+            L.orc_force_median.argtypes = [vp, dp, dp]
+            L.orc_force_median.restype = C.c_int
+            L.orc_velocity_cap.argtypes = [C.c_int, dp, C.c_double]
             _lib = L
     return _lib
 
@@ -190,6 +193,28 @@ class OracleType:
             for t in ts:
                 t.join()
         return xo, vo
+
+
+def force_median(T, f):
+    """One-ring median filter of per-vertex forces ([n, nV, 3] or [nV, 3])."""
+    f = _c(f)
+    flat = f.reshape(-1, T.nV, 3)
+    out = np.empty_like(flat)
+    for c in range(flat.shape[0]):
+        src = np.ascontiguousarray(flat[c])
+        dst = np.empty_like(src)
+        if lib().orc_force_median(T._h, src, dst) != 0:
+            raise MemoryError("orc_force_median")
+        out[c] = dst
+    return out.reshape(f.shape)
+
+
+def velocity_cap(v, umax):
+    """Copy of per-vertex velocities ([..., 3]) with |v| > umax scaled to umax."""
+    out = _c(v).copy()
+    flat = out.reshape(-1, 3)
+    lib().orc_velocity_cap(flat.shape[0], flat, float(umax))
+    return out
 
 
 def polar(F):

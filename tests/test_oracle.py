@@ -424,3 +424,47 @@ def test_dynamics_amplify_rounding_level_perturbations(O):
         xa, va = T.step_cells(xa, va, g.f_ext, K=10, m=5, threads=4)
         xb, vb = T.step_cells(xb, vb, g.f_ext, K=10, m=5, threads=4)
     assert np.linalg.norm(xa - xb, axis=2).max() > 100 * d0
+
+
+# ------------------------------------------------------- f2: force filter, velocity cap
+def _closed_one_rings(tris, nV):
+    ring = [set([v]) for v in range(nV)]
+    for a, b, c in tris:
+        for u, w in ((a, b), (b, c), (c, a)):
+            ring[u].add(w)
+            ring[w].add(u)
+    return [sorted(r) for r in ring]
+
+
+def test_force_median_matches_library_median(O, rbc):
+    # component-wise median over {v} + one-ring (valence 5 -> 6 values: mean of the two
+    # middle ones; valence 6 -> 7 values), against numpy's median on an independently
+    # built neighbourhood
+    mt, T = rbc
+    f = np.random.default_rng(21).standard_normal((2, mt.nV, 3))
+    got = O.force_median(T, f)
+    rings = _closed_one_rings(mt.tris, mt.nV)
+    assert {len(r) for r in rings} == {6, 7}
+    ref = np.stack([np.stack([np.median(fc[r], axis=0) for r in rings]) for fc in f])
+    assert np.array_equal(got, ref)
+
+
+def test_force_median_constant_field_and_spike(O, rbc):
+    mt, T = rbc
+    f = np.tile(np.array([0.3, -1.2, 2.5]), (mt.nV, 1))
+    assert np.array_equal(O.force_median(T, f), f)
+    g = f.copy()
+    g[100] = [1e6, -1e6, 3e3]                      # one spike: removed, neighbours untouched
+    assert np.array_equal(O.force_median(T, g), f)
+
+
+def test_velocity_cap_closed_form(O):
+    rng = np.random.default_rng(22)
+    v = rng.standard_normal((500, 3)) * rng.uniform(0.0, 0.2, (500, 1))
+    umax = 0.05
+    w = O.velocity_cap(v, umax)
+    n, m = np.linalg.norm(v, axis=1), np.linalg.norm(w, axis=1)
+    below = n <= umax
+    assert np.array_equal(w[below], v[below])
+    assert np.allclose(m[~below], umax, rtol=1e-15, atol=0)
+    assert np.allclose(w[~below] / m[~below, None], v[~below] / n[~below, None], rtol=0, atol=1e-15)
