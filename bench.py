@@ -211,6 +211,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-sample", type=int, nargs=2, default=[160, 16])
+    ap.add_argument("--force-median", action="store_true", help="one-ring median filter of the forces before each step")
+    ap.add_argument("--u-max", type=float, default=0.0, help="velocity cap after each step (0: off)")
     args = ap.parse_args()
     rank, world, local = env_rank()
 
@@ -254,7 +256,7 @@ def main():
     stream = torch.cuda.Stream()
 
     def make(prec):
-        s = Solver(precision=prec, stream=stream)
+        s = Solver(precision=prec, stream=stream, force_median=args.force_median, u_max=args.u_max)
         for g in groups:
             s.add_cells(s.create_type(g.mtype), g.x0, g.v0)
         return s
@@ -312,8 +314,9 @@ def main():
             shape = (g.n_cells, g.mtype.nV, 3)
             idx = np.unique(np.linspace(0, g.n_cells - 1, PARITY_CELLS).astype(int))
             T = O.OracleType.from_mesh_type(g.mtype)
+            fs = O.force_median(T, g.f_ext[idx]) if args.force_median else g.f_ext[idx]
             xo, _ = T.step_cells(xn[off:off + n].reshape(shape)[idx].copy(), vn[off:off + n].reshape(shape)[idx].copy(),
-                                 g.f_ext[idx], K=K, m=5, threads=os.cpu_count() or 4)
+                                 fs, K=K, m=5, threads=os.cpu_count() or 4)
             errs.append(float(np.linalg.norm(x1[off:off + n].reshape(shape)[idx] - xo, axis=2).max() / g.mtype.radius))
             off += n
         parity = {"rel_pos_err": max(errs), "sampled_cells": PARITY_CELLS * len(groups),
@@ -377,8 +380,11 @@ def main():
                 idx = np.array([0, g.n_cells - 1])
                 T = O.OracleType.from_mesh_type(g.mtype)
                 xo, vo = g.x0[idx].copy(), g.v0[idx].copy()
+                fs = O.force_median(T, g.f_ext[idx]) if args.force_median else g.f_ext[idx]
                 for _ in range(1 + args.fp64_steps):
-                    xo, vo = T.step_cells(xo, vo, g.f_ext[idx], K=K, m=5, threads=2)
+                    xo, vo = T.step_cells(xo, vo, fs, K=K, m=5, threads=2)
+                    if args.u_max > 0:
+                        vo = O.velocity_cap(vo, args.u_max)
                 errs.append(float(np.linalg.norm(xg[idx] - xo, axis=2).max() / g.mtype.radius))
             fp64["rel_pos_err"] = max(errs)
             fp64["measure"] = f"trajectory of {1 + args.fp64_steps} steps from the initial state, 2 cells per type"
@@ -427,7 +433,8 @@ def main():
                        "iters_per_step": K, "history": 5, "precision": precision,
                        "local_step": "fp32" if precision != "fp64" else "fp64",
                        "l2": "inputs larger than L2 (state + forces ~1.6 GB), no flush",
-                       "parallelism": f"{world} independent ranks" if world > 1 else "1 GPU"},
+                       "parallelism": f"{world} independent ranks" if world > 1 else "1 GPU",
+                       "force_median": bool(args.force_median), "u_max": args.u_max},
             "clocks": clk, "gpu_launches": launches, "parity": parity, "fp64_gpu": fp64, "e2e": e2e,
             "roofline": roof, "kernels": kernels, "solver": solver}
     if not args.no_cpu:

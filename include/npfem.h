@@ -78,6 +78,13 @@ typedef struct {
                                (r_hi P_hi + r_lo P_hi + r_hi P_lo) accumulated in FP32, so one
                                correction reduces the residual ~100x further than a plain BF16
                                one (1, default); plain BF16 corrections (0) */
+    int force_median;       /* 1: before each step, replace every vertex force by the component-wise
+                               median over the vertex and its edge neighbours (closed one-ring; even
+                               count: mean of the two middle values); paper Sec. 2.2.  Default 0.
+                               Meshes with a vertex of more than 31 neighbours are rejected (EINVAL). */
+    double u_max;           /* > 0: after each step, vertex velocities with |v| > u_max are scaled to
+                               |v| = u_max (direction kept), in the state; paper Sec. 2.2.  Default 0
+                               (off). */
 } npfem_options;
 
 /* Material and time step of one mesh type.  Element weights follow the
@@ -109,6 +116,7 @@ typedef struct {
 #define NPFEM_K_GEMM_REFINE 4    /* refinement correction applies */
 #define NPFEM_K_RESIDUAL 5       /* FP64 refinement residuals */
 #define NPFEM_K_FALLBACK_APPLY 6 /* P^{-1} grad for non-descent cells */
+#define NPFEM_K_FILTER 7         /* force median filter and velocity cap */
 #define NPFEM_KCLASSES 8
 
 typedef struct {

@@ -64,6 +64,8 @@ struct MeshTypeImpl {
     int n_off = 0;
     // vertex numbering: vpub[i] = caller's index of internal vertex i, vint its inverse
     int *vpub = nullptr, *vint = nullptr;
+    // edge neighbours of each (internal) vertex, CSR: the median filter's one-rings
+    int *adj_ptr = nullptr, *adj = nullptr;
     // fixed-width row table of the off-diagonal entries for the block-per-cell
     // residual (ell_W = 0: rows too long or too many vertices, CSR kernel)
     unsigned short *ell_col = nullptr;
@@ -99,6 +101,7 @@ struct npfem_ctx {
     double *d_f = nullptr;               // device copy of host forces (public layout)
     double **d_fslot = nullptr;          // device slot: base of the forces read by the step
     double *d_stage = nullptr;           // staging for get/set (public layout)
+    double *d_ffilt = nullptr;           // median-filtered forces (public layout), force_median only
     DevStatus *d_st = nullptr;
     DevStatus *h_st = nullptr;           // pinned
     int *d_any = nullptr;
@@ -401,6 +404,7 @@ void set_kernel_attrs(npfem_ctx *ctx) {
     all(k_residual<true>);
     for (int W : {12, 16})
         for (int KR = 1; KR <= 4; ++KR) all(resid_ell_fn(W, KR));
+    all(k_force_median);
     ctx->smem_optin = mx;
 }
 
@@ -586,6 +590,22 @@ void enqueue_step(npfem_ctx *ctx) {
     // counters only: a pending error word survives until a synchronising call reads it
     CK(cudaMemsetAsync(reinterpret_cast<char *>(ctx->d_st) + sizeof(unsigned long long), 0,
                        sizeof(DevStatus) - sizeof(unsigned long long), ctx->stream));
+    if (ctx->opt.force_median) {
+        // filtered copy of the forces; the step then reads it through the slot
+        for (auto *t : ctx->types) {
+            if (!t->ncells) continue;
+            prof_begin(ctx, NPFEM_K_FILTER);
+            k_force_median<<<std::min(t->ncells, 8 * ctx->nsm), 256, 2 * 3 * (size_t)t->nV * sizeof(double),
+                             ctx->stream>>>(t->ncells, t->nV, t->pub_off, t->vpub, t->adj_ptr, t->adj, ctx->d_fslot,
+                                            ctx->d_ffilt);
+            CK(cudaGetLastError());
+            prof_end(ctx);
+        }
+        prof_begin(ctx, NPFEM_K_FILTER);
+        k_set_ptr<<<1, 1, 0, ctx->stream>>>(ctx->d_fslot, ctx->d_ffilt);
+        CK(cudaGetLastError());
+        prof_end(ctx);
+    }
     for (auto *t : ctx->types)
         if (t->ncells) run_predict(ctx, t);
     const int K = ctx->opt.iters;
@@ -598,6 +618,16 @@ void enqueue_step(npfem_ctx *ctx) {
             run_iterate(ctx, t, last, false);
             fallback_apply(ctx, t);
             run_iterate(ctx, t, last, true);
+        }
+    }
+    if (ctx->opt.u_max > 0) {
+        for (auto *t : ctx->types) {
+            if (!t->ncells) continue;
+            prof_begin(ctx, NPFEM_K_FILTER);
+            k_vel_cap<<<grid_for((long long)t->ncells * t->nV, 256, 8192), 256, 0, ctx->stream>>>(
+                t->ncells, t->nV, t->nVp, t->vn, ctx->opt.u_max);
+            CK(cudaGetLastError());
+            prof_end(ctx);
         }
     }
 }
@@ -1154,7 +1184,8 @@ int npfem_create(const npfem_options *opt, npfem_ctx **out) {
     int rc = guard(ctx, [&] {
         const npfem_options &o = ctx->opt;
         if (o.precision < 0 || o.precision > 2 || o.iters < 1 || o.history < 0 || o.history > NPFEM_MAX_HISTORY ||
-            o.max_backtracks < 0 || !(o.armijo_c1 > 0 && o.armijo_c1 < 1) || o.refine_max < 0 || !(o.refine_tol > 0))
+            o.max_backtracks < 0 || !(o.armijo_c1 > 0 && o.armijo_c1 < 1) || o.refine_max < 0 || !(o.refine_tol > 0) ||
+            o.force_median < 0 || o.force_median > 1 || !(o.u_max >= 0) || !std::isfinite(o.u_max))
             fail(ctx, NPFEM_EINVAL, "invalid option value");
         CK(cudaSetDevice(o.device));
         ctx->device = o.device;
@@ -1197,7 +1228,7 @@ void npfem_destroy(npfem_ctx *ctx) {
         for (void *p : t->owned) cudaFree(p);
         delete t;
     }
-    void *bufs[] = {ctx->d_f, ctx->d_fslot, ctx->d_stage, ctx->d_st, ctx->d_any};
+    void *bufs[] = {ctx->d_f, ctx->d_fslot, ctx->d_stage, ctx->d_st, ctx->d_any, ctx->d_ffilt};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
@@ -1256,6 +1287,28 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         build_host_type(ctx, nV, rest_i.data(), nT, tris_i.data(), mass.data(), *mat, vpub.data(), tpub.data(), H);
         t->vpub = upload(ctx, vpub, t->owned);
         t->vint = upload(ctx, intl, t->owned);
+        {
+            // edge neighbours in the internal numbering (the median filter's one-rings)
+            std::vector<std::vector<int>> nb(nV);
+            for (int k = 0; k < nT; ++k)
+                for (int j = 0; j < 3; ++j) {
+                    const int a = tris_i[3 * k + j], b = tris_i[3 * k + (j + 1) % 3];
+                    nb[a].push_back(b);
+                    nb[b].push_back(a);
+                }
+            std::vector<int> ap(nV + 1, 0), aj;
+            for (int v = 0; v < nV; ++v) {
+                std::sort(nb[v].begin(), nb[v].end());
+                nb[v].erase(std::unique(nb[v].begin(), nb[v].end()), nb[v].end());
+                if (ctx->opt.force_median && (int)nb[v].size() + 1 > MEDIAN_MAX)
+                    fail(ctx, NPFEM_EINVAL, "vertex %d has %d neighbours; the median filter takes at most %d",
+                         vpub[v], (int)nb[v].size(), MEDIAN_MAX - 1);
+                aj.insert(aj.end(), nb[v].begin(), nb[v].end());
+                ap[v + 1] = (int)aj.size();
+            }
+            t->adj_ptr = upload(ctx, ap, t->owned);
+            t->adj = upload(ctx, aj, t->owned);
+        }
         t->nV = nV;
         t->nVp = (nV + 7) / 8 * 8;
         t->nT = nT;
@@ -1408,8 +1461,10 @@ int npfem_add_cells(npfem_ctx *ctx, int type_id, int n_cells, const double *x0, 
         // the public layout grew: re-stage buffers
         dfree((void *&)ctx->d_f);
         dfree((void *&)ctx->d_stage);
+        dfree((void *&)ctx->d_ffilt);
         ctx->d_f = dalloc<double>(ctx, ctx->ndofs);
         ctx->d_stage = dalloc<double>(ctx, ctx->ndofs);
+        if (ctx->opt.force_median) ctx->d_ffilt = dalloc<double>(ctx, ctx->ndofs);
         invalidate_graph(ctx);
     });
 }

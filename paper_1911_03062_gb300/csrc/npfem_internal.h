@@ -8,3 +8,4 @@
 #include "gemm_tc.cuh"
 #include "gemm_grouped.cuh"
 #include "residual_ell.cuh"
+#include "filters.cuh"
