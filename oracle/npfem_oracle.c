@@ -853,6 +853,53 @@ void orc_velocity_cap(int nV, double *v, double umax) {
     }
 }
 
+/* Position-based-dynamics velocity damping (paper Sec. 2.1 cites it as the
+ * second viscoelastic proxy; definition from Mueller et al. 2007, Sec. 3.5).
+ * Reading: after the step, with the lumped masses m_i, total mass M:
+ *   x_cm = sum m_i x_i / M, v_cm = sum m_i v_i / M, r_i = x_i - x_cm,
+ *   L = sum r_i x (m_i v_i), I = sum m_i (|r_i|^2 E - r_i r_i^T), omega = I^{-1} L,
+ *   v_i <- v_i + kappa (v_cm + omega x r_i - v_i).
+ * The rigid part of the velocity field is kept, the rest scaled by (1 - kappa).
+ * x, v: [nV][3]; v in place.  Returns ORC_EINVAL if I is singular. */
+int orc_pbd_damping(const orc_type *T, const double *x, double *v, double kappa) {
+    int nV = T->nV;
+    double Mt = 0, xc[3] = {0, 0, 0}, vc[3] = {0, 0, 0};
+    for (int i = 0; i < nV; ++i) {
+        double m = T->mass[i];
+        Mt += m;
+        for (int c = 0; c < 3; ++c) { xc[c] += m * x[3*i+c]; vc[c] += m * v[3*i+c]; }
+    }
+    for (int c = 0; c < 3; ++c) { xc[c] /= Mt; vc[c] /= Mt; }
+    double L[3] = {0, 0, 0}, I[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < nV; ++i) {
+        double m = T->mass[i], r[3], p[3];
+        for (int c = 0; c < 3; ++c) { r[c] = x[3*i+c] - xc[c]; p[c] = m * v[3*i+c]; }
+        L[0] += r[1]*p[2] - r[2]*p[1];
+        L[1] += r[2]*p[0] - r[0]*p[2];
+        L[2] += r[0]*p[1] - r[1]*p[0];
+        double rr = r[0]*r[0] + r[1]*r[1] + r[2]*r[2];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                I[3*a+b] += m * ((a == b ? rr : 0.0) - r[a]*r[b]);
+    }
+    /* omega = I^{-1} L by the adjugate */
+    double C[9];
+    C[0] = I[4]*I[8] - I[5]*I[7]; C[1] = I[2]*I[7] - I[1]*I[8]; C[2] = I[1]*I[5] - I[2]*I[4];
+    C[3] = I[5]*I[6] - I[3]*I[8]; C[4] = I[0]*I[8] - I[2]*I[6]; C[5] = I[2]*I[3] - I[0]*I[5];
+    C[6] = I[3]*I[7] - I[4]*I[6]; C[7] = I[1]*I[6] - I[0]*I[7]; C[8] = I[0]*I[4] - I[1]*I[3];
+    double det = I[0]*C[0] + I[1]*C[3] + I[2]*C[6];
+    if (!(fabs(det) > 0)) return ORC_EINVAL;
+    double w[3];
+    for (int a = 0; a < 3; ++a) w[a] = (C[3*a]*L[0] + C[3*a+1]*L[1] + C[3*a+2]*L[2]) / det;
+    for (int i = 0; i < nV; ++i) {
+        double r[3];
+        for (int c = 0; c < 3; ++c) r[c] = x[3*i+c] - xc[c];
+        double rig[3] = {vc[0] + w[1]*r[2] - w[2]*r[1], vc[1] + w[2]*r[0] - w[0]*r[2], vc[2] + w[0]*r[1] - w[1]*r[0]};
+        for (int c = 0; c < 3; ++c) v[3*i+c] += kappa * (rig[c] - v[3*i+c]);
+    }
+    return ORC_OK;
+}
+
 /* n cells of one type, one after another (arrays: [n][nV][3]). */
 int orc_step_cells(const orc_type *T, int n, const double *xn, const double *vn, const double *f,
                    int K, int m, double c1, int max_bt, double *x_out, double *v_out) {

@@ -72,6 +72,8 @@ def lib():
             L.orc_force_median.argtypes = [vp, dp, dp]
             L.orc_force_median.restype = C.c_int
             L.orc_velocity_cap.argtypes = [C.c_int, dp, C.c_double]
+            L.orc_pbd_damping.argtypes = [vp, dp, dp, C.c_double]
+            L.orc_pbd_damping.restype = C.c_int
             _lib = L
     return _lib
 
@@ -215,6 +217,18 @@ def velocity_cap(v, umax):
     flat = out.reshape(-1, 3)
     lib().orc_velocity_cap(flat.shape[0], flat, float(umax))
     return out
+
+
+def pbd_damping(T, x, v, kappa):
+    """Copy of the velocities of cells ([n, nV, 3] or [nV, 3]) after PBD damping."""
+    xs = _c(x).reshape(-1, T.nV, 3)
+    out = _c(v).copy().reshape(-1, T.nV, 3)
+    for c in range(xs.shape[0]):
+        vc = np.ascontiguousarray(out[c])
+        if lib().orc_pbd_damping(T._h, np.ascontiguousarray(xs[c]), vc, float(kappa)) != 0:
+            raise ValueError("singular inertia tensor")
+        out[c] = vc
+    return out.reshape(np.shape(v))
 
 
 def polar(F):

@@ -468,3 +468,31 @@ def test_velocity_cap_closed_form(O):
     assert np.array_equal(w[below], v[below])
     assert np.allclose(m[~below], umax, rtol=1e-15, atol=0)
     assert np.allclose(w[~below] / m[~below, None], v[~below] / n[~below, None], rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------- f1: PBD velocity damping
+def test_pbd_damping_keeps_rigid_motion_and_scales_the_rest(O, rbc):
+    mt, T = rbc
+    rng = np.random.default_rng(23)
+    R = rot(5)
+    x = mt.rest @ R.T + np.array([3.0, -1.0, 2.0])
+    vcm, w = np.array([0.2, -0.1, 0.05]), np.array([0.3, 0.7, -0.4])
+    xc = x.mean(axis=0)                                  # uniform masses
+    rigid = vcm + np.cross(w, x - xc)
+    # a rigid velocity field is left unchanged
+    assert np.allclose(O.pbd_damping(T, x, rigid, 0.8), rigid, rtol=0, atol=1e-12)
+    # a field with zero momentum and zero angular momentum is scaled by (1 - kappa)
+    u = rng.standard_normal(x.shape)
+    u -= u.mean(axis=0)
+    r = x - xc
+    Iten = (np.sum(r * r) * np.eye(3) - r.T @ r)
+    Lmom = np.cross(r, u).sum(axis=0)
+    u -= np.cross(np.linalg.solve(Iten, Lmom), r)        # remove the rigid rotation part
+    assert np.allclose(O.pbd_damping(T, x, u, 0.7), 0.3 * u, rtol=0, atol=1e-12)
+    # linear superposition: rigid part kept, the rest scaled
+    assert np.allclose(O.pbd_damping(T, x, rigid + u, 0.5), rigid + 0.5 * u, rtol=0, atol=1e-12)
+    # linear and angular momentum are conserved
+    v0 = rigid + rng.standard_normal(x.shape)
+    d = O.pbd_damping(T, x, v0, 0.9)
+    assert np.allclose(d.sum(axis=0), v0.sum(axis=0), rtol=1e-12, atol=1e-12)
+    assert np.allclose(np.cross(r, d).sum(axis=0), np.cross(r, v0).sum(axis=0), rtol=1e-12, atol=1e-10)
