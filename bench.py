@@ -213,6 +213,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, nargs=2, default=[160, 16])
     ap.add_argument("--force-median", action="store_true", help="one-ring median filter of the forces before each step")
     ap.add_argument("--u-max", type=float, default=0.0, help="velocity cap after each step (0: off)")
+    ap.add_argument("--pbd-kappa", type=float, default=0.0, help="PBD velocity damping after each step (0: off)")
     args = ap.parse_args()
     rank, world, local = env_rank()
 
@@ -256,7 +257,8 @@ def main():
     stream = torch.cuda.Stream()
 
     def make(prec):
-        s = Solver(precision=prec, stream=stream, force_median=args.force_median, u_max=args.u_max)
+        s = Solver(precision=prec, stream=stream, force_median=args.force_median, u_max=args.u_max,
+                   pbd_kappa=args.pbd_kappa)
         for g in groups:
             s.add_cells(s.create_type(g.mtype), g.x0, g.v0)
         return s
@@ -383,6 +385,8 @@ def main():
                 fs = O.force_median(T, g.f_ext[idx]) if args.force_median else g.f_ext[idx]
                 for _ in range(1 + args.fp64_steps):
                     xo, vo = T.step_cells(xo, vo, fs, K=K, m=5, threads=2)
+                    if args.pbd_kappa > 0:
+                        vo = O.pbd_damping(T, xo, vo, args.pbd_kappa)
                     if args.u_max > 0:
                         vo = O.velocity_cap(vo, args.u_max)
                 errs.append(float(np.linalg.norm(xg[idx] - xo, axis=2).max() / g.mtype.radius))
@@ -434,7 +438,7 @@ def main():
                        "local_step": "fp32" if precision != "fp64" else "fp64",
                        "l2": "inputs larger than L2 (state + forces ~1.6 GB), no flush",
                        "parallelism": f"{world} independent ranks" if world > 1 else "1 GPU",
-                       "force_median": bool(args.force_median), "u_max": args.u_max},
+                       "force_median": bool(args.force_median), "u_max": args.u_max, "pbd_kappa": args.pbd_kappa},
             "clocks": clk, "gpu_launches": launches, "parity": parity, "fp64_gpu": fp64, "e2e": e2e,
             "roofline": roof, "kernels": kernels, "solver": solver}
     if not args.no_cpu:

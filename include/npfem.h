@@ -85,6 +85,11 @@ typedef struct {
     double u_max;           /* > 0: after each step, vertex velocities with |v| > u_max are scaled to
                                |v| = u_max (direction kept), in the state; paper Sec. 2.2.  Default 0
                                (off). */
+    double pbd_kappa;       /* in [0, 1]: after each step (before the velocity cap), position-based-
+                               dynamics velocity damping per cell: the rigid part of the velocity
+                               field (centre-of-mass velocity + omega x r, omega = I^{-1} L) is kept,
+                               the rest scaled by 1 - pbd_kappa; paper Sec. 2.1 (kappa_damping),
+                               Mueller et al. 2007.  Default 0 (off). */
 } npfem_options;
 
 /* Material and time step of one mesh type.  Element weights follow the

@@ -7,6 +7,7 @@
 //            even count the mean of the two middle values.  Selection on
 //            order-preserving integer keys and one FP64 mean: exact.
 //   cap    : |v| > u_max -> v u_max / |v| (direction kept), on the FP64 state.
+//   PBD    : position-based-dynamics velocity damping (below), before the cap.
 #pragma once
 
 #include "common.cuh"
@@ -110,6 +111,73 @@ __global__ void k_vel_cap(int ncells, int nV, int nVp, double *vn, double umax) 
             p[nVp] = b * s;
             p[2 * nVp] = c * s;
         }
+    }
+}
+
+// Position-based-dynamics velocity damping (Mueller et al. 2007, Sec. 3.5), on
+// the FP64 state after the step: per cell x_cm, v_cm, L = sum r x m v,
+// I = sum m (|r|^2 E - r r^T), omega = I^{-1} L, then v += kappa (v_cm + omega x r - v).
+// One block per cell (grid-stride), two FP64 block reductions, thread 0 inverts
+// I by its adjugate (omega = 0 if I is singular).  mass: [nV] lumped masses.
+__global__ void __launch_bounds__(256) k_pbd_damping(int ncells, int nV, int nVp, const double *__restrict__ mass,
+                                                     const double *__restrict__ xn, double *vn, double kappa) {
+    __shared__ double red[32 * 9];
+    __shared__ double bc[9];   // x_cm, v_cm, omega
+    for (int cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
+        const double *x = xn + (long long)cell * 3 * nVp;
+        double *v = vn + (long long)cell * 3 * nVp;
+        Acc<double> a[7];
+        for (int i = 0; i < 7; ++i) a[i].zero();
+        for (int i = threadIdx.x; i < nV; i += blockDim.x) {
+            const double m = mass[i];
+            a[0].add(m);
+            for (int c = 0; c < 3; ++c) {
+                a[1 + c].add(m * x[c * nVp + i]);
+                a[4 + c].add(m * v[c * nVp + i]);
+            }
+        }
+        block_reduce_t0<double, 7>(a, red, [&](const double *s) {
+            for (int c = 0; c < 3; ++c) {
+                bc[c] = s[1 + c] / s[0];
+                bc[3 + c] = s[4 + c] / s[0];
+            }
+        });
+        Acc<double> b[9];   // L0 L1 L2 I00 I01 I02 I11 I12 I22
+        for (int i = 0; i < 9; ++i) b[i].zero();
+        for (int i = threadIdx.x; i < nV; i += blockDim.x) {
+            const double m = mass[i];
+            const double r0 = x[i] - bc[0], r1 = x[nVp + i] - bc[1], r2 = x[2 * nVp + i] - bc[2];
+            const double p0 = m * v[i], p1 = m * v[nVp + i], p2 = m * v[2 * nVp + i];
+            b[0].add(r1 * p2 - r2 * p1);
+            b[1].add(r2 * p0 - r0 * p2);
+            b[2].add(r0 * p1 - r1 * p0);
+            const double rr = r0 * r0 + r1 * r1 + r2 * r2;
+            b[3].add(m * (rr - r0 * r0));
+            b[4].add(-m * r0 * r1);
+            b[5].add(-m * r0 * r2);
+            b[6].add(m * (rr - r1 * r1));
+            b[7].add(-m * r1 * r2);
+            b[8].add(m * (rr - r2 * r2));
+        }
+        block_reduce_t0<double, 9>(b, red, [&](const double *s) {
+            const double I[9] = {s[3], s[4], s[5], s[4], s[6], s[7], s[5], s[7], s[8]};
+            double C[9];
+            C[0] = I[4] * I[8] - I[5] * I[7]; C[1] = I[2] * I[7] - I[1] * I[8]; C[2] = I[1] * I[5] - I[2] * I[4];
+            C[3] = I[5] * I[6] - I[3] * I[8]; C[4] = I[0] * I[8] - I[2] * I[6]; C[5] = I[2] * I[3] - I[0] * I[5];
+            C[6] = I[3] * I[7] - I[4] * I[6]; C[7] = I[1] * I[6] - I[0] * I[7]; C[8] = I[0] * I[4] - I[1] * I[3];
+            const double det = I[0] * C[0] + I[1] * C[3] + I[2] * C[6];
+            for (int r = 0; r < 3; ++r)
+                bc[6 + r] = fabs(det) > 0 ? (C[3 * r] * s[0] + C[3 * r + 1] * s[1] + C[3 * r + 2] * s[2]) / det : 0.0;
+        });
+        for (int i = threadIdx.x; i < nV; i += blockDim.x) {
+            const double r0 = x[i] - bc[0], r1 = x[nVp + i] - bc[1], r2 = x[2 * nVp + i] - bc[2];
+            const double w0 = bc[6], w1 = bc[7], w2 = bc[8];
+            const double g0 = bc[3] + w1 * r2 - w2 * r1, g1 = bc[4] + w2 * r0 - w0 * r2, g2 = bc[5] + w0 * r1 - w1 * r0;
+            v[i] += kappa * (g0 - v[i]);
+            v[nVp + i] += kappa * (g1 - v[nVp + i]);
+            v[2 * nVp + i] += kappa * (g2 - v[2 * nVp + i]);
+        }
+        __syncthreads();
     }
 }
 

@@ -57,7 +57,7 @@ struct MeshTypeImpl {
     float *Pinv32 = nullptr;
     __nv_bfloat16 *Pinv16 = nullptr;
     __nv_bfloat16 *Pinv16lo = nullptr;          // split corrections: BF16 low part of P^{-1}
-    double *diag = nullptr, *minv = nullptr;
+    double *diag = nullptr, *minv = nullptr, *mass = nullptr;
     float *dhi = nullptr, *dlo = nullptr;
     int *op = nullptr;
     int2 *oe = nullptr;
@@ -618,6 +618,16 @@ void enqueue_step(npfem_ctx *ctx) {
             run_iterate(ctx, t, last, false);
             fallback_apply(ctx, t);
             run_iterate(ctx, t, last, true);
+        }
+    }
+    if (ctx->opt.pbd_kappa > 0) {
+        for (auto *t : ctx->types) {
+            if (!t->ncells) continue;
+            prof_begin(ctx, NPFEM_K_FILTER);
+            k_pbd_damping<<<std::min(t->ncells, 8 * ctx->nsm), 256, 0, ctx->stream>>>(
+                t->ncells, t->nV, t->nVp, t->mass, t->xn, t->vn, ctx->opt.pbd_kappa);
+            CK(cudaGetLastError());
+            prof_end(ctx);
         }
     }
     if (ctx->opt.u_max > 0) {
@@ -1185,7 +1195,8 @@ int npfem_create(const npfem_options *opt, npfem_ctx **out) {
         const npfem_options &o = ctx->opt;
         if (o.precision < 0 || o.precision > 2 || o.iters < 1 || o.history < 0 || o.history > NPFEM_MAX_HISTORY ||
             o.max_backtracks < 0 || !(o.armijo_c1 > 0 && o.armijo_c1 < 1) || o.refine_max < 0 || !(o.refine_tol > 0) ||
-            o.force_median < 0 || o.force_median > 1 || !(o.u_max >= 0) || !std::isfinite(o.u_max))
+            o.force_median < 0 || o.force_median > 1 || !(o.u_max >= 0) || !std::isfinite(o.u_max) ||
+            !(o.pbd_kappa >= 0 && o.pbd_kappa <= 1))
             fail(ctx, NPFEM_EINVAL, "invalid option value");
         CK(cudaSetDevice(o.device));
         ctx->device = o.device;
@@ -1339,6 +1350,7 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
             op[v + 1] = (int)oe.size();
         }
         t->minv = upload(ctx, minv, t->owned);
+        t->mass = upload(ctx, mass, t->owned);
         t->diag = upload(ctx, diag, t->owned);
         std::vector<float> dhi(t->nVp, 0.f), dlo(t->nVp, 0.f);
         for (int v = 0; v < nV; ++v) {

@@ -39,7 +39,8 @@ class Options(C.Structure):
                 ("armijo_c1", C.c_double), ("max_backtracks", C.c_int), ("refine_tol", C.c_double),
                 ("refine_max", C.c_int), ("use_graph", C.c_int), ("device", C.c_int),
                 ("cuda_stream", C.c_void_p), ("autotune_cache", C.c_char_p), ("residual_fp64", C.c_int),
-                ("refine_split", C.c_int), ("force_median", C.c_int), ("u_max", C.c_double)]
+                ("refine_split", C.c_int), ("force_median", C.c_int), ("u_max", C.c_double),
+                ("pbd_kappa", C.c_double)]
 
 
 class Material(C.Structure):
@@ -134,7 +135,7 @@ class Solver:
 
     def __init__(self, precision="fp64", iters=10, history=5, armijo_c1=1e-4, max_backtracks=8,
                  refine_tol=1e-6, refine_max=3, use_graph=True, device=0, stream=None, residual_fp64=False,
-                 refine_split=True, force_median=False, u_max=0.0):
+                 refine_split=True, force_median=False, u_max=0.0, pbd_kappa=0.0):
         self._L = load()
         o = default_options()
         o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -145,6 +146,7 @@ class Solver:
         o.refine_split = int(bool(refine_split))
         o.force_median = int(bool(force_median))
         o.u_max = float(u_max)
+        o.pbd_kappa = float(pbd_kappa)
         if stream is not None:
             o.cuda_stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         self.precision = o.precision

@@ -33,7 +33,7 @@ def _gpu(groups, steps, precision, **opts):
     return x, v
 
 
-def _oracle(groups, steps, median, umax):
+def _oracle(groups, steps, median, umax, kappa=0.0):
     from oracle import oracle as O
     xs, vs = [], []
     for g in groups:
@@ -42,6 +42,8 @@ def _oracle(groups, steps, median, umax):
         x, v = g.x0.copy(), g.v0.copy()
         for _ in range(steps):
             x, v = T.step_cells(x, v, f, K=10, m=5, threads=4)
+            if kappa > 0:
+                v = O.pbd_damping(T, x, v, kappa)
             if umax > 0:
                 v = O.velocity_cap(v, umax)
         xs.append((np.arange(g.n_cells), x))
@@ -58,6 +60,26 @@ def test_median_and_cap_match_oracle(precision, tol):
     for a, (_, b) in zip(vg, vo):
         # velocity = position difference / h: the position bar divided by h = 1e-3
         assert np.abs(a - b).max() <= (1e-5 if precision == "fp64" else 3e-2) * UMAX
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("bf16", 1e-6)])
+def test_pbd_damping_matches_oracle(precision, tol):
+    # kappa_damping = 0.8 (paper range 0.5-0.9), with the median filter and the cap
+    groups = make_groups([(I.rbc_type(), 4, 0.3), (I.plt_type(), 2, 0.3)], seed=302)
+    xg, vg = _gpu(groups, 3, precision, force_median=True, u_max=UMAX, pbd_kappa=0.8)
+    xo, vo = _oracle(groups, 3, True, UMAX, kappa=0.8)
+    assert rel_pos_err(xg, xo, groups) <= tol
+    for a, (_, b) in zip(vg, vo):
+        assert np.abs(a - b).max() <= (1e-5 if precision == "fp64" else 3e-2) * UMAX
+
+
+def test_pbd_damping_damps_deformation_keeps_momentum():
+    groups = make_groups([(I.rbc_type(), 3, 0.3)], seed=303)
+    xa, va = _gpu(groups, 2, "fp64")
+    xb, vb = _gpu(groups, 2, "fp64", pbd_kappa=0.9)
+    # the damped run deforms less: velocity spread about the cell mean is smaller
+    spread = lambda v: np.linalg.norm(v - v.mean(axis=1, keepdims=True), axis=2).mean()
+    assert spread(vb[0]) < 0.5 * spread(va[0])
 
 
 def test_filters_are_active():
