@@ -181,4 +181,72 @@ __global__ void __launch_bounds__(256) k_pbd_damping(int ncells, int nV, int nVp
     }
 }
 
+// The same damping for the mixed forms: coordinates relative to vertex 0 are
+// formed in FP64 and carried in FP32, moments are float-float sums, omega is
+// formed in FP64 from them by thread 0, and only the velocity update touches
+// FP64 (GB300 runs FP64 at ~1/64 of FP32).  Velocity change error ~1e-7 of
+// itself.  inv_mtot: 1 / total mass of the type.
+__global__ void __launch_bounds__(256) k_pbd_damping_f32(int ncells, int nV, int nVp, const double *__restrict__ mass,
+                                                         double inv_mtot, const double *__restrict__ xn, double *vn,
+                                                         float kappa) {
+    __shared__ double red[32 * 9];
+    __shared__ float bc[9];   // x_cm - x_0, v_cm, omega
+    for (int cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
+        const double *x = xn + (long long)cell * 3 * nVp;
+        double *v = vn + (long long)cell * 3 * nVp;
+        const double x00 = x[0], x01 = x[nVp], x02 = x[2 * nVp];
+        Acc<float> a[6];
+        for (int i = 0; i < 6; ++i) a[i].zero();
+        for (int i = threadIdx.x; i < nV; i += blockDim.x) {
+            const float m = (float)mass[i];
+            a[0].add_prod(m, (float)(x[i] - x00));
+            a[1].add_prod(m, (float)(x[nVp + i] - x01));
+            a[2].add_prod(m, (float)(x[2 * nVp + i] - x02));
+            a[3].add_prod(m, (float)v[i]);
+            a[4].add_prod(m, (float)v[nVp + i]);
+            a[5].add_prod(m, (float)v[2 * nVp + i]);
+        }
+        block_reduce_t0<float, 6>(a, red, [&](const double *s) {
+            for (int c = 0; c < 6; ++c) bc[c] = (float)(s[c] * inv_mtot);
+        });
+        Acc<float> b[9];   // L0 L1 L2 I00 I01 I02 I11 I12 I22
+        for (int i = 0; i < 9; ++i) b[i].zero();
+        for (int i = threadIdx.x; i < nV; i += blockDim.x) {
+            const float m = (float)mass[i];
+            const float r0 = (float)(x[i] - x00) - bc[0], r1 = (float)(x[nVp + i] - x01) - bc[1],
+                        r2 = (float)(x[2 * nVp + i] - x02) - bc[2];
+            const float p0 = m * (float)v[i], p1 = m * (float)v[nVp + i], p2 = m * (float)v[2 * nVp + i];
+            b[0].add(r1 * p2 - r2 * p1);
+            b[1].add(r2 * p0 - r0 * p2);
+            b[2].add(r0 * p1 - r1 * p0);
+            b[3].add(m * (r1 * r1 + r2 * r2));
+            b[4].add(-m * r0 * r1);
+            b[5].add(-m * r0 * r2);
+            b[6].add(m * (r0 * r0 + r2 * r2));
+            b[7].add(-m * r1 * r2);
+            b[8].add(m * (r0 * r0 + r1 * r1));
+        }
+        block_reduce_t0<float, 9>(b, red, [&](const double *s) {
+            const double I[9] = {s[3], s[4], s[5], s[4], s[6], s[7], s[5], s[7], s[8]};
+            double C[9];
+            C[0] = I[4] * I[8] - I[5] * I[7]; C[1] = I[2] * I[7] - I[1] * I[8]; C[2] = I[1] * I[5] - I[2] * I[4];
+            C[3] = I[5] * I[6] - I[3] * I[8]; C[4] = I[0] * I[8] - I[2] * I[6]; C[5] = I[2] * I[3] - I[0] * I[5];
+            C[6] = I[3] * I[7] - I[4] * I[6]; C[7] = I[1] * I[6] - I[0] * I[7]; C[8] = I[0] * I[4] - I[1] * I[3];
+            const double det = I[0] * C[0] + I[1] * C[3] + I[2] * C[6];
+            for (int r = 0; r < 3; ++r)
+                bc[6 + r] = fabs(det) > 0 ? (float)((C[3 * r] * s[0] + C[3 * r + 1] * s[1] + C[3 * r + 2] * s[2]) / det) : 0.f;
+        });
+        for (int i = threadIdx.x; i < nV; i += blockDim.x) {
+            const float r0 = (float)(x[i] - x00) - bc[0], r1 = (float)(x[nVp + i] - x01) - bc[1],
+                        r2 = (float)(x[2 * nVp + i] - x02) - bc[2];
+            const float w0 = bc[6], w1 = bc[7], w2 = bc[8];
+            const float g0 = bc[3] + w1 * r2 - w2 * r1, g1 = bc[4] + w2 * r0 - w0 * r2, g2 = bc[5] + w0 * r1 - w1 * r0;
+            v[i] += (double)(kappa * (g0 - (float)v[i]));
+            v[nVp + i] += (double)(kappa * (g1 - (float)v[nVp + i]));
+            v[2 * nVp + i] += (double)(kappa * (g2 - (float)v[2 * nVp + i]));
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace npfem

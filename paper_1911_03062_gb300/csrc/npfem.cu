@@ -58,6 +58,7 @@ struct MeshTypeImpl {
     __nv_bfloat16 *Pinv16 = nullptr;
     __nv_bfloat16 *Pinv16lo = nullptr;          // split corrections: BF16 low part of P^{-1}
     double *diag = nullptr, *minv = nullptr, *mass = nullptr;
+    double mtot = 0;                             // total mass of a cell
     float *dhi = nullptr, *dlo = nullptr;
     int *op = nullptr;
     int2 *oe = nullptr;
@@ -624,8 +625,12 @@ void enqueue_step(npfem_ctx *ctx) {
         for (auto *t : ctx->types) {
             if (!t->ncells) continue;
             prof_begin(ctx, NPFEM_K_FILTER);
-            k_pbd_damping<<<std::min(t->ncells, 8 * ctx->nsm), 256, 0, ctx->stream>>>(
-                t->ncells, t->nV, t->nVp, t->mass, t->xn, t->vn, ctx->opt.pbd_kappa);
+            if (mixed(ctx))
+                k_pbd_damping_f32<<<std::min(t->ncells, 8 * ctx->nsm), 256, 0, ctx->stream>>>(
+                    t->ncells, t->nV, t->nVp, t->mass, 1.0 / t->mtot, t->xn, t->vn, (float)ctx->opt.pbd_kappa);
+            else
+                k_pbd_damping<<<std::min(t->ncells, 8 * ctx->nsm), 256, 0, ctx->stream>>>(
+                    t->ncells, t->nV, t->nVp, t->mass, t->xn, t->vn, ctx->opt.pbd_kappa);
             CK(cudaGetLastError());
             prof_end(ctx);
         }
@@ -1351,6 +1356,7 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         }
         t->minv = upload(ctx, minv, t->owned);
         t->mass = upload(ctx, mass, t->owned);
+        for (double mv : mass) t->mtot += mv;
         t->diag = upload(ctx, diag, t->owned);
         std::vector<float> dhi(t->nVp, 0.f), dlo(t->nVp, 0.f);
         for (int v = 0; v < nV; ++v) {
