@@ -134,18 +134,15 @@ constexpr int SMEM_VECS = 3;   // pos, grad, gva: 3 nVp values each
 // S = V diag(l1, l2) V^T, sigma = sqrt(l), u_i = F v_i / sigma_i; a collapsed
 // triangle (sigma2 <= tol sigma1) gets a deterministic orthonormal u2.
 template <typename T>
-__device__ __forceinline__ void svd32(const T F[6], T U[6], T V[4], T s[2]) {
-    T a = F[0] * F[0] + F[2] * F[2] + F[4] * F[4];
-    T b = F[0] * F[1] + F[2] * F[3] + F[4] * F[5];
-    T c = F[1] * F[1] + F[3] * F[3] + F[5] * F[5];
+__device__ __forceinline__ void sym_eig2(T a, T b, T c, T &l1, T &l2, T &v1x, T &v1y) {
+    // [[a, b], [b, c]] = l1 v1 v1^T + l2 v2 v2^T, l1 >= l2 >= 0, v1 unit
     T half = T(0.5) * (a + c);
     T hd = T(0.5) * (a - c);
     T dd = sqrt(hd * hd + b * b);
-    T l1 = half + dd;
+    l1 = half + dd;
     T det = a * c - b * b;
-    T l2 = (l1 > T(0)) ? det / l1 : T(0);
+    l2 = (l1 > T(0)) ? det / l1 : T(0);
     if (l2 < T(0)) l2 = T(0);
-    T v1x, v1y;
     if (dd == T(0)) {
         v1x = T(1); v1y = T(0);
     } else {
@@ -154,6 +151,15 @@ __device__ __forceinline__ void svd32(const T F[6], T U[6], T V[4], T s[2]) {
         if (n1 >= n2) { T n = T(1) / sqrt(n1); v1x = w1x * n; v1y = w1y * n; }
         else          { T n = T(1) / sqrt(n2); v1x = w2x * n; v1y = w2y * n; }
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void svd32(const T F[6], T U[6], T V[4], T s[2]) {
+    T a = F[0] * F[0] + F[2] * F[2] + F[4] * F[4];
+    T b = F[0] * F[1] + F[2] * F[3] + F[4] * F[5];
+    T c = F[1] * F[1] + F[3] * F[3] + F[5] * F[5];
+    T l1, l2, v1x, v1y;
+    sym_eig2(a, b, c, l1, l2, v1x, v1y);
     T v2x = -v1y, v2y = v1x;
     V[0] = v1x; V[1] = v2x; V[2] = v1y; V[3] = v2y;
     s[0] = sqrt(l1);
@@ -235,22 +241,48 @@ __device__ __forceinline__ T tri_local(const T *pos, int nVp, int4 tv, const T (
         F[2 * c] = E1[c] * Di[0] + E2[c] * Di[2];
         F[2 * c + 1] = E1[c] * Di[1] + E2[c] * Di[3];
     }
-    T U[6], V[4], s[2], d[2];
-    svd32(F, U, V, s);
-    area_target(s[0], s[1], d);
-    T ns = T(0), na = T(0), nf = T(0);
+    // S = F^T F = V diag(s^2) V^T.  For a triangle that has not collapsed,
+    // R = ws (F - U V^T) + wa (F - U diag(d) V^T) = F G with the 2x2
+    // G = V diag((ws + wa) - (ws + wa d_i) / s_i) V^T (U = F V diag(1/s)),
+    // and |F - U V^T|^2 = sum (s_i - 1)^2, |F - U diag(d) V^T|^2 = sum (s_i - d_i)^2.
+    const T sa = F[0] * F[0] + F[2] * F[2] + F[4] * F[4];
+    const T sb = F[0] * F[1] + F[2] * F[3] + F[4] * F[5];
+    const T sc = F[1] * F[1] + F[3] * F[3] + F[5] * F[5];
+    T l1, l2, v1x, v1y;
+    sym_eig2(sa, sb, sc, l1, l2, v1x, v1y);
+    T s[2] = {sqrt(l1), sqrt(l2)}, d[2];
+    T ns, na, nf = sa + sc;
+    if (s[1] > T(Prec<T>::degen_tol) * s[0]) {
+        area_target(s[0], s[1], d);
+        const T g1 = (ws + wa) - (ws + wa * d[0]) / s[0], g2 = (ws + wa) - (ws + wa * d[1]) / s[1];
+        const T G00 = g1 * v1x * v1x + g2 * v1y * v1y, G11 = g1 * v1y * v1y + g2 * v1x * v1x;
+        const T G01 = (g1 - g2) * v1x * v1y;
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            T u1v = U[2 * r] * V[c * 2 + 0], u2v = U[2 * r + 1] * V[c * 2 + 1];
-            T rs = F[2 * r + c] - (u1v + u2v);
-            T ra = F[2 * r + c] - (d[0] * u1v + d[1] * u2v);
-            ns += rs * rs;
-            na += ra * ra;
-            nf += F[2 * r + c] * F[2 * r + c];
-            R[2 * r + c] = ws * rs + wa * ra;
+        for (int r = 0; r < 3; ++r) {
+            R[2 * r] = F[2 * r] * G00 + F[2 * r + 1] * G01;
+            R[2 * r + 1] = F[2 * r] * G01 + F[2 * r + 1] * G11;
         }
+        ns = (s[0] - T(1)) * (s[0] - T(1)) + (s[1] - T(1)) * (s[1] - T(1));
+        na = (s[0] - d[0]) * (s[0] - d[0]) + (s[1] - d[1]) * (s[1] - d[1]);
+    } else {
+        // collapsed: the polar factor needs the chosen second left vector
+        T U[6], V[4];
+        svd32(F, U, V, s);
+        area_target(s[0], s[1], d);
+        ns = T(0);
+        na = T(0);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                T u1v = U[2 * r] * V[c * 2 + 0], u2v = U[2 * r + 1] * V[c * 2 + 1];
+                T rs = F[2 * r + c] - (u1v + u2v);
+                T ra = F[2 * r + c] - (d[0] * u1v + d[1] * u2v);
+                ns += rs * rs;
+                na += ra * ra;
+                R[2 * r + c] = ws * rs + wa * ra;
+            }
+    }
     en += T(0.5) * ws * ns + T(0.5) * wa * na;
     al += (ws * sqrt(ns) + wa * sqrt(na)) * sqrt(nf);
     T C0 = E1[1] * E2[2] - E1[2] * E2[1], C1 = E1[2] * E2[0] - E1[0] * E2[2], C2 = E1[0] * E2[1] - E1[1] * E2[0];
