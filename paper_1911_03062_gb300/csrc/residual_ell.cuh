@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(RESID_MAX_THREADS, (KR * W <= 24) ? 3 : 2) k_r
     __shared__ int cell_sh[RESID_STAGES];
     __shared__ float4 red[2][RESID_MAX_THREADS / 32];
     __shared__ int abort_sh;
+    __shared__ int conv_sh;    // the current cell converged (deferred stores)
 
     const int nVp = a.nVp, n3 = 3 * nVp, nV = a.nV;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
@@ -119,6 +120,22 @@ __global__ void __launch_bounds__(RESID_MAX_THREADS, (KR * W <= 24) ? 3 : 2) k_r
         const float *zs = ring + (size_t)(2 * s) * n3;
         const float *qs = zs + n3;
         const size_t base = (size_t)cell * n3;
+        // After the first pass most cells converge: there r is kept in registers and
+        // stored only for a cell that did not (one extra barrier per cell).
+        const bool defer = !a.first && !a.final_pass;
+        auto store_r = [&](int v, const float (&r)[3]) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (a.r_bf16) {
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(r[c]);
+                    a.r_bf16[base + c * nVp + v] = hi;
+                    if (a.r_lo) a.r_lo[base + c * nVp + v] = __float2bfloat16_rn(r[c] - __bfloat162float(hi));
+                } else {
+                    a.r_f32[base + c * nVp + v] = r[c];
+                }
+            }
+        };
+        float rk[KR][3];
         float nr = 0.f, nq = 0.f;
 #pragma unroll
         for (int k = 0; k < KR; ++k) {
@@ -144,18 +161,9 @@ __global__ void __launch_bounds__(RESID_MAX_THREADS, (KR * W <= 24) ? 3 : 2) k_r
                     nq = fmaf(qv, qv, nq);
                 }
             }
-            if (!a.final_pass) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (a.r_bf16) {
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(r[c]);
-                        a.r_bf16[base + c * nVp + v] = hi;
-                        if (a.r_lo) a.r_lo[base + c * nVp + v] = __float2bfloat16_rn(r[c] - __bfloat162float(hi));
-                    } else {
-                        a.r_f32[base + c * nVp + v] = r[c];
-                    }
-                }
-            }
+            for (int c = 0; c < 3; ++c) rk[k][c] = r[c];
+            if (!a.final_pass && !defer) store_r(v, r);
         }
         Acc<float> acc[2];
         acc[0].zero();
@@ -189,6 +197,7 @@ __global__ void __launch_bounds__(RESID_MAX_THREADS, (KR * W <= 24) ? 3 : 2) k_r
                 } else {
                     if (ok) atomicMax(&a.st->max_resid_bits, __float_as_uint(ratio));
                     a.conv[cell] = ok ? 1 : 0;
+                    conv_sh = ok ? 1 : 0;
                     if (!ok) {
                         atomicOr(a.any_active, 1);
                         atomicAdd(&a.st->refine_sweeps, 1ull);
@@ -196,6 +205,16 @@ __global__ void __launch_bounds__(RESID_MAX_THREADS, (KR * W <= 24) ? 3 : 2) k_r
                 }
             }
             issue(s);       // every thread has finished reading stage s
+        }
+        if (defer) {
+            __syncthreads();
+            if (!conv_sh) {
+#pragma unroll
+                for (int k = 0; k < KR; ++k) {
+                    const int v = tid + k * nt;
+                    if (v < nVp) store_r(v, rk[k]);
+                }
+            }
         }
     }
     if (abort_sh) {
