@@ -155,6 +155,46 @@ __device__ __forceinline__ void block_reduce_t0(Acc<T> (&a)[N], double *red, F &
     __syncthreads();
 }
 
+// The two halves of block_reduce_t0 for callers that already have barriers:
+// warp_partials_store (every thread) before a __syncthreads, block_combine_t0
+// (every thread; warp 0 merges, thread 0 calls fn) after it; fn's results are
+// visible after the caller's next __syncthreads.  Same order as block_reduce_t0.
+template <typename T, int N>
+__device__ __forceinline__ void warp_partials_store(Acc<T> (&a)[N], double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i) a[i].merge_shfl(0xffffffffu, off);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) a[i].store(red + warp * N + i);
+}
+
+template <typename T, int N, typename F>
+__device__ __forceinline__ void block_combine_t0(const double *red, F &&fn) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    if (warp != 0) return;
+    Acc<T> t[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (lane < nw) t[i].load(red + lane * N + i);
+        else t[i].zero();
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        if (off >= nw * 2) continue;
+#pragma unroll
+        for (int i = 0; i < N; ++i) t[i].merge_shfl(0xffffffffu, off);
+    }
+    if (lane == 0) {
+        double s[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) s[i] = t[i].get();
+        fn(s);
+    }
+}
+
 // ------------------------------------------------------------ type traits
 template <typename T> struct Prec;
 template <> struct Prec<double> {

@@ -350,6 +350,7 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             if (S.bc->i[3]) break;
             alpha = S.bc->t[2];
         }
+        load_vec<T, EPT>(a.grad + base, gr, n3);      // old gradient (dead during the search)
         store_vec<T, EPT>(a.delta + base, dt, n3);
         store_vec<T, EPT>(a.grad + base, gt, n3);
         if (a.last) {
