@@ -556,118 +556,56 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
     //    iteration p_{j+1} = x + lambda_j gV(p_j),
     //    lambda_j = (V0 - V(p_j) - gV(p_j).(x - p_j)) / |gV(p_j)|^2,
     //    stopped once |V(p_j) - V0| <= tol V0 or after 8 updates.  gV(x) was
-    //    gathered with the triangles (gva), lambda_0 formed above.  The first
-    //    update's volume check shares the final reduction (energy, allowance,
-    //    V(p_1)); if it fails, the later updates run (gradients at p_j from the
-    //    one-ring cross products, overwriting gva) and the final sums are redone.
+    //    gathered with the triangles (gva) and lambda_0 formed during the hinge
+    //    phase; later gradients come from the one-ring cross products (into gva).
+    //    pos holds p.
     T p[EPT];
 #pragma unroll
     for (int j = 0; j < EPT; ++j) p[j] = x[j];
-    const bool update = !S.bc->i[0];
-    if (update) {
-        const T lam = S.bc->t[0];
-#pragma unroll
-        for (int g4 = 0; g4 < EPT / 4; ++g4) {
-            const int e0 = 4 * (tid + g4 * B);
-            if (e0 >= n3) continue;
-            T gv[4], pv[4];
-            ld4(gva + e0, gv);                              // zero on padding
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int j = 4 * g4 + i;
-                p[j] = x[j] + lam * gv[i];
-                pv[i] = p[j];
-            }
-            st4(pos + e0, pv);
-        }
-        __syncthreads();
-    }
-    // 5. gradient to registers (+ volume term) and the energy, for the current p
-    T env = T(0), alv = T(0);
-    auto volume_term = [&]() {
-        env = T(0);
-        alv = T(0);
-#pragma unroll
-        for (int g4 = 0; g4 < EPT / 4; ++g4) {
-            const int e0 = 4 * (tid + g4 * B);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) gr[4 * g4 + i] = T(0);
-            if (e0 >= n3) continue;
-            int v0;
-            elem_cv(e0, nVp, v0);
-            T gs[4];
-            ld4(gsh + e0, gs);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (v0 + i >= nV) continue;
-                const int j = 4 * g4 + i;
-                T r = x[j] - p[j];
-                env += T(0.5) * tc.kv * r * r;
-                alv += tc.kv * fabs(r) * fabs(x[j]);
-                gr[j] = gs[i] + tc.kv * r;
-            }
-        }
-    };
-    volume_term();
     {
-        Acc<T> fin[3];
-        fin[0].zero();
-        fin[1].zero();
-        fin[2].zero();
-        fin[0].add(en + env);
-        fin[1].add(al + alv);
-        if (update) volume_pass(tc, pos, nVp, fin[2]);    // 6 V(p_1)
-        block_reduce_t0<T, 3>(fin, S.red, [&](const double *s) {
-            const bool ok = !update || fabs(tc.V0x6 - s[2]) <= tc.vtol6;
-            S.bc->i[1] = !ok;
-            if (ok) done(s[0], 8.0 * Prec<T>::round_unit * s[1]);
-            else S.bc->d[0] = s[2];
-        });
-    }
-    if (S.bc->i[1]) {
-        // rare: updates 2 .. 8
         T *gV = gva;
-        for (int it = 1; S.bc->i[1]; ++it) {
-            // gradient at p_it, vertex by vertex: sum over the one-ring of (p_b - q) x (p_c - q) / 6
-            const T q0 = pos[0], q1 = pos[nVp], q2 = pos[2 * nVp];
-            for (int v = tid; v < nV; v += B) {
-                T g[3] = {T(0), T(0), T(0)};
-                const int end = tc.vt_ptr[v + 1];
-                for (int k = tc.vt_ptr[v]; k < end; ++k) {
-                    const int bc = tc.vt[k].bc;
-                    const int vb = bc & 0xffff, vc = bc >> 16;
-                    T bx = pos[vb] - q0, by = pos[nVp + vb] - q1, bz = pos[2 * nVp + vb] - q2;
-                    T cx = pos[vc] - q0, cy = pos[nVp + vc] - q1, cz = pos[2 * nVp + vc] - q2;
-                    g[0] += by * cz - bz * cy;
-                    g[1] += bz * cx - bx * cz;
-                    g[2] += bx * cy - by * cx;
+        for (int it = 0; !S.bc->i[0]; ++it) {
+            if (it > 0) {
+                const T q0 = pos[0], q1 = pos[nVp], q2 = pos[2 * nVp];
+                for (int v = tid; v < nV; v += B) {
+                    T g[3] = {T(0), T(0), T(0)};
+                    const int end = tc.vt_ptr[v + 1];
+                    for (int k = tc.vt_ptr[v]; k < end; ++k) {
+                        const int bc = tc.vt[k].bc;
+                        const int vb = bc & 0xffff, vc = bc >> 16;
+                        T bx = pos[vb] - q0, by = pos[nVp + vb] - q1, bz = pos[2 * nVp + vb] - q2;
+                        T cx = pos[vc] - q0, cy = pos[nVp + vc] - q1, cz = pos[2 * nVp + vc] - q2;
+                        g[0] += by * cz - bz * cy;
+                        g[1] += bz * cx - bx * cz;
+                        g[2] += bx * cy - by * cx;
+                    }
+                    gV[v] = g[0] / T(6);
+                    gV[nVp + v] = g[1] / T(6);
+                    gV[2 * nVp + v] = g[2] / T(6);
                 }
-                gV[v] = g[0] / T(6);
-                gV[nVp + v] = g[1] / T(6);
-                gV[2 * nVp + v] = g[2] / T(6);
-            }
-            __syncthreads();
-            Acc<T> a2[2];
-            a2[0].zero();
-            a2[1].zero();
+                __syncthreads();
+                Acc<T> a2[2];
+                a2[0].zero();
+                a2[1].zero();
 #pragma unroll
-            for (int g4 = 0; g4 < EPT / 4; ++g4) {
-                const int e0 = 4 * (tid + g4 * B);
-                if (e0 >= n3) continue;
-                int v0;
-                elem_cv(e0, nVp, v0);
-                T gv[4];
-                ld4(gV + e0, gv);
+                for (int g4 = 0; g4 < EPT / 4; ++g4) {
+                    const int e0 = 4 * (tid + g4 * B);
+                    if (e0 >= n3) continue;
+                    int v0;
+                    elem_cv(e0, nVp, v0);
+                    T gv[4];
+                    ld4(gV + e0, gv);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (v0 + i >= nV) continue;
-                    a2[0].add_prod(gv[i], gv[i]);
-                    a2[1].add_prod(gv[i], x[4 * g4 + i] - p[4 * g4 + i]);
+                    for (int i = 0; i < 4; ++i) {
+                        if (v0 + i >= nV) continue;
+                        a2[0].add_prod(gv[i], gv[i]);
+                        a2[1].add_prod(gv[i], x[4 * g4 + i] - p[4 * g4 + i]);
+                    }
                 }
+                block_reduce_t0<T, 2>(a2, S.red, [&](const double *s) {
+                    S.bc->t[0] = T(tc.V0x6 - S.bc->d[0] - 6.0 * s[1]) / T(6.0 * s[0]);
+                });
             }
-            block_reduce_t0<T, 2>(a2, S.red, [&](const double *s) {
-                S.bc->t[0] = T(tc.V0x6 - S.bc->d[0] - 6.0 * s[1]) / T(6.0 * s[0]);
-            });
             const T lam = S.bc->t[0];
 #pragma unroll
             for (int g4 = 0; g4 < EPT / 4; ++g4) {
@@ -690,18 +628,38 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
             a3[0].zero();
             volume_pass(tc, pos, nVp, a3[0]);
             block_reduce_t0<T, 1>(a3, S.red, [&](const double *s) {
-                S.bc->d[0] = s[0];                           // 6 V(p)
-                S.bc->i[1] = !(fabs(tc.V0x6 - s[0]) <= tc.vtol6 || it == 7);
+                S.bc->d[0] = s[0];
+                S.bc->i[0] = fabs(tc.V0x6 - s[0]) <= tc.vtol6 || it == 7;
             });
         }
-        volume_term();
-        Acc<T> fin[2];
-        fin[0].zero();
-        fin[1].zero();
-        fin[0].add(en + env);
-        fin[1].add(al + alv);
-        block_reduce_t0<T, 2>(fin, S.red, [&](const double *s) { done(s[0], 8.0 * Prec<T>::round_unit * s[1]); });
     }
+    // 5. gradient to registers (+ volume term), energy
+#pragma unroll
+    for (int g4 = 0; g4 < EPT / 4; ++g4) {
+        const int e0 = 4 * (tid + g4 * B);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) gr[4 * g4 + i] = T(0);
+        if (e0 >= n3) continue;
+        int v0;
+        elem_cv(e0, nVp, v0);
+        T gs[4];
+        ld4(gsh + e0, gs);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (v0 + i >= nV) continue;
+            const int j = 4 * g4 + i;
+            T r = x[j] - p[j];
+            en += T(0.5) * tc.kv * r * r;
+            al += tc.kv * fabs(r) * fabs(x[j]);
+            gr[j] = gs[i] + tc.kv * r;
+        }
+    }
+    Acc<T> fin[2];
+    fin[0].zero();
+    fin[1].zero();
+    fin[0].add(en);
+    fin[1].add(al);
+    block_reduce_t0<T, 2>(fin, S.red, [&](const double *s) { done(s[0], 8.0 * Prec<T>::round_unit * s[1]); });
 }
 
 }  // namespace npfem
