@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 # averaged over the RBC and platelet launches of one step, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass, launches of one timed step).
 # Set to None whenever k_iterate changes until it is captured again.
-ITERATE_TRAFFIC = 2.1875e9
+ITERATE_TRAFFIC = 2.1418e9
 PARITY_CELLS = 16        # cells per mesh type compared with the oracle (evenly spaced)
 METRIC = "cell-iterations/sec at 50k cells, mixed vs FP64 GPU at ≤1e-6 rel pos error"
 UNIT = "cell-iterations/s"

@@ -47,6 +47,7 @@ constexpr uint32_t EPI_SMEM = 4 * 2 * EPI_BOX_BYTES;   // 4 warps x double buffe
 struct GroupArgs {
     int nprob, total_units, stages, accumulate, stage_bytes_b;   // B-tile bytes per stage (max n_tile)
     int split;   // 1: Z (+)= Q_hi P_hi + Q_lo P_hi + Q_hi P_lo (BF16 parts, FP32 accumulation)
+    const int *active;   // corrections: 0 here = no cell left unconverged, nothing to do (null: run)
     GroupProblem pr[MAXG];
     DevStatus *st;
 };
@@ -83,6 +84,7 @@ __device__ __forceinline__ bool unit_skipped(const GroupArgs &a, const Unit &w) 
 
 template <bool TF32>
 __global__ void __launch_bounds__(192, 1) k_gemm_grouped(const __grid_constant__ GroupMaps maps, GroupArgs a) {
+    if (a.active && *a.active == 0) return;      // uniform: before any barrier or TMEM use
     extern __shared__ __align__(1024) uint8_t smem_g[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t base = smem_u32(smem_g);

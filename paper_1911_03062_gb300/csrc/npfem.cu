@@ -41,6 +41,7 @@ void fail(npfem_ctx *ctx, int code, const char *fmt, ...);
     } while (0)
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+constexpr int NPFEM_SWEEP_FLAGS = 16;   // per-sweep "a cell is still unconverged" flags (last one: final pass)
 thread_local std::string g_create_error = "no error";   // message of the last failed npfem_create
 
 }  // namespace
@@ -419,7 +420,8 @@ struct GemmItem {
 };
 
 // One persistent launch (per MAXG items) over every item's (row tile, N tile) units.
-void gemm_group(npfem_ctx *ctx, const std::vector<GemmItem> &items, int accumulate, bool split_form = false) {
+void gemm_group(npfem_ctx *ctx, const std::vector<GemmItem> &items, int accumulate, bool split_form = false,
+                const int *active = nullptr) {
     for (size_t i0 = 0; i0 < items.size(); i0 += tc::MAXG) {
         const size_t i1 = std::min(items.size(), i0 + tc::MAXG);
         tc::GroupArgs g{};
@@ -456,6 +458,7 @@ void gemm_group(npfem_ctx *ctx, const std::vector<GemmItem> &items, int accumula
         g.stages = stages;
         g.accumulate = accumulate;
         g.split = split_form ? 1 : 0;
+        g.active = active;
         g.stage_bytes_b = max_nt * tc::KB_BYTES;
         g.st = ctx->d_st;
         const int grid = std::min(units, ctx->nsm);
@@ -474,7 +477,8 @@ void gemm_tc(npfem_ctx *ctx, MeshTypeImpl *t, const CUtensorMap &mapQ, int rows,
 }
 
 void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, const float *z, void *r,
-              int *conv, int first, int final_pass, __nv_bfloat16 *r_lo = nullptr) {
+              int *conv, int first, int final_pass, __nv_bfloat16 *r_lo = nullptr, int *active = nullptr,
+              const int *prev_active = nullptr) {
     ResidArgs a{};
     a.ncells = rows_cells;
     a.nV = t->nV;
@@ -493,7 +497,8 @@ void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, c
     a.r_f32 = bf16(ctx) ? nullptr : (float *)r;
     a.r_lo = r_lo;
     a.conv = conv;
-    a.any_active = ctx->d_any;
+    a.any_active = active ? active : ctx->d_any + NPFEM_SWEEP_FLAGS - 1;
+    a.prev_active = prev_active;
     a.st = ctx->d_st;
     a.n_off = t->n_off;
     if (t->ell_W && !ctx->opt.residual_fp64) {
@@ -514,7 +519,8 @@ void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, c
         e.r_f32 = a.r_f32;
         e.r_lo = r_lo;
         e.conv = conv;
-        e.any_active = ctx->d_any;
+        e.any_active = a.any_active;
+        e.prev_active = prev_active;
         e.st = ctx->d_st;
         const int grid = std::min(rows_cells, t->ell_grid);
         prof_begin(ctx, NPFEM_K_RESIDUAL);
@@ -557,18 +563,23 @@ void apply_all(npfem_ctx *ctx) {
         first.push_back(GemmItem{t, &t->mapQ, 3 * t->ncells, &t->mapZ, nullptr});
         corr.push_back(GemmItem{t, &t->mapR, 3 * t->ncells, &t->mapZ, t->conv, split(ctx) ? &t->mapRlo : nullptr});
     }
+    // per-sweep flags: residual pass s raises flag s when it leaves a cell unconverged;
+    // the correction of sweep s and every later pass return at once while it is 0
+    CK(cudaMemsetAsync(ctx->d_any, 0, NPFEM_SWEEP_FLAGS * sizeof(int), ctx->stream));
+    auto flag = [&](int sweep) { return ctx->d_any + std::min(sweep, NPFEM_SWEEP_FLAGS - 2); };
     gemm_group(ctx, first, 0);
     for (int s = 0; s < ctx->opt.refine_max; ++s) {
         for (auto *t : ctx->types)
             if (t->ncells)
                 residual(ctx, t, t->ncells, (const float *)t->q, (const float *)t->z, t->rlo, t->conv, s == 0, 0,
-                         t->rlo_lo);
-        gemm_group(ctx, corr, 1, split(ctx));
+                         t->rlo_lo, flag(s), s == 0 ? nullptr : flag(s - 1));
+        gemm_group(ctx, corr, 1, split(ctx), flag(s));
     }
     for (auto *t : ctx->types)
         if (t->ncells)
             residual(ctx, t, t->ncells, (const float *)t->q, (const float *)t->z, nullptr, t->conv,
-                     ctx->opt.refine_max == 0, 1);
+                     ctx->opt.refine_max == 0, 1, nullptr, ctx->d_any + NPFEM_SWEEP_FLAGS - 1,
+                     ctx->opt.refine_max == 0 ? nullptr : flag(ctx->opt.refine_max - 1));
 }
 
 void fallback_apply(npfem_ctx *ctx, MeshTypeImpl *t) {
@@ -1221,7 +1232,7 @@ int npfem_create(const npfem_options *opt, npfem_ctx **out) {
         }
         ctx->d_st = dalloc<DevStatus>(ctx, 1);
         ctx->d_fslot = dalloc<double *>(ctx, 1);
-        ctx->d_any = dalloc<int>(ctx, 1);
+        ctx->d_any = dalloc<int>(ctx, NPFEM_SWEEP_FLAGS);
         CK(cudaMallocHost(&ctx->h_st, sizeof(DevStatus)));
         set_kernel_attrs(ctx);
         CK(cudaStreamSynchronize(ctx->stream));

@@ -36,12 +36,14 @@ struct ResidEllArgs {
     __nv_bfloat16 *r_lo;             // split corrections: r - r_hi in BF16, or null
     float *r_f32;                    // TF32 form
     int *conv;                       // [cell]
+    const int *prev_active;          // the previous sweep left no cell unconverged if 0 here (null: run)
     int *any_active;
     DevStatus *st;
 };
 
 template <int W, int KR>
 __global__ void __launch_bounds__(RESID_MAX_THREADS, (KR * W <= 24) ? 3 : 2) k_residual_ell(ResidEllArgs a) {
+    if (a.prev_active && *a.prev_active == 0) return;   // uniform: every cell already converged
     extern __shared__ __align__(16) unsigned char smem_res[];
     __shared__ uint64_t full[RESID_STAGES];
     __shared__ int cell_sh[RESID_STAGES];

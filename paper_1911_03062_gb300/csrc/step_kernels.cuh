@@ -552,6 +552,7 @@ struct ResidArgs {
     __nv_bfloat16 *r_lo;     // split corrections: r - r_hi in BF16, or null
     float *r_f32;            // TF32 form
     int *conv;               // [cell]
+    const int *prev_active;  // the previous sweep left no cell unconverged if 0 here (null: run)
     int *any_active;         // set when a cell is not converged
     DevStatus *st;
 };
@@ -563,6 +564,7 @@ struct ResidArgs {
 // the two norms by shuffles.
 template <bool FP64R>
 __global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
+    if (a.prev_active && *a.prev_active == 0) return;   // uniform: every cell already converged
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nVp = a.nVp, n3 = 3 * nVp, nV = a.nV;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
