@@ -51,7 +51,7 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
 
 // Sum accumulators: FP64 for the FP64 path; float-float (about 44 bits) for
 // the FP32 path, whose per-thread partials are combined across the block in
-// FP64 (see block_reduce).
+// FP64 (see block_reduce_t0).
 template <typename T> struct Acc;
 
 template <> struct Acc<double> {
@@ -88,32 +88,6 @@ template <> struct Acc<float> {
     }
     __device__ __forceinline__ double get() const { return (double)v.hi + (double)v.lo; }
 };
-
-// Block-wide sum of N accumulators; every thread receives the N totals.
-// Scratch: red[32 * N + N] doubles in shared memory.  Deterministic: fixed
-// shuffle tree inside each warp, warps combined in index order in FP64.
-template <typename T, int N>
-__device__ __forceinline__ void block_reduce(Acc<T> (&a)[N], double (&out)[N], double *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-        for (int i = 0; i < N; ++i) a[i].merge_shfl(0xffffffffu, off);
-    if (lane == 0)
-#pragma unroll
-        for (int i = 0; i < N; ++i) red[warp * N + i] = a[i].get();
-    __syncthreads();
-    if (threadIdx.x < N) {
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += red[w * N + threadIdx.x];
-        red[32 * N + threadIdx.x] = s;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < N; ++i) out[i] = red[32 * N + i];
-    __syncthreads();
-}
 
 // Block-wide sums of N accumulators: each warp reduces by shuffles, warp 0
 // combines the per-warp partials by a second shuffle tree (fixed order, so

@@ -29,7 +29,6 @@ constexpr int MAXG = 16;
 
 struct GroupProblem {
     int rows, nV, nVp, n_tile, n_ntiles, m_tiles, kblocks, unit_begin;
-    float *Z;
     const int *conv;
 };
 

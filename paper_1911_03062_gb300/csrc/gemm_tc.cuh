@@ -1,21 +1,18 @@
-// gemm_tc.cuh -- the global step on tcgen05 tensor cores (sm_103a):
+// gemm_tc.cuh -- tcgen05 / TMA / mbarrier building blocks (sm_103a) of the
+// global step z = P^{-1} q (the grouped kernel in gemm_grouped.cuh):
 //
 //   Z[r][v] (+)= sum_k Q[r][k] * Pinv[v][k]      (z = P^{-1} q for every RHS row r)
 //
-// Rows r are the stacked x/y/z right-hand sides of all cells of one mesh type
+// Rows r are the stacked x/y/z right-hand sides of all cells of a mesh type
 // (one row = one component of one cell, vertex contiguous, stride nVp), so the
 // apply is one [3C x nV] x [nV x nV] product with the type's shared inverse
 // (Supplementary Sec. 2.1: the constant Hessian approximation of the
 // quadratic energies, applied to all cells at once).
 //
-// Mapping: MMA A operand = a 128-row tile of Q (K-major), B operand = an
-// N-row tile of P^{-1} (K-major, N <= 256), accumulator D = 128 x N FP32 in
-// tensor memory.  Operands are staged by TMA (128-byte swizzle) through an
-// S-stage mbarrier pipeline; one thread issues TMA, one thread issues
-// tcgen05.mma, all four warps drain TMEM (tcgen05.ld) and store Z.
-// Element type: BF16 (kind::f16) or FP32 read as TF32 (kind::tf32), FP32
-// accumulation in both.  Every wait is bounded: on expiry the kernel records
-// NPFEM_ETIMEOUT, waits (bounded) for its own copies, frees TMEM and returns.
+// Here: bounded mbarrier waits, 2D TMA loads / stores / reduce-adds and 1D
+// bulk copies, TMEM allocation, the SW128 K-major shared-memory descriptor,
+// the instruction descriptor, tcgen05.mma (kind::f16 BF16 / kind::tf32) with
+// its commit, and the 32-column TMEM load.
 #pragma once
 
 #include <cuda.h>
@@ -175,151 +172,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-struct GemmArgs {
-    int rows, nV, nVp;           // Q / Z: rows x nVp (K = nV valid columns)
-    int n_tile;                  // N of one tile (multiple of 16, <= 256)
-    int stages;
-    int accumulate;              // Z += product
-    const int *conv;             // per cell: skip tiles whose cells are all converged (or null)
-    float *Z;
-    DevStatus *st;
-};
-
-// smem: [stages][A 128 x 128B | B n_tile x 128B] (1024-aligned), then
-// full[stages], empty[stages], accum barrier, tmem address.
-template <bool TF32>
-__global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapQ,
-                                                     const __grid_constant__ CUtensorMap mapP, GemmArgs a) {
-    extern __shared__ __align__(1024) uint8_t smem_tc[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n0 = blockIdx.x * a.n_tile;
-    const int m0 = blockIdx.y * BM;
-    if (a.conv) {
-        // all cells of this row tile converged: nothing to correct
-        int c0 = m0 / 3, c1 = min(a.rows - 1, m0 + BM - 1) / 3;
-        int any = 0;
-        for (int c = c0 + threadIdx.x; c <= c1; c += blockDim.x) any |= !a.conv[c];
-        if (!__syncthreads_or(any)) return;
-    }
-    uint32_t base = smem_u32(smem_tc);
-    uint32_t pad = ((base + 1023u) & ~1023u) - base;
-    uint8_t *tiles = smem_tc + pad;
-    const uint32_t a_bytes = BM * KB_BYTES, b_bytes = (uint32_t)a.n_tile * KB_BYTES;
-    const uint32_t stage_bytes = a_bytes + b_bytes;
-    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + (size_t)a.stages * stage_bytes);
-    uint64_t *empty = full + a.stages;
-    uint64_t *accum = empty + a.stages;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
-    __shared__ int abort_sh;
-    volatile int &abort_flag = abort_sh;
-
-    const int kblocks = (a.nV * (TF32 ? 4 : 2) + KB_BYTES - 1) / KB_BYTES;
-    const int k_per_block = TF32 ? 32 : 64;      // elements of K in one stage
-    const uint32_t tcols = a.n_tile <= 32 ? 32 : (a.n_tile <= 64 ? 64 : (a.n_tile <= 128 ? 128 : 256));
-
-    if (threadIdx.x == 0) {
-        abort_flag = 0;
-        for (int s = 0; s < a.stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        mbar_init(accum, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 2) tmem_alloc(tmem_slot, tcols);
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = make_idesc(TF32 ? 2u : 1u, BM, a.n_tile);
-
-    if (warp == 0 && lane == 0) {
-        // producer: TMA loads of A (Q rows) and B (P^{-1} rows), K in 128-byte steps
-        int issued_phase[8];
-        for (int s = 0; s < 8; ++s) issued_phase[s] = -1;
-        for (int kb = 0; kb < kblocks; ++kb) {
-            const int s = kb % a.stages;
-            const uint32_t round = kb / a.stages;
-            if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
-                dev_raise(a.st, DEV_ETIMEOUT, 1);
-                abort_flag = 1;
-                break;
-            }
-            if (abort_flag) break;
-            uint8_t *sa = tiles + (size_t)s * stage_bytes;
-            mbar_expect_tx(&full[s], stage_bytes);
-            tma_load_2d(sa, &mapQ, &full[s], kb * k_per_block, m0);
-            tma_load_2d(sa + a_bytes, &mapP, &full[s], kb * k_per_block, n0);
-            issued_phase[s] = round & 1;
-        }
-        // copies in flight must land before the block may exit
-        for (int s = 0; s < a.stages && s < 8; ++s)
-            if (issued_phase[s] >= 0 && !mbar_wait(&full[s], (uint32_t)issued_phase[s]))
-                dev_raise(a.st, DEV_ETIMEOUT, 2);
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        bool ok = true;
-        for (int kb = 0; kb < kblocks; ++kb) {
-            const int s = kb % a.stages;
-            const uint32_t round = kb / a.stages;
-            if (!mbar_wait(&full[s], round & 1) || abort_flag) {
-                dev_raise(a.st, DEV_ETIMEOUT, 3);
-                abort_flag = 1;
-                ok = false;
-                break;
-            }
-            fence_after();
-            const uint32_t sa = smem_u32(tiles + (size_t)s * stage_bytes);
-            const uint32_t sb = sa + a_bytes;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                // 32 bytes of K per instruction (16 BF16 or 8 TF32)
-                const uint64_t ad = desc_sw128(sa + 32 * k);
-                const uint64_t bd = desc_sw128(sb + 32 * k);
-                mma<TF32>(tmem, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-            }
-            mma_commit(&empty[s]);
-        }
-        if (ok) mma_commit(accum);
-    }
-    __syncwarp();
-    // epilogue: warp w owns TMEM lanes [32w, 32w + 32) = Q rows m0 + 32w + lane
-    bool have = mbar_wait(accum, 0);
-    if (!have) {
-        if (lane == 0) dev_raise(a.st, DEV_ETIMEOUT, 4);
-    }
-    __syncwarp();
-    fence_after();
-    const int row = m0 + warp * 32 + lane;
-    if (have) {
-        for (int c0 = 0; c0 < a.n_tile; c0 += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (row < a.rows && !(a.accumulate && a.conv && a.conv[row / 3])) {
-                float *zr = a.Z + (long long)row * a.nVp + n0 + c0;
-                const int lim = min(min(32, a.n_tile - c0), a.nV - (n0 + c0));
-                if (lim == 32) {
-                    float4 *z4 = reinterpret_cast<float4 *>(zr);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        float4 o = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                        if (a.accumulate) {
-                            float4 p = z4[i];
-                            o.x += p.x; o.y += p.y; o.z += p.z; o.w += p.w;
-                        }
-                        z4[i] = o;
-                    }
-                } else {
-                    for (int i = 0; i < lim; ++i) zr[i] = a.accumulate ? zr[i] + v[i] : v[i];
-                }
-            }
-        }
-    }
-    fence_before();
-    __syncthreads();
-    if (warp == 2) {
-        fence_after();
-        tmem_dealloc(tmem, tcols);
-    }
 }
 
 }  // namespace tc

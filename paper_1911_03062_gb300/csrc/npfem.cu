@@ -63,7 +63,6 @@ struct MeshTypeImpl {
     float *dhi = nullptr, *dlo = nullptr;
     int *op = nullptr;
     int2 *oe = nullptr;
-    int n_off = 0;
     // vertex numbering: vpub[i] = caller's index of internal vertex i, vint its inverse
     int *vpub = nullptr, *vint = nullptr;
     // edge neighbours of each (internal) vertex, CSR: the median filter's one-rings
@@ -438,7 +437,6 @@ void gemm_group(npfem_ctx *ctx, const std::vector<GemmItem> &items, int accumula
             P.m_tiles = (it.rows + tc::BM - 1) / tc::BM;
             P.kblocks = (it.t->nV * (bf16(ctx) ? 2 : 4) + tc::KB_BYTES - 1) / tc::KB_BYTES;
             P.unit_begin = units;
-            P.Z = nullptr;
             P.conv = it.conv;
             units += P.m_tiles * P.n_ntiles;
             maps.q[g.nprob] = *it.mapQ;
@@ -500,7 +498,6 @@ void residual(npfem_ctx *ctx, MeshTypeImpl *t, int rows_cells, const float *q, c
     a.any_active = active ? active : ctx->d_any + NPFEM_SWEEP_FLAGS - 1;
     a.prev_active = prev_active;
     a.st = ctx->d_st;
-    a.n_off = t->n_off;
     if (t->ell_W && !ctx->opt.residual_fp64) {
         ResidEllArgs e{};
         e.ncells = rows_cells;
@@ -1378,7 +1375,6 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         t->dlo = upload(ctx, dlo, t->owned);
         t->op = upload(ctx, op, t->owned);
         t->oe = upload(ctx, oe, t->owned);
-        t->n_off = (int)oe.size();
         if (mixed(ctx)) {
             int wmax = 0;
             for (int v = 0; v < nV; ++v) wmax = std::max(wmax, op[v + 1] - op[v]);

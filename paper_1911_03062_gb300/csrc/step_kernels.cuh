@@ -541,7 +541,7 @@ __global__ void k_fallback_apply(int nV, int nVp, const T *__restrict__ Pinv, co
 // their rows untouched).  final_pass: norms only, for the statistics of
 // cells that never converged.
 struct ResidArgs {
-    int ncells, nV, nVp, first, final_pass, n_off;
+    int ncells, nV, nVp, first, final_pass;
     double tol;
     const double *diag;      // [nV] diag(P)
     const float *dhi, *dlo;  // [nV] diag(P) = dhi + dlo (+ O(2^-48))
