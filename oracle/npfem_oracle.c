@@ -19,7 +19,10 @@
  *   bending : per interior edge, cotangent hinge vector b, p = b |b_rest|/|b|
  *   volume  : per cell, p = closest point with V(p) = V_rest (Gauss-Newton)
  *   step    : L-BFGS (history m, H_0 = P^{-1}) + Armijo backtracking, fixed K.
- * The global solve uses this file's own sparse (RCM + envelope) Cholesky.
+ *   damping : optional Rayleigh C = alpha M + beta L, L = sum_i w_i A_i^T A_i
+ *             (volume term included); Mt = M + h C replaces M in the inertia
+ *             term and y = x_n + h Mt^{-1}(M v_n + h F_ext).
+ * The global solves use this file's own sparse (RCM + envelope) Cholesky.
  *
  * Public layout: positions, velocities, forces are [nV][3] doubles per cell.
  */
@@ -53,6 +56,7 @@ typedef struct {
     double *hc;        /* nH*4 stencil coefficients */
     double *hrest;     /* nH rest |b| */
     double V0;
+    double ra, rb;     /* Rayleigh damping C = ra M + rb L (0, 0: none) */
     /* P in CSR (full symmetric pattern, sorted columns) */
     int *Pp, *Pj;
     double *Px;
@@ -61,6 +65,13 @@ typedef struct {
     int *first;        /* first column (new numbering) of row i */
     long *rowstart;    /* offset of row i in env */
     double *env;       /* row i holds L[i][first[i] .. i] */
+    /* damping only: L = sum_i w_i A_i^T A_i (with the volume term) in CSR, and the
+       envelope Cholesky of Mt = (1 + h ra) M + h rb L */
+    int *Lp, *Lj;
+    double *Lx;
+    int *mperm, *mfirst;
+    long *mrowstart;
+    double *menv;
 } orc_type;
 
 /* ---------------------------------------------------------------- helpers */
@@ -262,22 +273,35 @@ static int volume_project(const orc_type *T, const double *x, double *p, double 
 #define TERM_ALL 31
 
 /*
- * g(x) = 1/(2h^2) sum_v m_v |x_v - y_v|^2 + sum_i E_i(x)   (Eq. genericOptimizationNewton, C = 0)
- * and its gradient M/h^2 (x - y) + sum_i w_i A_i^T (A_i x - p_i).
- * terms[0..4] receive the inertia/strain/area/bending/volume parts.
+ * g(x) = 1/(2h^2) (x - y)^T Mt (x - y) + sum_i E_i(x)   (Eq. genericOptimizationNewton),
+ * Mt = M + h C, C = ra M + rb L (Rayleigh; none: Mt = M), and its gradient
+ * Mt/h^2 (x - y) + sum_i w_i A_i^T (A_i x - p_i).
+ * terms[0..4] receive the inertia(+damping)/strain/area/bending/volume parts.
  */
 double orc_energy(const orc_type *T, const double *x, const double *y, int mask,
                   double *grad, double *terms) {
     int nV = T->nV;
     double e[5] = {0, 0, 0, 0, 0};
     if (grad) memset(grad, 0, sizeof(double)*3*nV);
-    double ih2 = 1.0/(T->h*T->h);
+    double ih2 = (1.0 + T->h*T->ra)/(T->h*T->h);      /* (1 + h ra)/h^2: Mt's mass part */
     if (mask & TERM_INERTIA) {
         for (int v = 0; v < nV; ++v) {
             double dx[3];
             sub3(x + 3*v, y + 3*v, dx);
             e[0] += 0.5*ih2*T->mass[v]*dot3(dx, dx);
             if (grad) for (int r = 0; r < 3; ++r) grad[3*v+r] += ih2*T->mass[v]*dx[r];
+        }
+        if (T->rb != 0) {
+            /* Rayleigh stiffness part of 1/(2h^2) (x-y)^T Mt (x-y): rb/(2h) d^T L d, d = x - y */
+            double c = T->rb/T->h;
+            for (int v = 0; v < nV; ++v)
+                for (int r = 0; r < 3; ++r) {
+                    double Ld = 0;
+                    for (int p = T->Lp[v]; p < T->Lp[v+1]; ++p)
+                        Ld += T->Lx[p]*(x[3*T->Lj[p]+r] - y[3*T->Lj[p]+r]);
+                    e[0] += 0.5*c*(x[3*v+r] - y[3*v+r])*Ld;
+                    if (grad) grad[3*v+r] += c*Ld;
+                }
         }
     }
     if (mask & (TERM_STRAIN | TERM_AREA)) {
@@ -356,22 +380,22 @@ static int trip_cmp(const void *a, const void *b) {
 }
 
 /*
- * P = M/h^2 + sum_t (w_strain + w_area) A_t^T A_t + sum_e w_bend A_e^T A_e + w_vol I.
- * A_t maps the triangle's vertices to F (F[:,c] = sum_j G[j][c] x_j), A_e to
- * b = sum_j c_j x_j; the block for xyz is the same nV x nV matrix.
+ * wm M + wl (sum_t (w_strain + w_area) A_t^T A_t + sum_e w_bend A_e^T A_e + w_vol I).
+ * P: wm = 1/h^2, wl = 1 (undamped; with Rayleigh damping (1 + h ra)/h^2 and
+ * 1 + rb/h).  A_t maps the triangle's vertices to F (F[:,c] = sum_j G[j][c] x_j),
+ * A_e to b = sum_j c_j x_j; the block for xyz is the same nV x nV matrix.
  */
-static int assemble_P(orc_type *T) {
+static int assemble(const orc_type *T, double wm, double wl, int **Ap_, int **Aj_, double **Ax_) {
     int nV = T->nV;
     long cap = (long)nV + 9L*T->nT + 16L*T->nH;
     trip *tr = (trip *)malloc(sizeof(trip)*cap);
     if (!tr) return ORC_ENOMEM;
     long n = 0;
-    double ih2 = 1.0/(T->h*T->h);
-    for (int v = 0; v < nV; ++v) { tr[n].i = v; tr[n].j = v; tr[n].v = T->mass[v]*ih2 + T->kv; ++n; }
+    for (int v = 0; v < nV; ++v) { tr[n].i = v; tr[n].j = v; tr[n].v = T->mass[v]*wm + T->kv*wl; ++n; }
     for (int t = 0; t < T->nT; ++t) {
         double G[3][2];
         tri_G(T, t, G);
-        double w = (T->ks + T->ka)*T->area[t];
+        double w = wl*(T->ks + T->ka)*T->area[t];
         const int *v = T->tri + 3*t;
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) {
@@ -385,36 +409,41 @@ static int assemble_P(orc_type *T) {
         const double *c = T->hc + 4*hh;
         for (int a = 0; a < 4; ++a)
             for (int b = 0; b < 4; ++b) {
-                tr[n].i = hv[a]; tr[n].j = hv[b]; tr[n].v = T->kb*c[a]*c[b]; ++n;
+                tr[n].i = hv[a]; tr[n].j = hv[b]; tr[n].v = wl*T->kb*c[a]*c[b]; ++n;
             }
     }
     qsort(tr, n, sizeof(trip), trip_cmp);
-    T->Pp = (int *)calloc(nV + 1, sizeof(int));
-    T->Pj = (int *)malloc(sizeof(int)*n);
-    T->Px = (double *)malloc(sizeof(double)*n);
-    if (!T->Pp || !T->Pj || !T->Px) { free(tr); return ORC_ENOMEM; }
+    int *Ap = (int *)calloc(nV + 1, sizeof(int));
+    int *Aj = (int *)malloc(sizeof(int)*n);
+    double *Ax = (double *)malloc(sizeof(double)*n);
+    if (!Ap || !Aj || !Ax) { free(tr); free(Ap); free(Aj); free(Ax); return ORC_ENOMEM; }
     long m = 0;
     for (long k = 0; k < n; ++k) {
-        if (m > 0 && T->Pj[m-1] == tr[k].j && k > 0 && tr[k-1].i == tr[k].i) {
-            T->Px[m-1] += tr[k].v;
+        if (m > 0 && Aj[m-1] == tr[k].j && k > 0 && tr[k-1].i == tr[k].i) {
+            Ax[m-1] += tr[k].v;
         } else {
-            T->Pj[m] = tr[k].j; T->Px[m] = tr[k].v; T->Pp[tr[k].i + 1]++; ++m;
+            Aj[m] = tr[k].j; Ax[m] = tr[k].v; Ap[tr[k].i + 1]++; ++m;
         }
     }
-    for (int i = 0; i < nV; ++i) T->Pp[i+1] += T->Pp[i];
+    for (int i = 0; i < nV; ++i) Ap[i+1] += Ap[i];
     free(tr);
+    *Ap_ = Ap; *Aj_ = Aj; *Ax_ = Ax;
     return ORC_OK;
 }
 
-/* Reverse Cuthill-McKee ordering of P's graph (start: lowest-degree unvisited
- * vertex; neighbours queued by increasing degree, then index). */
-static void rcm(const orc_type *T, int *perm) {
-    int n = T->nV;
+static int assemble_P(orc_type *T) {
+    const double h = T->h;
+    return assemble(T, (1.0 + h*T->ra)/(h*h), 1.0 + T->rb/h, &T->Pp, &T->Pj, &T->Px);
+}
+
+/* Reverse Cuthill-McKee ordering of a symmetric CSR pattern (start: lowest-degree
+ * unvisited vertex; neighbours queued by increasing degree, then index). */
+static void rcm(int n, const int *Ap, const int *Aj, int *perm) {
     int *deg = (int *)malloc(sizeof(int)*n);
     char *seen = (char *)calloc(n, 1);
     int *order = (int *)malloc(sizeof(int)*n);
     int *nb = (int *)malloc(sizeof(int)*n);
-    for (int i = 0; i < n; ++i) deg[i] = T->Pp[i+1] - T->Pp[i] - 1;
+    for (int i = 0; i < n; ++i) deg[i] = Ap[i+1] - Ap[i] - 1;
     int head = 0, tail = 0;
     while (tail < n) {
         int s = -1;
@@ -423,8 +452,8 @@ static void rcm(const orc_type *T, int *perm) {
         seen[s] = 1; order[tail++] = s;
         while (head < tail) {
             int u = order[head++], k = 0;
-            for (int p = T->Pp[u]; p < T->Pp[u+1]; ++p) {
-                int w = T->Pj[p];
+            for (int p = Ap[u]; p < Ap[u+1]; ++p) {
+                int w = Aj[p];
                 if (!seen[w]) { seen[w] = 1; nb[k++] = w; }
             }
             for (int a = 1; a < k; ++a) {          /* insertion sort by (deg, idx) */
@@ -441,40 +470,44 @@ static void rcm(const orc_type *T, int *perm) {
     free(deg); free(seen); free(order); free(nb);
 }
 
-/* Envelope (profile) Cholesky of the RCM-permuted P, row by row. */
-static int factor_P(orc_type *T) {
-    int n = T->nV;
-    T->perm = (int *)malloc(sizeof(int)*n);
+/* Envelope (profile) Cholesky of an RCM-permuted SPD CSR matrix, row by row.
+ * Outputs (allocated here): perm[new] = old, first column of each row, row
+ * offsets into env, env. */
+static int factor_env(int n, const int *Ap, const int *Aj, const double *Ax, int **perm_, int **first_,
+                      long **rowstart_, double **env_) {
+    int *perm = (int *)malloc(sizeof(int)*n);
     int *iperm = (int *)malloc(sizeof(int)*n);
-    T->first = (int *)malloc(sizeof(int)*n);
-    T->rowstart = (long *)malloc(sizeof(long)*(n + 1));
-    rcm(T, T->perm);
-    for (int i = 0; i < n; ++i) iperm[T->perm[i]] = i;
+    int *first = (int *)malloc(sizeof(int)*n);
+    long *rowstart = (long *)malloc(sizeof(long)*(n + 1));
+    *perm_ = perm; *first_ = first; *rowstart_ = rowstart; *env_ = NULL;
+    rcm(n, Ap, Aj, perm);
+    for (int i = 0; i < n; ++i) iperm[perm[i]] = i;
     for (int i = 0; i < n; ++i) {
-        int old = T->perm[i], f = i;
-        for (int p = T->Pp[old]; p < T->Pp[old+1]; ++p) {
-            int j = iperm[T->Pj[p]];
+        int old = perm[i], f = i;
+        for (int p = Ap[old]; p < Ap[old+1]; ++p) {
+            int j = iperm[Aj[p]];
             if (j < f) f = j;
         }
-        T->first[i] = f;
+        first[i] = f;
     }
-    T->rowstart[0] = 0;
-    for (int i = 0; i < n; ++i) T->rowstart[i+1] = T->rowstart[i] + (i - T->first[i] + 1);
-    T->env = (double *)calloc(T->rowstart[n], sizeof(double));
-    if (!T->env) { free(iperm); return ORC_ENOMEM; }
-#define L(i, j) T->env[T->rowstart[i] + ((j) - T->first[i])]
+    rowstart[0] = 0;
+    for (int i = 0; i < n; ++i) rowstart[i+1] = rowstart[i] + (i - first[i] + 1);
+    double *env = (double *)calloc(rowstart[n], sizeof(double));
+    *env_ = env;
+    if (!env) { free(iperm); return ORC_ENOMEM; }
+#define L(i, j) env[rowstart[i] + ((j) - first[i])]
     for (int i = 0; i < n; ++i) {
-        int old = T->perm[i];
-        for (int p = T->Pp[old]; p < T->Pp[old+1]; ++p) {
-            int j = iperm[T->Pj[p]];
-            if (j <= i) L(i, j) = T->Px[p];
+        int old = perm[i];
+        for (int p = Ap[old]; p < Ap[old+1]; ++p) {
+            int j = iperm[Aj[p]];
+            if (j <= i) L(i, j) = Ax[p];
         }
     }
     for (int i = 0; i < n; ++i) {
-        int fi = T->first[i];
+        int fi = first[i];
         for (int j = fi; j < i; ++j) {
             double s = L(i, j);
-            int k0 = fi > T->first[j] ? fi : T->first[j];
+            int k0 = fi > first[j] ? fi : first[j];
             for (int k = k0; k < j; ++k) s -= L(i, k)*L(j, k);
             L(i, j) = s / L(j, j);
         }
@@ -487,26 +520,35 @@ static int factor_P(orc_type *T) {
     return ORC_OK;
 }
 
-/* x = P^{-1} b for each of the 3 components (b, x: [nV][3]). */
-void orc_solve(const orc_type *T, const double *b, double *x) {
-    int n = T->nV;
+static int factor_P(orc_type *T) {
+    return factor_env(T->nV, T->Pp, T->Pj, T->Px, &T->perm, &T->first, &T->rowstart, &T->env);
+}
+
+/* x = A^{-1} b for each of the 3 components (b, x: [nV][3]) with an envelope factor. */
+static void solve_env(int n, const int *perm, const int *first, const long *rowstart, const double *env,
+                      const double *b, double *x) {
     double *z = (double *)malloc(sizeof(double)*n);
     for (int c = 0; c < 3; ++c) {
-        for (int i = 0; i < n; ++i) z[i] = b[3*T->perm[i] + c];
+        for (int i = 0; i < n; ++i) z[i] = b[3*perm[i] + c];
         for (int i = 0; i < n; ++i) {                 /* L z = b */
             double s = z[i];
-            for (int k = T->first[i]; k < i; ++k) s -= L(i, k)*z[k];
+            for (int k = first[i]; k < i; ++k) s -= L(i, k)*z[k];
             z[i] = s / L(i, i);
         }
         for (int i = n - 1; i >= 0; --i) {            /* L^T w = z */
             z[i] /= L(i, i);
-            for (int k = T->first[i]; k < i; ++k) z[k] -= L(i, k)*z[i];
+            for (int k = first[i]; k < i; ++k) z[k] -= L(i, k)*z[i];
         }
-        for (int i = 0; i < n; ++i) x[3*T->perm[i] + c] = z[i];
+        for (int i = 0; i < n; ++i) x[3*perm[i] + c] = z[i];
     }
     free(z);
 }
 #undef L
+
+/* x = P^{-1} b for each of the 3 components (b, x: [nV][3]). */
+void orc_solve(const orc_type *T, const double *b, double *x) {
+    solve_env(T->nV, T->perm, T->first, T->rowstart, T->env, b, x);
+}
 
 /* ------------------------------------------------------------ type set-up */
 void orc_type_destroy(orc_type *T) {
@@ -514,6 +556,7 @@ void orc_type_destroy(orc_type *T) {
     free(T->tri); free(T->rest); free(T->mass); free(T->Dinv); free(T->area);
     free(T->hv); free(T->hc); free(T->hrest); free(T->Pp); free(T->Pj); free(T->Px);
     free(T->perm); free(T->first); free(T->rowstart); free(T->env);
+    free(T->Lp); free(T->Lj); free(T->Lx); free(T->mperm); free(T->mfirst); free(T->mrowstart); free(T->menv);
     free(T);
 }
 
@@ -639,6 +682,32 @@ int orc_type_create(int nV, const double *rest, int nT, const int *tris, const d
     return ORC_OK;
 }
 
+/* Rayleigh damping C = ra M + rb L (paper Sec. 2.1, Eq. Newton2nd; Table Params
+ * gives alpha_D = 0, beta_D = 0.01).  Reading: L = sum_i w_i A_i^T A_i (with the
+ * volume term), the constant stiffness of the quadratic energies.  Rebuilds P =
+ * Mt/h^2 + L = (1 + h ra) M/h^2 + (1 + rb/h) L and factors Mt = (1 + h ra) M + h rb L
+ * for the predictor.  ra = rb = 0 restores the undamped type. */
+int orc_type_set_damping(orc_type *T, double ra, double rb) {
+    if (!(ra >= 0) || !(rb >= 0)) return ORC_EINVAL;
+    free(T->Pp); free(T->Pj); free(T->Px); free(T->perm); free(T->first); free(T->rowstart); free(T->env);
+    free(T->Lp); free(T->Lj); free(T->Lx); free(T->mperm); free(T->mfirst); free(T->mrowstart); free(T->menv);
+    T->Pp = T->Pj = T->perm = T->first = T->Lp = T->Lj = T->mperm = T->mfirst = NULL;
+    T->Px = T->env = T->Lx = T->menv = NULL;
+    T->rowstart = T->mrowstart = NULL;
+    T->ra = ra; T->rb = rb;
+    int rc = assemble_P(T);
+    if (!rc) rc = factor_P(T);
+    if (!rc && (ra != 0 || rb != 0)) {
+        rc = assemble(T, 0.0, 1.0, &T->Lp, &T->Lj, &T->Lx);
+        int *Mp = NULL, *Mj = NULL;
+        double *Mx = NULL;
+        if (!rc) rc = assemble(T, 1.0 + T->h*ra, T->h*rb, &Mp, &Mj, &Mx);
+        if (!rc) rc = factor_env(T->nV, Mp, Mj, Mx, &T->mperm, &T->mfirst, &T->mrowstart, &T->menv);
+        free(Mp); free(Mj); free(Mx);
+    }
+    return rc;
+}
+
 void orc_type_info(const orc_type *T, int *nH, double *V0, int *nnzP, long *nnzL) {
     if (nH) *nH = T->nH;
     if (V0) *V0 = T->V0;
@@ -719,9 +788,17 @@ int orc_step(const orc_type *T, const double *xn, const double *vn, const double
     double *q = gt + n3, *r = q + n3;
     double *S = r + n3, *Y = S + n3*mm;
     double *rho = (double *)malloc(sizeof(double)*mm), *al = (double *)malloc(sizeof(double)*mm);
-    for (int v = 0; v < nV; ++v)
-        for (int c = 0; c < 3; ++c)
-            y[3*v+c] = xn[3*v+c] + h*vn[3*v+c] + h*h/T->mass[v]*f[3*v+c];
+    if (T->ra == 0 && T->rb == 0) {
+        for (int v = 0; v < nV; ++v)
+            for (int c = 0; c < 3; ++c)
+                y[3*v+c] = xn[3*v+c] + h*vn[3*v+c] + h*h/T->mass[v]*f[3*v+c];
+    } else {
+        /* y = x_n + h Mt^{-1} (M v_n + h F_ext)  (x buffer as scratch) */
+        for (int v = 0; v < nV; ++v)
+            for (int c = 0; c < 3; ++c) x[3*v+c] = T->mass[v]*vn[3*v+c] + h*f[3*v+c];
+        solve_env(nV, T->mperm, T->mfirst, T->mrowstart, T->menv, x, y);
+        for (int i = 0; i < n3; ++i) y[i] = xn[i] + h*y[i];
+    }
     memcpy(x, y, sizeof(double)*n3);
     double g = orc_energy(T, x, y, TERM_ALL, gr, NULL);
     if (g_tr) g_tr[0] = g;

@@ -74,6 +74,8 @@ def lib():
             L.orc_velocity_cap.argtypes = [C.c_int, dp, C.c_double]
             L.orc_pbd_damping.argtypes = [vp, dp, dp, C.c_double]
             L.orc_pbd_damping.restype = C.c_int
+            L.orc_type_set_damping.argtypes = [vp, C.c_double, C.c_double]
+            L.orc_type_set_damping.restype = C.c_int
             _lib = L
     return _lib
 
@@ -117,6 +119,15 @@ class OracleType:
                 lib().orc_type_destroy(self._h)
         except Exception:
             pass
+
+    def set_damping(self, alpha, beta):
+        """Rayleigh damping C = alpha M + beta L (Sec. 2.1): rebuilds P and factors
+        Mt = M + h C for the predictor; (0, 0) is the undamped type."""
+        rc = lib().orc_type_set_damping(self._h, float(alpha), float(beta))
+        if rc != 0:
+            raise ValueError(f"oracle damping set-up failed ({rc})")
+        self.alpha, self.beta = float(alpha), float(beta)
+        return self
 
     # -- pieces -------------------------------------------------------------
     def P_dense(self):

@@ -496,3 +496,85 @@ def test_pbd_damping_keeps_rigid_motion_and_scales_the_rest(O, rbc):
     d = O.pbd_damping(T, x, v0, 0.9)
     assert np.allclose(d.sum(axis=0), v0.sum(axis=0), rtol=1e-12, atol=1e-12)
     assert np.allclose(np.cross(r, d).sum(axis=0), np.cross(r, v0).sum(axis=0), rtol=1e-12, atol=1e-10)
+
+
+# ------------------------------------------------------------------ Rayleigh damping
+ALPHA, BETA = 2.0, 0.01          # beta_D = 0.01 as in the paper's parameter table; alpha > 0 to pin both
+
+
+def damped(mt, O, alpha=ALPHA, beta=BETA):
+    return O.OracleType.from_mesh_type(mt).set_damping(alpha, beta)
+
+
+def test_damping_zero_is_the_undamped_type(O, rbc):
+    mt, T = rbc
+    xn, vn, f = seeded_cell(mt, 40, amp=5.0)
+    x1, v1 = T.step(xn, vn, f)
+    x2, v2 = damped(mt, O, 0.0, 0.0).step(xn, vn, f)
+    assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
+    with pytest.raises(ValueError):
+        damped(mt, O, -1.0, 0.0)
+
+
+def test_damped_P_is_Mt_over_h2_plus_L(O, rbc):
+    # P = Mt/h^2 + L with Mt = M + h (alpha M + beta L), L = P_undamped - M/h^2
+    mt, T = rbc
+    h, m = mt.material.dt, 1.0 / mt.nV
+    P0 = T.P_dense()
+    L = P0 - np.eye(mt.nV) * m / h ** 2
+    expect = P0 + (ALPHA * m * np.eye(mt.nV) + BETA * L) / h
+    assert np.allclose(damped(mt, O).P_dense(), expect, rtol=1e-13, atol=1e-13 * np.abs(expect).max())
+
+
+def test_damped_inertia_gradient_central_differences(O):
+    rest, tris, T = small_rbc(O, 1)
+    T.set_damping(ALPHA, 0.5)                        # large beta so the L term is not swamped
+    rng = np.random.default_rng(41)
+    x = rest * 1.08 + 0.08 * rng.standard_normal(rest.shape)
+    y = rest + 0.05 * rng.standard_normal(rest.shape)
+    e, g, _ = T.energy(x, y, mask=1)
+    hh = 1e-6
+    fd = np.zeros_like(x)
+    for i in range(x.shape[0]):
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, c] += hh
+            xm[i, c] -= hh
+            fd[i, c] = (T.energy(xp, y, 1, grad=False)[0] - T.energy(xm, y, 1, grad=False)[0]) / (2 * hh)
+    assert np.linalg.norm(g - fd) <= 1e-7 * np.linalg.norm(g)
+    # and the quadratic form itself: e = 1/(2h^2) d^T Mt d, Mt from the undamped P
+    _, _, T0 = small_rbc(O, 1)
+    h, m = T.dt, 1.0 / rest.shape[0]
+    L = T0.P_dense() - np.eye(rest.shape[0]) * m / h ** 2
+    Mt = (1 + h * ALPHA) * m * np.eye(rest.shape[0]) + h * 0.5 * L
+    d = x - y
+    assert e == pytest.approx(np.einsum("vc,vw,wc->", d, Mt, d) / (2 * h ** 2), rel=1e-12)
+
+
+def test_damped_step_converges_to_newtons_law(O, rbc):
+    # Eq. (Newton2nd) with C = alpha M + beta L:  M (v1 - v0)/h + C v1 = F_int(x1) + F_ext
+    mt, T = rbc
+    xn, vn, f = seeded_cell(mt, 42, amp=20.0)
+    vn = vn + 2.0 * np.random.default_rng(43).standard_normal(vn.shape)
+    x1, v1 = damped(mt, O).step(xn, vn, f, K=40)
+    h, m = mt.material.dt, 1.0 / mt.nV
+    L = T.P_dense() - np.eye(mt.nV) * m / h ** 2
+    _, gint, _ = T.energy(x1, x1, mask=30)
+    lhs = m * (v1 - vn) / h + ALPHA * m * v1 + BETA * (L @ v1)
+    assert np.abs(lhs - (-gint + f)).max() < 1e-7 * np.abs(m * (v1 - vn) / h).max()
+    # the damping force is not negligible at this state
+    assert np.abs(ALPHA * m * v1 + BETA * (L @ v1)).max() > 1e-3 * np.abs(m * (v1 - vn) / h).max()
+
+
+def test_damped_step_mean_velocity_closed_form(O, rbc):
+    # F_ext summing to zero: 1^T L = k_vol 1^T (elastic parts annihilate constants),
+    # so at every iterate mean(v1) = mean(v0) / (1 + h alpha + h beta k_vol / m)
+    mt, T = rbc
+    xn, vn, _ = seeded_cell(mt, 44, amp=5.0)
+    vn = vn + np.random.default_rng(45).standard_normal(vn.shape)
+    f = np.random.default_rng(46).standard_normal(vn.shape)
+    f -= f.mean(axis=0)
+    x1, v1 = damped(mt, O).step(xn, vn, f)
+    h, m, kv = mt.material.dt, 1.0 / mt.nV, mt.material.k_vol
+    expect = vn.mean(axis=0) / (1 + h * ALPHA + h * BETA * kv / m)
+    assert np.allclose(v1.mean(axis=0), expect, rtol=1e-9, atol=1e-12)
