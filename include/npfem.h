@@ -6,14 +6,16 @@
  * FEM solver of arXiv 1911.03062 (Supplementary Sec. 2.1):
  *
  *   v_{n+1} = (x_{n+1} - x_n) / h                                   Eq. (vel)
- *   x_{n+1} = argmin g(x),  g(x) = 1/(2h^2) |M^{1/2}(x - y_n)|_F^2 + sum_i E_i(x)
- *   y_n     = x_n + h v_n + h^2 M^{-1} F_ext                       Eq. (genericOptimizationNewton), C = 0
+ *   x_{n+1} = argmin g(x),  g(x) = 1/(2h^2) (x - y_n)^T Mt (x - y_n) + sum_i E_i(x)
+ *   y_n     = x_n + h Mt^{-1} (M v_n + h F_ext),  Mt = M + h C       Eq. (genericOptimizationNewton)
  *
  * minimised by a fixed number of quasi-Newton iterations
  * x^{k+1} = x^k - H grad g(x^k) (the unnumbered update after that equation),
  * with H an L-BFGS operator whose initial matrix is the inverse of the
- * constant SPD matrix P = M/h^2 + sum_i w_i A_i^T A_i of the quadratic
- * (projective) energies, and an Armijo line search.
+ * constant SPD matrix P = Mt/h^2 + sum_i w_i A_i^T A_i of the quadratic
+ * (projective) energies, and an Armijo line search.  C is the Rayleigh
+ * damping of Eq. (Newton2nd), zero unless the material sets it (then y_n =
+ * x_n + h v_n + h^2 M^{-1} F_ext).
  *
  * Conventions for every call below
  *  - Return value: NPFEM_OK (0) or a negative NPFEM_E* code; the message of
@@ -95,10 +97,18 @@ typedef struct {
 /* Material and time step of one mesh type.  Element weights follow the
  * projective-dynamics reading of the paper's energies: w_strain = k_strain *
  * rest area, w_area = k_area * rest area (per triangle), w_bend = k_bend (per
- * interior edge), w_vol = k_vol (per cell). */
+ * interior edge), w_vol = k_vol (per cell).
+ * Rayleigh damping (Supp. Sec. 2.1, Eq. (Newton2nd); the paper's parameter
+ * table uses alpha = 0, beta = 0.01): C = rayleigh_alpha M + rayleigh_beta L
+ * with L = sum_i w_i A_i^T A_i (volume term included), the constant stiffness
+ * of the quadratic energies.  Both >= 0; zero (the default of a zeroed
+ * struct) is the undamped step.  A damped type keeps Mt^{-1} beside P^{-1}
+ * and applies it once per step for the predictor, in FP64 (FP64 form), TF32,
+ * or BF16 split into high and low parts (BF16 form, whatever refine_split). */
 typedef struct {
     double k_strain, k_area, k_bend, k_vol;
     double dt;              /* h */
+    double rayleigh_alpha, rayleigh_beta;
 } npfem_material;
 
 /* Per-step counters of the last completed npfem_step (summed over cells). */
@@ -150,7 +160,7 @@ void npfem_destroy(npfem_ctx *ctx);
  * keeps P^{-1} (and its TF32/BF16 copy in the mixed forms).
  * Errors: EINVAL (nV < 4, index out of range, open or non-manifold mesh,
  * inconsistent orientation, degenerate triangle, inward orientation,
- * non-positive mass or dt), ENOTSPD, ENOMEM, ECUDA, ESTATE (after cells were
+ * non-positive mass or dt, negative or non-finite damping), ENOTSPD, ENOMEM, ECUDA, ESTATE (after cells were
  * added to a graph-captured context the call is still allowed; the graph is
  * rebuilt on the next step). */
 int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz,

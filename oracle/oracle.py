@@ -111,7 +111,9 @@ class OracleType:
     @classmethod
     def from_mesh_type(cls, mt):
         m = mt.material
-        return cls(mt.rest, mt.tris, m.k_strain, m.k_area, m.k_bend, m.k_vol, m.dt, mt.mass)
+        T = cls(mt.rest, mt.tris, m.k_strain, m.k_area, m.k_bend, m.k_vol, m.dt, mt.mass)
+        a, b = getattr(m, "rayleigh_alpha", 0.0), getattr(m, "rayleigh_beta", 0.0)
+        return T.set_damping(a, b) if (a or b) else T
 
     def __del__(self):
         try:

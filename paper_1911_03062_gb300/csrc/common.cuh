@@ -184,4 +184,10 @@ template <> struct Prec<float> {
     static constexpr double round_unit = 5.9604644775390625e-08;
 };
 
+// x rounded to the nearest value with a TF32 (10-bit) significand, ties away from
+// zero: the high part of a TF32 split (exactly what the tensor core reads of it).
+__device__ __forceinline__ float tf32_hi(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+}
+
 }  // namespace npfem

@@ -5,7 +5,8 @@
 //   * k_gj_*      : in-place Gauss-Jordan inversion of the SPD matrix P in FP64,
 //                   one pivot per launch pair (no pivoting: P is SPD and strongly
 //                   diagonally dominant through M/h^2);
-//   * k_convert_pinv : FP64 inverse -> FP32 / BF16 (high and low part) operand copies.
+//   * k_convert_pinv : FP64 inverse -> FP32 (or TF32 high and low part) / BF16 (high and
+//                      low part) operand copies.
 #pragma once
 
 #include "common.cuh"
@@ -90,14 +91,15 @@ __global__ void k_gj_update(int n, int k, double *A, const double *rowk, const d
 
 // dense n x n FP64 -> padded [n][nVp] copies (FP64, FP32, BF16; null = skip)
 __global__ void k_convert_pinv(int n, int nVp, const double *A, double *P64, float *P32, __nv_bfloat16 *P16,
-                               __nv_bfloat16 *P16lo) {
+                               __nv_bfloat16 *P16lo, float *P32lo) {
     long long total = (long long)n * nVp;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         int i = (int)(idx / nVp), j = (int)(idx - (long long)i * nVp);
         double v = j < n ? 0.5 * (A[(long long)i * n + j] + A[(long long)j * n + i]) : 0.0;
         if (P64) P64[idx] = v;
-        if (P32) P32[idx] = (float)v;
+        if (P32) P32[idx] = P32lo ? tf32_hi((float)v) : (float)v;
+        if (P32lo) P32lo[idx] = (float)(v - (double)P32[idx]);   // TF32 split: low part
         if (P16) P16[idx] = __float2bfloat16_rn((float)v);
         if (P16lo) {   // low part: v - hi, rounded to BF16 (hi + lo carries ~16 bits)
             const double hi = (double)__bfloat162float(__float2bfloat16_rn((float)v));

@@ -2,8 +2,13 @@
 // energy g(x) and gradient grad g(x) of the implicit-Euler objective
 // (arXiv 1911.03062, Supplementary Sec. 2.1, Eq. (genericOptimizationNewton)),
 //
-//   g(x) = 1/(2h^2) sum_v m_v |x_v - y_v|^2 + sum_i w_i/2 |A_i x - p_i(x)|^2,
-//   grad = M/h^2 (x - y) + sum_i w_i A_i^T (A_i x - p_i(x)),
+//   g(x) = 1/(2h^2) (x - y)^T Mt (x - y) + sum_i w_i/2 |A_i x - p_i(x)|^2,
+//   grad = Mt/h^2 (x - y) + sum_i w_i A_i^T (A_i x - p_i(x)),
+//
+// Mt = M undamped; with Rayleigh damping C = alpha M + beta L (Eq. (Newton2nd),
+// L = sum_i w_i A_i^T A_i), Mt = M + h C: its diagonal part ((1 + h alpha) M +
+// h beta k_vol I) is the per-vertex inertia coefficient, its element parts are
+// evaluated with the elements on x - y.
 //
 // with the projective element energies (strain and area per triangle,
 // bending per interior edge, volume per cell) and their closest-point
@@ -39,10 +44,11 @@ struct TypeConst {
     const TriInc<T> *vt;
     const int *vh_ptr;      // nV + 1: vertex -> hinge incidences (sorted by hinge)
     const HingeInc<T> *vh;
-    const T *mh2;           // nV: m_v / h^2
+    const T *mh2;           // nV: m_v / h^2 (damped: (1 + h alpha) m_v / h^2 + (beta / h) k_vol)
     double V0;              // rest volume
     double V0x6, vtol6;     // 6 V0 and 6 tol |V0| (the volume sums give 6 V)
     T kb, kv;               // bending and volume weights
+    T cd;                   // Rayleigh beta / h (0: undamped)
     // slot-major padded copies of the incidence lists (slot q of vertex v at
     // [q * nV + v]; unused slots carry zero weights), for one-round gathers:
     int pad_t, pad_h;       // slots per vertex (0 = not available)
@@ -223,13 +229,45 @@ __device__ __forceinline__ void area_target(T s1, T s2, T d[2]) {
     d[1] = (s2 + lam * s1) * iq;
 }
 
+// Rayleigh damping part of one element, returned by value: r = wd A(x - y),
+// e = wd/2 |A(x - y)|^2, a = wd |A(x - y)| |A x| (rounding allowance).  Out of
+// line, with scalar arguments, so the undamped path keeps its registers.
+template <typename T>
+struct Damp {
+    T r[6];
+    T e, a;
+};
+
+template <typename T>
+__device__ __noinline__ Damp<T> tri_damp(const T *pos, const T *__restrict__ yr, int nVp, int4 tv, T D0, T D1, T D2,
+                                         T D3, T wd, T nfx) {
+    Damp<T> o;
+    T nd = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T *pc = pos + c * nVp, *yc = yr + c * nVp;
+        const T d0 = pc[tv.x] - yc[tv.x];
+        const T e1 = (pc[tv.y] - yc[tv.y]) - d0, e2 = (pc[tv.z] - yc[tv.z]) - d0;
+        const T f0 = e1 * D0 + e2 * D2, f1 = e1 * D1 + e2 * D3;
+        o.r[2 * c] = wd * f0;
+        o.r[2 * c + 1] = wd * f1;
+        nd += f0 * f0 + f1 * f1;
+    }
+    o.e = T(0.5) * wd * nd;
+    o.a = wd * sqrt(nd) * nfx;
+    return o;
+}
+
 // Strain + area projection of one triangle.  Returns R = w_s (F - T_s) +
 // w_a (F - T_a) (the vertex gradient is sum_c R[:, c] G[corner][c]), N =
 // (e1 x e2) / 6 (each corner's share of the volume gradient) and the
 // signed-volume term (x0 - o).(e1 x e2) of the triangle.
+// Rayleigh damping (cd = beta/h != 0): the triangle's part of
+// beta/(2h) (x - y)^T L (x - y), i.e. cd (w_s + w_a)/2 |F(x - y)|^2, adds
+// cd (w_s + w_a) F(x - y) to R; yr holds y (same frame as pos).
 template <typename T>
-__device__ __forceinline__ T tri_local(const T *pos, int nVp, int4 tv, const T (&Di)[4], T ws, T wa, const T o[3],
-                                       T R[6], T N[3], T &en, T &al) {
+__device__ __forceinline__ T tri_local(const T *pos, const T *__restrict__ yr, int nVp, int4 tv, const T (&Di)[4], T ws,
+                                       T wa, T cd, const T o[3], T R[6], T N[3], T &en, T &al) {
     T F[6], E1[3], E2[3], A0[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -285,6 +323,13 @@ __device__ __forceinline__ T tri_local(const T *pos, int nVp, int4 tv, const T (
     }
     en += T(0.5) * ws * ns + T(0.5) * wa * na;
     al += (ws * sqrt(ns) + wa * sqrt(na)) * sqrt(nf);
+    if (cd != T(0)) {
+        const Damp<T> dm = tri_damp(pos, yr, nVp, tv, Di[0], Di[1], Di[2], Di[3], cd * (ws + wa), sqrt(nf));
+#pragma unroll
+        for (int i = 0; i < 6; ++i) R[i] += dm.r[i];
+        en += dm.e;
+        al += dm.a;
+    }
     T C0 = E1[1] * E2[2] - E1[2] * E2[1], C1 = E1[2] * E2[0] - E1[0] * E2[2], C2 = E1[0] * E2[1] - E1[1] * E2[0];
     N[0] = C0 / T(6);
     N[1] = C1 / T(6);
@@ -292,10 +337,31 @@ __device__ __forceinline__ T tri_local(const T *pos, int nVp, int4 tv, const T (
     return A0[0] * C0 + A0[1] * C1 + A0[2] * C2;
 }
 
-// Bending of one hinge: b = sum_j c_j x_j, p = b |b_rest| / |b|; stash kb (b - p).
+// Rayleigh damping part of one hinge (out of line, as tri_damp; r[0..2] used).
 template <typename T>
-__device__ __forceinline__ void hinge_local(const T *pos, int nVp, int4 hv, const T (&hc)[4], T rest, T kb,
-                                            T R[3], T &en, T &al) {
+__device__ __noinline__ Damp<T> hinge_damp(const T *pos, const T *__restrict__ yr, int nVp, int4 hv, T c0, T c1, T c2,
+                                           T c3, T wd, T nb) {
+    Damp<T> o;
+    T nd = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T *pc = pos + c * nVp, *yc = yr + c * nVp;
+        const T bd = c0 * (pc[hv.x] - yc[hv.x]) + c1 * (pc[hv.y] - yc[hv.y]) + c2 * (pc[hv.z] - yc[hv.z]) +
+                     c3 * (pc[hv.w] - yc[hv.w]);
+        o.r[c] = wd * bd;
+        nd += bd * bd;
+    }
+    o.r[3] = o.r[4] = o.r[5] = T(0);
+    o.e = T(0.5) * wd * nd;
+    o.a = wd * sqrt(nd) * nb;
+    return o;
+}
+
+// Bending of one hinge: b = sum_j c_j x_j, p = b |b_rest| / |b|; stash kb (b - p)
+// (+ cd kb b(x - y) with Rayleigh damping, energy cd kb/2 |b(x - y)|^2).
+template <typename T>
+__device__ __forceinline__ void hinge_local(const T *pos, const T *__restrict__ yr, int nVp, int4 hv, const T (&hc)[4],
+                                            T rest, T kb, T cd, T R[3], T &en, T &al) {
     T b[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -313,6 +379,14 @@ __device__ __forceinline__ void hinge_local(const T *pos, int nVp, int4 hv, cons
     }
     en += T(0.5) * kb * n2;
     al += kb * sqrt(n2) * nb;
+    if (cd != T(0)) {
+        const Damp<T> dm = hinge_damp(pos, yr, nVp, hv, hc[0], hc[1], hc[2], hc[3], cd * kb, nb);
+        R[0] += dm.r[0];
+        R[1] += dm.r[1];
+        R[2] += dm.r[2];
+        en += dm.e;
+        al += dm.a;
+    }
 }
 
 // Signed volume of the current positions in pos (relative to vertex 0), partial per thread.
@@ -391,7 +465,7 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                 ld4(tc.dinv + 4 * t, Di);
                 ld2(tc.wtri + 2 * t, w);
                 T R[6], N[3];
-                aV.add(tri_local(pos, nVp, tv, Di, w[0], w[1], o, R, N, en, al));
+                aV.add(tri_local(pos, yrel, nVp, tv, Di, w[0], w[1], tc.cd, o, R, N, en, al));
                 T *st = stash + 9 * (t - t0);
 #pragma unroll
                 for (int i = 0; i < 6; ++i) st[i] = R[i];
@@ -496,7 +570,7 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                     rest_n = tc.hrest[h + B];
                 }
                 T R[3];
-                hinge_local(pos, nVp, hv, hc, rest, tc.kb, R, en, al);
+                hinge_local(pos, yrel, nVp, hv, hc, rest, tc.kb, tc.cd, R, en, al);
                 T *st = stash + 3 * (h - h0);
                 st[0] = R[0]; st[1] = R[1]; st[2] = R[2];
             }

@@ -58,6 +58,12 @@ struct MeshTypeImpl {
     float *Pinv32 = nullptr;
     __nv_bfloat16 *Pinv16 = nullptr;
     __nv_bfloat16 *Pinv16lo = nullptr;          // split corrections: BF16 low part of P^{-1}
+    // Rayleigh damping: Mt^{-1} (Mt = M + h C) for the predictor, in the form's operand type
+    double ra = 0, rb = 0;
+    bool damped = false;
+    double *Minv64 = nullptr;
+    float *Minv32 = nullptr, *Minv32lo = nullptr;   // TF32 form: TF32 high part and FP32 rest
+    __nv_bfloat16 *Minv16 = nullptr, *Minv16lo = nullptr;
     double *diag = nullptr, *minv = nullptr, *mass = nullptr;
     double mtot = 0;                             // total mass of a cell
     float *dhi = nullptr, *dlo = nullptr;
@@ -74,7 +80,7 @@ struct MeshTypeImpl {
     int ell_W = 0, ell_KR = 0, ell_nt = 0, ell_grid = 0;
     // tensor-core GEMM configuration
     int n_tile = 0, stages = 0;
-    CUtensorMap mapP{}, mapPlo{};
+    CUtensorMap mapP{}, mapPlo{}, mapM{}, mapMlo{};
     // cells
     int ncells = 0, cap = 0;
     std::vector<long long> pub_off_h;
@@ -82,11 +88,12 @@ struct MeshTypeImpl {
     double *xn = nullptr, *vn = nullptr;        // state SoA FP64
     void *yrel = nullptr, *delta = nullptr, *grad = nullptr, *q = nullptr, *z = nullptr;
     void *S = nullptr, *Y = nullptr, *rlo = nullptr;
+    void *zp = nullptr;                          // Rayleigh-damped type: Mt^{-1}(M v_n + h F_ext), kept for the step
     __nv_bfloat16 *rlo_lo = nullptr;             // split corrections: BF16 low part of r
     __nv_bfloat16 *q16 = nullptr;
     double *origin = nullptr, *rho = nullptr, *alpha = nullptr, *M = nullptr, *g = nullptr, *allow = nullptr;
     int *hcount = nullptr, *hhead = nullptr, *conv = nullptr, *fb_list = nullptr, *fb_count = nullptr;
-    CUtensorMap mapQ{}, mapR{}, mapRlo{}, mapZ{};
+    CUtensorMap mapQ{}, mapR{}, mapRlo{}, mapZ{}, mapZp{};
     int ept = 8, block = 256, stash_T = 0;
     size_t smem_step = 0;
     int pf_iter = 0, pf_pred = 0;                // L2 prefetch distance: resident blocks of the kernel
@@ -258,6 +265,7 @@ IterArgs<T> make_args(npfem_ctx *ctx, MeshTypeImpl *t) {
     if constexpr (sizeof(T) == 8) a.tc = t->tc64;
     else a.tc = t->tc32;
     a.ncells = t->ncells;
+    a.zpred = (const T *)t->zp;
     a.m = ctx->opt.history;
     a.max_bt = ctx->opt.max_backtracks;
     a.use_allow = mixed(ctx) ? 1 : 0;
@@ -416,6 +424,8 @@ struct GemmItem {
     const CUtensorMap *mapZ;               // Z (FP32, width nV, 32 x 32 boxes)
     const int *conv;
     const CUtensorMap *mapQlo = nullptr;   // split form: low part of Q (P's low part from the type)
+    const CUtensorMap *mapB = nullptr;     // the matrix instead of P^{-1} (Mt^{-1}: damped predictor)
+    const CUtensorMap *mapBlo = nullptr;   // its low part (split form)
 };
 
 // One persistent launch (per MAXG items) over every item's (row tile, N tile) units.
@@ -440,11 +450,11 @@ void gemm_group(npfem_ctx *ctx, const std::vector<GemmItem> &items, int accumula
             P.conv = it.conv;
             units += P.m_tiles * P.n_ntiles;
             maps.q[g.nprob] = *it.mapQ;
-            maps.p[g.nprob] = it.t->mapP;
+            maps.p[g.nprob] = it.mapB ? *it.mapB : it.t->mapP;
             maps.z[g.nprob] = *it.mapZ;
             if (split_form) {
                 maps.q_lo[g.nprob] = *it.mapQlo;
-                maps.p_lo[g.nprob] = it.t->mapPlo;
+                maps.p_lo[g.nprob] = it.mapBlo ? *it.mapBlo : it.t->mapPlo;
             }
             max_nt = std::max(max_nt, it.t->n_tile);
             if (it.rows > best_rows) { best_rows = it.rows; stages = it.t->stages; }
@@ -595,6 +605,48 @@ void fallback_apply(npfem_ctx *ctx, MeshTypeImpl *t) {
 
 __global__ void k_set_ptr(double **slot, const double *p) { *slot = const_cast<double *>(p); }
 
+// Rayleigh-damped types: zp = Mt^{-1}(M v_n + h F_ext) for every cell, read by the
+// predictor (y = x_n + h zp) and again where the last iteration re-forms y in FP64.
+// FP64 form: SIMT FP64 apply; mixed forms: one grouped tensor-core apply of operands
+// split into high and low parts (three products, FP32 accumulation), no refinement.
+void damped_predictor_rhs(npfem_ctx *ctx) {
+    std::vector<GemmItem> items;
+    for (auto *t : ctx->types) {
+        if (!t->ncells || !t->damped) continue;
+        const long long total = 3ll * t->nVp * t->ncells;
+        const int grid = grid_for(total, 256, 8 * ctx->nsm);
+        prof_begin(ctx, NPFEM_K_PREDICT);
+        if (mixed(ctx))
+            k_damp_rhs<float><<<grid, 256, 0, ctx->stream>>>(t->ncells, t->nV, t->nVp, t->mass, t->vn, ctx->d_fslot,
+                                                             t->pub_off, t->vpub, t->h, (float *)t->q,
+                                                             bf16(ctx) ? t->q16 : nullptr, t->rlo_lo,
+                                                             bf16(ctx) ? nullptr : (float *)t->rlo);
+        else
+            k_damp_rhs<double><<<grid, 256, 0, ctx->stream>>>(t->ncells, t->nV, t->nVp, t->mass, t->vn, ctx->d_fslot,
+                                                              t->pub_off, t->vpub, t->h, (double *)t->q, nullptr,
+                                                              nullptr, nullptr);
+        CK(cudaGetLastError());
+        prof_end(ctx);
+        if (!mixed(ctx)) {
+            const int rows = 3 * t->ncells;
+            dim3 g2((t->nV + SG_T - 1) / SG_T, (rows + SG_T - 1) / SG_T);
+            prof_begin(ctx, NPFEM_K_GEMM);
+            k_gemm_simt<double><<<g2, 256, 0, ctx->stream>>>(rows, t->nV, t->nVp, (const double *)t->q, t->Minv64,
+                                                              (double *)t->zp);
+            CK(cudaGetLastError());
+            prof_end(ctx);
+        } else {
+            // low part of b: the BF16 low buffer, or (TF32) the FP32 residual buffer, free until
+            // the first refinement sweep of the step
+            GemmItem it{t, &t->mapQ, 3 * t->ncells, &t->mapZp, nullptr, bf16(ctx) ? &t->mapRlo : &t->mapR};
+            it.mapB = &t->mapM;
+            it.mapBlo = &t->mapMlo;
+            items.push_back(it);
+        }
+    }
+    if (!items.empty()) gemm_group(ctx, items, 0, true);
+}
+
 void enqueue_step(npfem_ctx *ctx) {
     // counters only: a pending error word survives until a synchronising call reads it
     CK(cudaMemsetAsync(reinterpret_cast<char *>(ctx->d_st) + sizeof(unsigned long long), 0,
@@ -615,6 +667,7 @@ void enqueue_step(npfem_ctx *ctx) {
         CK(cudaGetLastError());
         prof_end(ctx);
     }
+    damped_predictor_rhs(ctx);
     for (auto *t : ctx->types)
         if (t->ncells) run_predict(ctx, t);
     const int K = ctx->opt.iters;
@@ -676,6 +729,7 @@ struct HostType {
     std::vector<int> vt_ptr, vt_inc, vh_ptr, vh_inc;
     std::vector<double> vt_g, vh_c;
     std::vector<double> P;              // dense nV*nV
+    std::vector<double> Mt;             // dense nV*nV, Rayleigh-damped types only: M + h C
     double V0 = 0;
 };
 
@@ -865,10 +919,13 @@ void build_host_type(npfem_ctx *ctx, int nV, const double *X, int nT, const int3
                 H.vh_c[pos] = H.hc[4 * h + j];
             }
     }
-    // P = M/h^2 + k_vol I + sum_t (ws + wa) A_t^T A_t + sum_e kb A_e^T A_e
+    // L = k_vol I + sum_t (ws + wa) A_t^T A_t + sum_e kb A_e^T A_e (assembled in P),
+    // then P = (1 + h alpha) M/h^2 + (1 + beta/h) L = Mt/h^2 + L and, when damped,
+    // Mt = (1 + h alpha) M + h beta L
+    const double h = m.dt, ra = m.rayleigh_alpha, rb = m.rayleigh_beta;
+    const bool damped = ra != 0 || rb != 0;
     H.P.assign((size_t)nV * nV, 0.0);
-    const double ih2 = 1.0 / (m.dt * m.dt);
-    for (int v = 0; v < nV; ++v) H.P[(size_t)v * nV + v] += mass[v] * ih2 + m.k_vol;
+    for (int v = 0; v < nV; ++v) H.P[(size_t)v * nV + v] += damped ? m.k_vol : mass[v] / (h * h) + m.k_vol;
     for (int t = 0; t < nT; ++t) {
         const double *Di = &H.dinv[4 * t];
         double G[3][2] = {{-Di[0] - Di[2], -Di[1] - Di[3]}, {Di[0], Di[1]}, {Di[2], Di[3]}};
@@ -881,6 +938,14 @@ void build_host_type(npfem_ctx *ctx, int nV, const double *X, int nT, const int3
         for (int i = 0; i < 4; ++i)
             for (int j = 0; j < 4; ++j)
                 H.P[(size_t)H.hv[4 * h + i] * nV + H.hv[4 * h + j]] += m.k_bend * H.hc[4 * h + i] * H.hc[4 * h + j];
+    if (damped) {
+        H.Mt.resize(H.P.size());
+        for (size_t i = 0; i < H.P.size(); ++i) H.Mt[i] = h * rb * H.P[i];
+        for (int v = 0; v < nV; ++v) H.Mt[(size_t)v * nV + v] += (1.0 + h * ra) * mass[v];
+        const double sl = 1.0 + rb / h, wm = (1.0 + h * ra) / (h * h);
+        for (double &p : H.P) p *= sl;
+        for (int v = 0; v < nV; ++v) H.P[(size_t)v * nV + v] += mass[v] * wm;
+    }
 }
 
 template <typename T>
@@ -903,7 +968,12 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
         wtri[2 * i] = t->ks * H.area[i];
         wtri[2 * i + 1] = t->ka * H.area[i];
     }
-    for (int v = 0; v < t->nV; ++v) mh2[v] = mass[v] / (t->h * t->h);
+    // inertia diagonal of the local step: m/h^2, damped (1 + h alpha) m/h^2 + (beta/h) k_vol
+    // (Mt's mass part and the volume part of its beta L; the element parts of beta L are
+    // evaluated with the elements, weighted by beta/h)
+    for (int v = 0; v < t->nV; ++v)
+        mh2[v] = t->damped ? (1.0 + t->h * t->ra) * mass[v] / (t->h * t->h) + t->rb / t->h * t->kv
+                           : mass[v] / (t->h * t->h);
     c.tri = upload(ctx, tri, t->owned);
     c.dinv = upload(ctx, cvt<T>(H.dinv), t->owned);
     c.wtri = upload(ctx, cvt<T>(wtri), t->owned);
@@ -968,11 +1038,22 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
     c.vtol6 = 6.0 * Prec<T>::vol_tol * std::fabs(H.V0);
     c.kb = (T)t->kb;
     c.kv = (T)t->kv;
+    c.cd = (T)(t->rb / t->h);
     return c;
 }
 
-// P^{-1} in FP64 on the GPU (Gauss-Jordan), then the operand copies.
-void invert_on_gpu(npfem_ctx *ctx, MeshTypeImpl *t, const std::vector<double> &P) {
+// A^{-1} of an SPD matrix A (P, or Mt) in FP64 on the GPU (Gauss-Jordan), then the
+// operand copies the form uses: FP64 (FP64 form), FP32 (mixed forms), BF16 (BF16
+// form) and its BF16 low part (want_lo).
+struct InvCopies {
+    double *i64 = nullptr;
+    float *i32 = nullptr, *i32lo = nullptr;
+    __nv_bfloat16 *i16 = nullptr, *i16lo = nullptr;
+};
+
+InvCopies invert_on_gpu(npfem_ctx *ctx, MeshTypeImpl *t, const std::vector<double> &P, bool want64, bool want_lo,
+                        const char *what) {
+    InvCopies out;
     const int n = t->nV;
     std::vector<void *> tmp;
     double *A = dalloc<double>(ctx, (size_t)n * n, &tmp);
@@ -989,14 +1070,15 @@ void invert_on_gpu(npfem_ctx *ctx, MeshTypeImpl *t, const std::vector<double> &P
         int hbad = 0;
         CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
-        if (hbad) fail(ctx, NPFEM_ENOTSPD, "system matrix P is not positive definite");
-        t->Pinv64 = dalloc<double>(ctx, (size_t)n * t->nVp, &t->owned);
-        if (mixed(ctx)) t->Pinv32 = dalloc<float>(ctx, (size_t)n * t->nVp, &t->owned);
-        if (bf16(ctx)) t->Pinv16 = dalloc<__nv_bfloat16>(ctx, (size_t)n * t->nVp, &t->owned);
-        if (split(ctx)) t->Pinv16lo = dalloc<__nv_bfloat16>(ctx, (size_t)n * t->nVp, &t->owned);
-        k_convert_pinv<<<grid_for((long long)n * t->nVp, 256, 4096), 256, 0, ctx->stream>>>(n, t->nVp, A, t->Pinv64,
-                                                                                          t->Pinv32, t->Pinv16,
-                                                                                          t->Pinv16lo);
+        if (hbad) fail(ctx, NPFEM_ENOTSPD, "%s is not positive definite", what);
+        if (want64) out.i64 = dalloc<double>(ctx, (size_t)n * t->nVp, &t->owned);
+        if (mixed(ctx)) out.i32 = dalloc<float>(ctx, (size_t)n * t->nVp, &t->owned);
+        if (bf16(ctx)) out.i16 = dalloc<__nv_bfloat16>(ctx, (size_t)n * t->nVp, &t->owned);
+        if (bf16(ctx) && want_lo) out.i16lo = dalloc<__nv_bfloat16>(ctx, (size_t)n * t->nVp, &t->owned);
+        if (mixed(ctx) && !bf16(ctx) && want_lo) out.i32lo = dalloc<float>(ctx, (size_t)n * t->nVp, &t->owned);
+        k_convert_pinv<<<grid_for((long long)n * t->nVp, 256, 4096), 256, 0, ctx->stream>>>(n, t->nVp, A, out.i64,
+                                                                                          out.i32, out.i16,
+                                                                                          out.i16lo, out.i32lo);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(ctx->stream));
     } catch (...) {
@@ -1004,6 +1086,7 @@ void invert_on_gpu(npfem_ctx *ctx, MeshTypeImpl *t, const std::vector<double> &P
         throw;
     }
     for (void *p : tmp) cudaFree(p);
+    return out;
 }
 
 // GEMM tile autotuner: for each (device, nV, operand type) time the grouped
@@ -1032,6 +1115,12 @@ void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
         t->stages = st;
         t->mapP = make_map(ctx, pb, bf16(ctx), t->nV, t->nV, t->nVp, nt);
         if (t->Pinv16lo) t->mapPlo = make_map(ctx, t->Pinv16lo, true, t->nV, t->nV, t->nVp, nt);
+        if (t->damped) {
+            t->mapM = make_map(ctx, bf16(ctx) ? (const void *)t->Minv16 : (const void *)t->Minv32, bf16(ctx), t->nV,
+                               t->nV, t->nVp, nt);
+            if (t->Minv16lo) t->mapMlo = make_map(ctx, t->Minv16lo, true, t->nV, t->nV, t->nVp, nt);
+            if (t->Minv32lo) t->mapMlo = make_map(ctx, t->Minv32lo, false, t->nV, t->nV, t->nVp, nt);
+        }
     };
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1105,7 +1194,7 @@ void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
 
 void free_cells(MeshTypeImpl *t) {
     void **bufs[] = {(void **)&t->pub_off, (void **)&t->xn, (void **)&t->vn, &t->yrel, &t->delta, &t->grad, &t->q,
-                     &t->z, &t->S, &t->Y, &t->rlo, (void **)&t->rlo_lo, (void **)&t->q16, (void **)&t->origin, (void **)&t->rho,
+                     &t->z, &t->zp, &t->S, &t->Y, &t->rlo, (void **)&t->rlo_lo, (void **)&t->q16, (void **)&t->origin, (void **)&t->rho,
                      (void **)&t->alpha, (void **)&t->M, (void **)&t->g, (void **)&t->allow, (void **)&t->hcount,
                      (void **)&t->hhead, (void **)&t->conv, (void **)&t->fb_list, (void **)&t->fb_count};
     for (void **b : bufs) dfree(*b);
@@ -1120,11 +1209,12 @@ void alloc_cells(npfem_ctx *ctx, MeshTypeImpl *t, int cap) {
     t->vn = dalloc<double>(ctx, cap * n3);
     auto vec = [&](void *&p) { p = dalloc<unsigned char>(ctx, cap * n3 * es); };
     vec(t->yrel); vec(t->delta); vec(t->grad); vec(t->q); vec(t->z);
+    if (t->damped) vec(t->zp);
     t->S = dalloc<unsigned char>(ctx, cap * n3 * es * m);
     t->Y = dalloc<unsigned char>(ctx, cap * n3 * es * m);
     t->q16 = bf16(ctx) ? dalloc<__nv_bfloat16>(ctx, cap * n3) : nullptr;
     t->rlo = mixed(ctx) ? dalloc<unsigned char>(ctx, cap * n3 * (bf16(ctx) ? 2 : 4)) : nullptr;
-    t->rlo_lo = split(ctx) ? dalloc<__nv_bfloat16>(ctx, cap * n3) : nullptr;
+    t->rlo_lo = (split(ctx) || (bf16(ctx) && t->damped)) ? dalloc<__nv_bfloat16>(ctx, cap * n3) : nullptr;
     t->origin = dalloc<double>(ctx, 3 * (size_t)cap);
     t->rho = dalloc<double>(ctx, m * cap);
     t->alpha = dalloc<double>(ctx, m * cap);
@@ -1146,8 +1236,9 @@ void alloc_cells(npfem_ctx *ctx, MeshTypeImpl *t, int cap) {
     if (mixed(ctx)) {
         t->mapQ = make_map(ctx, bf16(ctx) ? (const void *)t->q16 : t->q, bf16(ctx), t->nV, 3ll * cap, t->nVp, tc::BM);
         t->mapR = make_map(ctx, t->rlo, bf16(ctx), t->nV, 3ll * cap, t->nVp, tc::BM);
-        if (split(ctx)) t->mapRlo = make_map(ctx, t->rlo_lo, true, t->nV, 3ll * cap, t->nVp, tc::BM);
+        if (t->rlo_lo) t->mapRlo = make_map(ctx, t->rlo_lo, true, t->nV, 3ll * cap, t->nVp, tc::BM);
         t->mapZ = make_map(ctx, t->z, false, t->nV, 3ll * cap, t->nVp, 32);
+        if (t->zp) t->mapZp = make_map(ctx, t->zp, false, t->nV, 3ll * cap, t->nVp, 32);
     }
 }
 
@@ -1275,6 +1366,9 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         if (nV > 2720) fail(ctx, NPFEM_EINVAL, "nV = %d exceeds the supported 2720 vertices per cell", nV);
         if (!(mat->dt > 0) || mat->k_strain < 0 || mat->k_area < 0 || mat->k_bend < 0 || mat->k_vol < 0)
             fail(ctx, NPFEM_EINVAL, "bad material");
+        if (!(mat->rayleigh_alpha >= 0) || !(mat->rayleigh_beta >= 0) || !std::isfinite(mat->rayleigh_alpha) ||
+            !std::isfinite(mat->rayleigh_beta))
+            fail(ctx, NPFEM_EINVAL, "Rayleigh damping coefficients must be finite and >= 0");
         std::vector<double> mass(nV);
         for (int v = 0; v < nV; ++v) {
             mass[v] = vertex_mass ? vertex_mass[v] : 1.0 / nV;
@@ -1342,6 +1436,9 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         t->ka = mat->k_area;
         t->kb = mat->k_bend;
         t->kv = mat->k_vol;
+        t->ra = mat->rayleigh_alpha;
+        t->rb = mat->rayleigh_beta;
+        t->damped = !H.Mt.empty();
         t->V0 = H.V0;
         if (mixed(ctx)) t->tc32 = upload_consts<float>(ctx, t, H, mass);
         else t->tc64 = upload_consts<double>(ctx, t, H, mass);
@@ -1402,7 +1499,22 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
                 t->ell_grid = nb * ctx->nsm;
             }
         }
-        invert_on_gpu(ctx, t, H.P);
+        {
+            const InvCopies pi = invert_on_gpu(ctx, t, H.P, true, bf16(ctx) && split(ctx), "system matrix P");
+            t->Pinv64 = pi.i64;
+            t->Pinv32 = pi.i32;
+            t->Pinv16 = pi.i16;
+            t->Pinv16lo = pi.i16lo;
+        }
+        if (t->damped) {
+            // the predictor's Mt^{-1}: FP64 in the FP64 form; split in the mixed forms
+            const InvCopies mi = invert_on_gpu(ctx, t, H.Mt, !mixed(ctx), true, "damped mass matrix M + hC");
+            t->Minv64 = mi.i64;
+            t->Minv32 = mi.i32;
+            t->Minv32lo = mi.i32lo;
+            t->Minv16 = mi.i16;
+            t->Minv16lo = mi.i16lo;
+        }
         // per-cell kernel shape: EPT elements per thread, block <= 256 (<= 512 for big meshes)
         const int n3 = 3 * t->nVp;
         if ((n3 + 3) / 4 <= 256) t->ept = 4;

@@ -26,6 +26,7 @@ struct IterArgs {
     const long long *pub_off;     // [cell] offset of the cell in the public arrays (doubles)
     const int *vpub;              // [nV] the caller's index of internal vertex v
     const double *minv;           // [nV] 1 / m_v
+    const T *zpred;               // Rayleigh-damped type: Mt^{-1}(M v_n + h F_ext) per cell (SoA), else null
     T *yrel;                      // y - origin
     double *origin;               // [cell][3]
     T *delta, *grad, *q, *z;
@@ -80,7 +81,8 @@ __device__ __forceinline__ void store_vec_bf16(__nv_bfloat16 *__restrict__ p, co
     }
 }
 
-// y = x_n + h v_n + h^2 M^{-1} F_ext in FP64 for this thread's elements.
+// y = x_n + h v_n + h^2 M^{-1} F_ext in FP64 for this thread's elements; with
+// Rayleigh damping y = x_n + h Mt^{-1}(M v_n + h F_ext), the solve done before.
 template <typename T, int EPT>
 __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, double (&y)[EPT], double (&xo)[EPT]) {
     const int nVp = a.tc.nVp, nV = a.tc.nV, n3 = 3 * nVp;
@@ -99,6 +101,17 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
         const int c = elem_cv(e0, nVp, v0);
         double xv[4], vv[4];
         ld4(a.xn + base + e0, xv);
+        if (a.zpred) {
+            T zv[4];
+            ld4(a.zpred + base + e0, zv);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (v0 + i >= nV) continue;
+                xo[4 * g + i] = xv[i];
+                y[4 * g + i] = xv[i] + a.h * (double)zv[i];
+            }
+            continue;
+        }
         ld4(a.vn + base + e0, vv);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -146,6 +159,37 @@ __device__ __forceinline__ void block_sum_many(const T (&part)[NMAX], int n1, in
 
 // Start of a step: y, origin (centroid of y), y_rel, delta = 0, history
 // cleared, g and grad g at x^0 = y, and q = grad g (the first apply's RHS).
+// Right-hand side of the damped predictor, b = M v_n + h F_ext (SoA rows of nVp,
+// zero padding), as the apply's operand: q in the form's type and split into a
+// high and a low part for the tensor cores: BF16 form hi/lo in BF16 (~16 bits),
+// TF32 form q = its TF32 high part and lo32 the FP32 rest (~21 bits).
+template <typename T>
+__global__ void k_damp_rhs(int ncells, int nV, int nVp, const double *__restrict__ mass, const double *__restrict__ vn,
+                           const double *const *fptr, const long long *__restrict__ pub_off,
+                           const int *__restrict__ vpub, double h, T *__restrict__ q, __nv_bfloat16 *__restrict__ hi,
+                           __nv_bfloat16 *__restrict__ lo, float *__restrict__ lo32) {
+    const long long n3 = 3ll * nVp, total = (long long)ncells * n3;
+    const double *f = *fptr;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long cell = i / n3;
+        const int e = (int)(i - cell * n3), c = e / nVp, v = e - c * nVp;
+        double b = 0.0;
+        if (v < nV) b = mass[v] * vn[i] + h * f[pub_off[cell] + 3 * vpub[v] + c];
+        q[i] = (T)b;
+        if (lo32) {
+            const float bh = tf32_hi((float)b);
+            q[i] = (T)bh;
+            lo32[i] = (float)(b - (double)bh);
+        }
+        if (hi) {
+            const __nv_bfloat16 bh = __float2bfloat16_rn((float)b);
+            hi[i] = bh;
+            lo[i] = __float2bfloat16_rn((float)(b - (double)__bfloat162float(bh)));
+        }
+    }
+}
+
 template <typename T, int EPT, int MAXB>
 __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) : 1) k_predict(IterArgs<T> a) {
     const Smem<T> S = smem_layout<T>(a.tc.nVp);

@@ -133,6 +133,8 @@ class Material:
     k_bend: float
     k_vol: float
     dt: float
+    rayleigh_alpha: float = 0.0     # Rayleigh damping C = alpha M + beta L (0, 0: none)
+    rayleigh_beta: float = 0.0
 
 
 @dataclass

@@ -45,7 +45,8 @@ class Options(C.Structure):
 
 class Material(C.Structure):
     _fields_ = [("k_strain", C.c_double), ("k_area", C.c_double), ("k_bend", C.c_double),
-                ("k_vol", C.c_double), ("dt", C.c_double)]
+                ("k_vol", C.c_double), ("dt", C.c_double), ("rayleigh_alpha", C.c_double),
+                ("rayleigh_beta", C.c_double)]
 
 
 class StepStats(C.Structure):
@@ -172,13 +173,14 @@ class Solver:
             pass
 
     # -- set-up -----------------------------------------------------------------
-    def create_mesh_type(self, rest, tris, k_strain, k_area, k_bend, k_vol, dt, mass=None) -> int:
+    def create_mesh_type(self, rest, tris, k_strain, k_area, k_bend, k_vol, dt, mass=None,
+                         rayleigh_alpha=0.0, rayleigh_beta=0.0) -> int:
         rest, rp = _host(np.asarray(rest).reshape(-1, 3))
         tris = np.ascontiguousarray(np.asarray(tris).reshape(-1, 3), dtype=np.int32)
         mp = None
         if mass is not None:
             mass, mp = _host(mass)
-        mat = Material(k_strain, k_area, k_bend, k_vol, dt)
+        mat = Material(k_strain, k_area, k_bend, k_vol, dt, rayleigh_alpha, rayleigh_beta)
         tid = C.c_int()
         self._check(self._L.npfem_create_mesh_type(self._ctx, rest.shape[0], rp, tris.shape[0],
                                                    tris.ctypes.data_as(C.c_void_p), mp, C.byref(mat),
@@ -190,7 +192,8 @@ class Solver:
         """Register an inputs.MeshType."""
         m = mtype.material
         return self.create_mesh_type(mtype.rest, mtype.tris, m.k_strain, m.k_area, m.k_bend, m.k_vol,
-                                     m.dt, mtype.mass)
+                                     m.dt, mtype.mass, getattr(m, "rayleigh_alpha", 0.0),
+                                     getattr(m, "rayleigh_beta", 0.0))
 
     def add_cells(self, type_id, x0, v0=None) -> int:
         x0, xp = _host(x0)
