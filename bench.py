@@ -22,6 +22,7 @@ steps its own suspension (weak scaling, no data-path collective).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -139,13 +140,22 @@ def algorithmic_gemm(nV, cells, bf16):
     return n * ((2 if bf16 else 4) + 4), 2.0 * nV * n
 
 
+def with_damping(groups, alpha, beta):
+    """Rayleigh damping C = alpha M + beta L on every group's mesh type (0, 0: unchanged)."""
+    if alpha or beta:
+        for g in groups:
+            mat = dataclasses.replace(g.mtype.material, rayleigh_alpha=alpha, rayleigh_beta=beta)
+            g.mtype = dataclasses.replace(g.mtype, material=mat)
+    return groups
+
+
 # ---------------------------------------------------------------- reference
 def run_reference(args, workload):
     """The FP64 CPU oracle timed on the host cores (the reference arm)."""
     from paper_1911_03062_gb300 import inputs as I
     from oracle import oracle as O
     O.build()
-    groups = I.workload_groups(workload)
+    groups = with_damping(I.workload_groups(workload), args.rayleigh_alpha, args.rayleigh_beta)
     threads = os.cpu_count() or 1
     sample_rbc, sample_plt = args.ref_sample
     picks = []
@@ -178,13 +188,13 @@ def run_reference(args, workload):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(workload, n_rbc=768, n_plt=96):
+def cpu_baseline(workload, n_rbc=768, n_plt=96, alpha=0.0, beta=0.0):
     """Oracle on the host cores over a bounded sample (1 step, K=10)."""
     from paper_1911_03062_gb300 import inputs as I
     from oracle import oracle as O
     O.build()
     threads = os.cpu_count() or 1
-    groups = I.workload_groups(workload)
+    groups = with_damping(I.workload_groups(workload), alpha, beta)
     t_total, cells = 0.0, 0
     for g, n in zip(groups, (n_rbc, n_plt)):
         sub = I.materialise(I.Group(g.mtype, n, g.seed, g.amp))
@@ -214,6 +224,8 @@ def main():
     ap.add_argument("--force-median", action="store_true", help="one-ring median filter of the forces before each step")
     ap.add_argument("--u-max", type=float, default=0.0, help="velocity cap after each step (0: off)")
     ap.add_argument("--pbd-kappa", type=float, default=0.0, help="PBD velocity damping after each step (0: off)")
+    ap.add_argument("--rayleigh-alpha", type=float, default=0.0, help="Rayleigh damping C = alpha M + beta L")
+    ap.add_argument("--rayleigh-beta", type=float, default=0.0, help="(the paper's table: alpha 0, beta 0.01)")
     args = ap.parse_args()
     rank, world, local = env_rank()
 
@@ -247,7 +259,7 @@ def main():
 
     wl = I.WORKLOADS[args.workload]
     precision = args.precision or wl["precision"]
-    groups = I.workload_groups(args.workload)
+    groups = with_damping(I.workload_groups(args.workload), args.rayleigh_alpha, args.rayleigh_beta)
     for g in groups:
         g.seed += 7919 * rank           # each rank steps its own suspension
         I.materialise(g)
@@ -438,11 +450,12 @@ def main():
                        "local_step": "fp32" if precision != "fp64" else "fp64",
                        "l2": "inputs larger than L2 (state + forces ~1.6 GB), no flush",
                        "parallelism": f"{world} independent ranks" if world > 1 else "1 GPU",
-                       "force_median": bool(args.force_median), "u_max": args.u_max, "pbd_kappa": args.pbd_kappa},
+                       "force_median": bool(args.force_median), "u_max": args.u_max, "pbd_kappa": args.pbd_kappa,
+                       "rayleigh_alpha": args.rayleigh_alpha, "rayleigh_beta": args.rayleigh_beta},
             "clocks": clk, "gpu_launches": launches, "parity": parity, "fp64_gpu": fp64, "e2e": e2e,
             "roofline": roof, "kernels": kernels, "solver": solver}
     if not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args.workload)
+        line["cpu_baseline"] = cpu_baseline(args.workload, alpha=args.rayleigh_alpha, beta=args.rayleigh_beta)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
