@@ -22,6 +22,9 @@
  *   damping : optional Rayleigh C = alpha M + beta L, L = sum_i w_i A_i^T A_i
  *             (volume term included); Mt = M + h C replaces M in the inertia
  *             term and y = x_n + h Mt^{-1}(M v_n + h F_ext).
+ *   contact : optional particle-in-kernel (PIK) collisions: brute-force search
+ *             of the closest foreign vertex inside the kernel, its fluid force
+ *             dropped, kc/2 |x - p|^2 toward a plane projection p (fixed per step).
  * The global solves use this file's own sparse (RCM + envelope) Cholesky.
  *
  * Public layout: positions, velocities, forces are [nV][3] doubles per cell.
@@ -278,10 +281,32 @@ static int volume_project(const orc_type *T, const double *x, double *p, double 
  * Mt/h^2 (x - y) + sum_i w_i A_i^T (A_i x - p_i).
  * terms[0..4] receive the inertia(+damping)/strain/area/bending/volume parts.
  */
+/* PIK collision term of one cell: kc/2 |x_v - p_v|^2 for every vertex with hit[v] != 0. */
+typedef struct {
+    double kc;
+    const int *hit;      /* [nV] */
+    const double *p;     /* [nV][3] targets */
+} orc_coll;
+
+static double energy_impl(const orc_type *T, const double *x, const double *y, int mask,
+                          double *grad, double *terms, const orc_coll *cc);
+
 double orc_energy(const orc_type *T, const double *x, const double *y, int mask,
                   double *grad, double *terms) {
+    return energy_impl(T, x, y, mask, grad, terms, NULL);
+}
+
+/* g with the PIK collision term (its energy is in the total, not in terms[]). */
+double orc_energy_col(const orc_type *T, const double *x, const double *y, int mask,
+                      double *grad, double *terms, double kc, const int *hit, const double *p) {
+    orc_coll cc = {kc, hit, p};
+    return energy_impl(T, x, y, mask, grad, terms, &cc);
+}
+
+static double energy_impl(const orc_type *T, const double *x, const double *y, int mask,
+                          double *grad, double *terms, const orc_coll *cc) {
     int nV = T->nV;
-    double e[5] = {0, 0, 0, 0, 0};
+    double e[5] = {0, 0, 0, 0, 0}, ecol = 0;
     if (grad) memset(grad, 0, sizeof(double)*3*nV);
     double ih2 = (1.0 + T->h*T->ra)/(T->h*T->h);      /* (1 + h ra)/h^2: Mt's mass part */
     if (mask & TERM_INERTIA) {
@@ -365,8 +390,18 @@ double orc_energy(const orc_type *T, const double *x, const double *y, int mask,
         }
         free(p);
     }
+    if (cc && cc->hit) {
+        for (int v = 0; v < nV; ++v) {
+            if (!cc->hit[v]) continue;
+            for (int c = 0; c < 3; ++c) {
+                double r = x[3*v+c] - cc->p[3*v+c];
+                ecol += 0.5*cc->kc*r*r;
+                if (grad) grad[3*v+c] += cc->kc*r;
+            }
+        }
+    }
     if (terms) for (int i = 0; i < 5; ++i) terms[i] = e[i];
-    return e[0] + e[1] + e[2] + e[3] + e[4];
+    return e[0] + e[1] + e[2] + e[3] + e[4] + ecol;
 }
 
 /* ----------------------------------------------------------- sparse matrix */
@@ -776,10 +811,32 @@ static double vdot(const double *a, const double *b, int n) {
  * bt_tr[K] halvings, fb_tr[K] 1 where the descent fallback ran.
  * Returns the number of iterations whose line search hit the cap.
  */
+static int step_impl(const orc_type *T, const double *xn, const double *vn, const double *f_in,
+                     int K, int m, double c1, int max_bt, const orc_coll *cc,
+                     double *x_out, double *v_out,
+                     double *g_tr, double *a_tr, int *bt_tr, int *fb_tr);
+
 int orc_step(const orc_type *T, const double *xn, const double *vn, const double *f,
              int K, int m, double c1, int max_bt,
              double *x_out, double *v_out,
              double *g_tr, double *a_tr, int *bt_tr, int *fb_tr) {
+    return step_impl(T, xn, vn, f, K, m, c1, max_bt, NULL, x_out, v_out, g_tr, a_tr, bt_tr, fb_tr);
+}
+
+/* The step with the PIK collision framework (Sec. 2.2, Supp. PIK): the
+ * external (fluid) force of every vertex with hit[v] != 0 is disregarded and
+ * the term kc/2 |x_v - p_v|^2 joins g, with the targets p fixed over the step. */
+int orc_step_col(const orc_type *T, const double *xn, const double *vn, const double *f,
+                 int K, int m, double c1, int max_bt, double kc, const int *hit, const double *p,
+                 double *x_out, double *v_out) {
+    orc_coll cc = {kc, hit, p};
+    return step_impl(T, xn, vn, f, K, m, c1, max_bt, &cc, x_out, v_out, NULL, NULL, NULL, NULL);
+}
+
+static int step_impl(const orc_type *T, const double *xn, const double *vn, const double *f_in,
+                     int K, int m, double c1, int max_bt, const orc_coll *cc,
+                     double *x_out, double *v_out,
+                     double *g_tr, double *a_tr, int *bt_tr, int *fb_tr) {
     int nV = T->nV, n3 = 3*nV;
     double h = T->h;
     int mm = m > 0 ? m : 1;
@@ -788,19 +845,28 @@ int orc_step(const orc_type *T, const double *xn, const double *vn, const double
     double *q = gt + n3, *r = q + n3;
     double *S = r + n3, *Y = S + n3*mm;
     double *rho = (double *)malloc(sizeof(double)*mm), *al = (double *)malloc(sizeof(double)*mm);
+    double *fz = NULL;
+    const double *f = f_in;
+    if (cc && cc->hit) {                    /* PIK: contaminated vertices lose their fluid force */
+        fz = (double *)malloc(sizeof(double)*n3);
+        for (int v = 0; v < nV; ++v)
+            for (int c = 0; c < 3; ++c) fz[3*v+c] = cc->hit[v] ? 0.0 : f_in[3*v+c];
+        f = fz;
+    }
     if (T->ra == 0 && T->rb == 0) {
         for (int v = 0; v < nV; ++v)
             for (int c = 0; c < 3; ++c)
                 y[3*v+c] = xn[3*v+c] + h*vn[3*v+c] + h*h/T->mass[v]*f[3*v+c];
     } else {
         /* y = x_n + h Mt^{-1} (M v_n + h F_ext)  (x buffer as scratch) */
+        memset(x, 0, sizeof(double)*n3);
         for (int v = 0; v < nV; ++v)
             for (int c = 0; c < 3; ++c) x[3*v+c] = T->mass[v]*vn[3*v+c] + h*f[3*v+c];
         solve_env(nV, T->mperm, T->mfirst, T->mrowstart, T->menv, x, y);
         for (int i = 0; i < n3; ++i) y[i] = xn[i] + h*y[i];
     }
     memcpy(x, y, sizeof(double)*n3);
-    double g = orc_energy(T, x, y, TERM_ALL, gr, NULL);
+    double g = energy_impl(T, x, y, TERM_ALL, gr, NULL, cc);
     if (g_tr) g_tr[0] = g;
     int cnt = 0, head = 0, caps = 0;    /* ring: newest at (head-1) mod m */
     for (int k = 0; k < K; ++k) {
@@ -834,7 +900,7 @@ int orc_step(const orc_type *T, const double *xn, const double *vn, const double
         int bt = 0;
         for (;;) {
             for (int i = 0; i < n3; ++i) xt[i] = x[i] + alpha*d[i];
-            gtv = orc_energy(T, xt, y, TERM_ALL, gt, NULL);
+            gtv = energy_impl(T, xt, y, TERM_ALL, gt, NULL, cc);
             if (gtv <= g + c1*alpha*gd) break;
             if (bt == max_bt) { ++caps; break; }
             alpha *= 0.5; ++bt;
@@ -862,7 +928,7 @@ int orc_step(const orc_type *T, const double *xn, const double *vn, const double
         x_out[i] = x[i];
         v_out[i] = (x[i] - xn[i]) / h;
     }
-    free(buf); free(rho); free(al);
+    free(buf); free(rho); free(al); free(fz);
     return caps;
 }
 
@@ -986,4 +1052,81 @@ int orc_step_cells(const orc_type *T, int n, const double *xn, const double *vn,
         caps += orc_step(T, xn + c*n3, vn + c*n3, f + c*n3, K, m, c1, max_bt,
                          x_out + c*n3, v_out + c*n3, NULL, NULL, NULL, NULL);
     return caps;
+}
+
+/* n cells of one type with the PIK collision term (hit: [n][nV], p: [n][nV][3]). */
+int orc_step_cells_col(const orc_type *T, int n, const double *xn, const double *vn, const double *f,
+                       int K, int m, double c1, int max_bt, double kc, const int *hit, const double *p,
+                       double *x_out, double *v_out) {
+    long n3 = 3L*T->nV;
+    int caps = 0;
+    for (int c = 0; c < n; ++c)
+        caps += orc_step_col(T, xn + c*n3, vn + c*n3, f + c*n3, K, m, c1, max_bt, kc, hit + c*(long)T->nV,
+                             p + c*n3, x_out + c*n3, v_out + c*n3);
+    return caps;
+}
+
+/* ---------------------------------------------------- PIK collision framework
+ * Vertex normals of one cell: the sum over the incident triangles of
+ * (x_b - x_a) x (x_c - x_a) (area-weighted outward normal), normalised.
+ * x, n: [nV][3]. */
+void orc_vertex_normals(const orc_type *T, const double *x, double *n) {
+    int nV = T->nV;
+    memset(n, 0, sizeof(double)*3*nV);
+    for (int t = 0; t < T->nT; ++t) {
+        const int *v = T->tri + 3*t;
+        double e1[3], e2[3], cr[3];
+        sub3(x + 3*v[1], x + 3*v[0], e1);
+        sub3(x + 3*v[2], x + 3*v[0], e2);
+        cross3(e1, e2, cr);
+        for (int k = 0; k < 3; ++k)
+            for (int c = 0; c < 3; ++c) n[3*v[k]+c] += cr[c];
+    }
+    for (int i = 0; i < nV; ++i) {
+        double l = sqrt(dot3(n + 3*i, n + 3*i));
+        if (l > 0) for (int c = 0; c < 3; ++c) n[3*i+c] /= l;
+    }
+}
+
+/* Particle-in-kernel search (paper Sec. 2.2 and the supplementary PIK section)
+ * over ncells cells, cell c with nV[c] vertices at x[c] and normals nrm[c]
+ * ([nV][3] each).  For every vertex i: among the vertices j of the other cells
+ * inside the kernel, |x_j - x_i|^2 < rk^2, the closest one (ties: lower cell,
+ * then lower vertex) is the colliding neighbour.  Reading of the projection:
+ * p_i = x_i + (rk - s) n_j, s = (x_i - x_j).n_j, the closest point to x_i on the
+ * far side of the plane through x_j + rk n_j normal to n_j.
+ * Outputs, cells concatenated: hit_cell/hit_vert (-1 when no foreign vertex is in
+ * the kernel) and p ([.][3]; x_i when none). */
+int orc_pik(int ncells, const int *nV, const double *const *x, const double *const *nrm, double rk,
+            int *hit_cell, int *hit_vert, double *p) {
+    if (!(rk > 0)) return ORC_EINVAL;
+    double r2 = rk*rk;
+    long o = 0;
+    for (int a = 0; a < ncells; ++a) {
+        for (int i = 0; i < nV[a]; ++i, ++o) {
+            const double *xi = x[a] + 3*i;
+            double best = r2;
+            int bc = -1, bv = -1;
+            for (int b = 0; b < ncells; ++b) {
+                if (b == a) continue;
+                for (int j = 0; j < nV[b]; ++j) {
+                    const double *xj = x[b] + 3*j;
+                    double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+                    double d2 = dx*dx + dy*dy + dz*dz;
+                    /* cells and vertices are visited in increasing order: a strict
+                       improvement keeps the lowest index among equal distances */
+                    if (d2 < best) { best = d2; bc = b; bv = j; }
+                }
+            }
+            hit_cell[o] = bc;
+            hit_vert[o] = bv;
+            for (int c = 0; c < 3; ++c) p[3*o+c] = xi[c];
+            if (bc >= 0) {
+                const double *xj = x[bc] + 3*bv, *nj = nrm[bc] + 3*bv;
+                double s = (xi[0] - xj[0])*nj[0] + (xi[1] - xj[1])*nj[1] + (xi[2] - xj[2])*nj[2];
+                for (int c = 0; c < 3; ++c) p[3*o+c] = xi[c] + (rk - s)*nj[c];
+            }
+        }
+    }
+    return ORC_OK;
 }

@@ -76,6 +76,14 @@ def lib():
             L.orc_pbd_damping.restype = C.c_int
             L.orc_type_set_damping.argtypes = [vp, C.c_double, C.c_double]
             L.orc_type_set_damping.restype = C.c_int
+            L.orc_vertex_normals.argtypes = [vp, dp, dp]
+            L.orc_pik.argtypes = [C.c_int, ip, vp, vp, C.c_double, ip, ip, dp]
+            L.orc_pik.restype = C.c_int
+            L.orc_energy_col.argtypes = [vp, dp, dp, C.c_int, vp, vp, C.c_double, ip, dp]
+            L.orc_energy_col.restype = C.c_double
+            L.orc_step_cells_col.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, C.c_int, C.c_double,
+                                             C.c_int, C.c_double, vp, vp, vp, vp]
+            L.orc_step_cells_col.restype = C.c_int
             _lib = L
     return _lib
 
@@ -158,6 +166,23 @@ class OracleType:
         e = lib().orc_energy(self._h, x, y, mask, _ptr(g), _ptr(terms))
         return e, g, terms
 
+    def energy_col(self, x, y, kc, hit, p, mask=TERM_ALL, grad=True):
+        """g with the PIK collision term kc/2 |x_v - p_v|^2 over the vertices with hit != 0."""
+        x = _c(x).reshape(self.nV, 3)
+        y = _c(y).reshape(self.nV, 3)
+        g = np.empty_like(x) if grad else None
+        terms = np.empty(5)
+        e = lib().orc_energy_col(self._h, x, y, mask, _ptr(g), _ptr(terms), kc,
+                                 _c(hit, np.int32), _c(p).reshape(self.nV, 3))
+        return e, g, terms
+
+    def normals(self, x):
+        """Area-weighted outward vertex normals, normalised ([nV, 3])."""
+        x = _c(x).reshape(self.nV, 3)
+        n = np.empty_like(x)
+        lib().orc_vertex_normals(self._h, x, n)
+        return n
+
     def volume(self, p):
         return lib().orc_volume(self._h, _c(p).reshape(self.nV, 3))
 
@@ -183,6 +208,16 @@ class OracleType:
                                   _ptr(gt), _ptr(at), _ptr(bt), _ptr(fb))
             return xo, vo, dict(g=gt, alpha=at, backtracks=bt, fallback=fb, caps=caps)
         lib().orc_step(self._h, xn, vn, f, K, m, c1, max_bt, xo, vo, None, None, None, None)
+        return xo, vo
+
+    def step_cells_col(self, xn, vn, f, kc, hit, p, K=10, m=5, c1=1e-4, max_bt=8):
+        """Step n cells with the PIK collision term: hit [n, nV] (nonzero = contaminated
+        vertex: fluid force dropped, kc/2 |x - p|^2 added), p [n, nV, 3] targets."""
+        xn, vn, f, p = (_c(a).reshape(-1, self.nV, 3) for a in (xn, vn, f, p))
+        hit = _c(hit, np.int32).reshape(-1, self.nV)
+        xo, vo = np.empty_like(xn), np.empty_like(xn)
+        lib().orc_step_cells_col(self._h, xn.shape[0], _ptr(xn), _ptr(vn), _ptr(f), K, m, c1, max_bt, kc,
+                                 _ptr(hit), _ptr(p), _ptr(xo), _ptr(vo))
         return xo, vo
 
     def step_cells(self, xn, vn, f, K=10, m=5, c1=1e-4, max_bt=8, threads=1):
@@ -268,3 +303,38 @@ def predictor(xn, vn, f, dt, nV, mass=None):
     """y = x_n + h v_n + h^2 M^{-1} F_ext (Eq. genericOptimizationNewton, C = 0)."""
     m = (1.0 / nV) if mass is None else np.asarray(mass)[:, None]
     return xn + dt * vn + dt * dt / m * f
+
+
+def pik(cells, rk):
+    """Particle-in-kernel search over all cells (list of (OracleType, x [nV, 3])):
+    returns per cell (hit_cell [nV], hit_vert [nV], p [nV, 3]) with -1 where no
+    foreign vertex lies within rk, and the targets p (x where none)."""
+    xs = [_c(x).reshape(T.nV, 3) for T, x in cells]
+    ns = [T.normals(x) for (T, _), x in zip(cells, xs)]
+    nV = np.array([T.nV for T, _ in cells], np.int32)
+    tot = int(nV.sum())
+    hc, hv = np.empty(tot, np.int32), np.empty(tot, np.int32)
+    p = np.empty((tot, 3))
+    xp = (C.c_void_p * len(cells))(*[x.ctypes.data for x in xs])
+    npp = (C.c_void_p * len(cells))(*[n.ctypes.data for n in ns])
+    rc = lib().orc_pik(len(cells), nV, C.cast(xp, C.c_void_p), C.cast(npp, C.c_void_p), float(rk), hc, hv, p)
+    if rc != 0:
+        raise ValueError(f"orc_pik failed ({rc})")
+    out, o = [], 0
+    for T, _ in cells:
+        out.append((hc[o:o + T.nV], hv[o:o + T.nV], p[o:o + T.nV]))
+        o += T.nV
+    return out
+
+
+def pik_step(cells, f, rk, kc, K=10, m=5):
+    """One step of every cell with the PIK collision framework: the search on the
+    state at the start of the step, then each cell's step with its targets.
+    cells: list of (OracleType, x, v); f: list of forces.  Returns [(x1, v1)]."""
+    res = pik([(T, x) for T, x, _ in cells], rk)
+    out = []
+    for (T, x, v), fc, (hc, _, p) in zip(cells, f, res):
+        xo, vo = T.step_cells_col(x[None], v[None], fc[None], kc, (hc >= 0).astype(np.int32)[None], p[None],
+                                  K=K, m=m)
+        out.append((xo[0], vo[0]))
+    return out

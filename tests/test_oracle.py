@@ -578,3 +578,168 @@ def test_damped_step_mean_velocity_closed_form(O, rbc):
     h, m, kv = mt.material.dt, 1.0 / mt.nV, mt.material.k_vol
     expect = vn.mean(axis=0) / (1 + h * ALPHA + h * BETA * kv / m)
     assert np.allclose(v1.mean(axis=0), expect, rtol=1e-9, atol=1e-12)
+
+
+# ------------------------------------------------------------------ PIK collisions
+RK, KC = 0.5, 200.0
+
+
+def octahedron():
+    v = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], float)
+    t = []
+    for sx in (0, 1):
+        for sy in (2, 3):
+            for sz in (4, 5):
+                tri = [sx, sy, sz]
+                a, b, c = v[tri]
+                if np.dot(np.cross(b - a, c - a), a + b + c) < 0:
+                    tri = [sx, sz, sy]
+                t.append(tri)
+    return v, np.array(t, np.int32)
+
+
+def test_vertex_normals_of_regular_solids(O):
+    # by symmetry the area-weighted normal of a regular polyhedron's vertex is radial
+    v, t = octahedron()
+    T = O.OracleType(v, t, 1.0, 5.0, 0.05, 10.0, 1e-3)
+    assert np.array_equal(T.normals(v), v)
+    unit, tris = I.icosphere(0)
+    Ti = O.OracleType(unit * 2.0, tris, 1.0, 5.0, 0.05, 10.0, 1e-3)
+    R = rot(50)
+    x = unit @ R.T * 2.0 + np.array([3.0, -1.0, 7.0])
+    assert np.allclose(Ti.normals(x), unit @ R.T, atol=1e-14)
+
+
+def test_pik_head_on_closed_form(O):
+    # A's vertex (0,0,1) faces B's vertex (0,0,1+d) whose normal is (0,0,-1):
+    # s = d, p = x_i + (rk - d)(0,0,-1); every other pair is farther than rk
+    v, t = octahedron()
+    T = O.OracleType(v, t, 1.0, 5.0, 0.05, 10.0, 1e-3)
+    d = 0.2
+    xa, xb = v.copy(), v * np.array([1.0, -1.0, -1.0]) + np.array([0.0, 0.0, 2.0 + d])   # B: A turned about x
+    (hca, hva, pa), (hcb, hvb, pb) = O.pik([(T, xa), (T, xb)], RK)
+    assert (hca >= 0).sum() == 1 and hca[4] == 1 and hva[4] == 4      # B's vertex 4 sits at (0,0,1+d)
+    assert np.allclose(pa[4], [0.0, 0.0, 1.0 - (RK - d)], atol=1e-15)
+    assert hcb[4] == 0 and hvb[4] == 4 and np.allclose(pb[4], [0.0, 0.0, 1.0 + d + (RK - d)], atol=1e-15)
+    free = hca < 0
+    assert np.array_equal(pa[free], xa[free])
+
+
+def _overlapping_cells(seed, n=3, level=1):
+    unit, tris = I.icosphere(level)
+    rest = I.rbc_shape(unit) * 0.5
+    rng = np.random.default_rng(seed)
+    xs = [rest @ rot(seed + i).T + rng.uniform(-1.0, 1.0, 3) for i in range(n)]
+    return rest, tris, xs
+
+
+def test_pik_matches_kdtree_and_projects_onto_the_plane(O):
+    spatial = pytest.importorskip("scipy.spatial")
+    rest, tris, xs = _overlapping_cells(51)
+    T = O.OracleType(rest, tris, 1.0, 5.0, 0.05, 10.0, 1e-3)
+    res = O.pik([(T, x) for x in xs], RK)
+    nrm = [T.normals(x) for x in xs]
+    hits = 0
+    for a, (hc, hv, p) in enumerate(res):
+        others = [b for b in range(len(xs)) if b != a]
+        pts = np.vstack([xs[b] for b in others])
+        owner = np.concatenate([[b] * len(xs[b]) for b in others])
+        vert = np.concatenate([np.arange(len(xs[b])) for b in others])
+        dist, idx = spatial.cKDTree(pts).query(xs[a], distance_upper_bound=RK)
+        found = np.isfinite(dist)
+        assert np.array_equal(hc >= 0, found)
+        assert np.array_equal(hc[found], owner[idx[found]]) and np.array_equal(hv[found], vert[idx[found]])
+        for i in np.flatnonzero(found):
+            xj, nj = xs[hc[i]][hv[i]], nrm[hc[i]][hv[i]]
+            assert np.dot(p[i] - xj, nj) == pytest.approx(RK, abs=1e-13)          # on the plane
+            assert np.linalg.norm(np.cross(p[i] - xs[a][i], nj)) < 1e-13          # moved along n_j
+        hits += found.sum()
+    assert hits > 20
+
+
+def test_collision_gradient_central_differences(O):
+    rest, tris, T = small_rbc(O, 1)
+    rng = np.random.default_rng(52)
+    x = rest * 1.05 + 0.05 * rng.standard_normal(rest.shape)
+    y = rest + 0.05 * rng.standard_normal(rest.shape)
+    hit = (rng.uniform(size=rest.shape[0]) < 0.3).astype(np.int32)
+    p = x + 0.2 * rng.standard_normal(rest.shape)
+    e, g, _ = T.energy_col(x, y, KC, hit, p)
+    e0, g0, _ = T.energy(x, y)
+    assert e - e0 == pytest.approx(0.5 * KC * (((x - p) ** 2).sum(axis=1) * hit).sum(), rel=1e-12)
+    hh = 1e-6
+    fd = np.zeros_like(x)
+    for i in range(x.shape[0]):
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, c] += hh
+            xm[i, c] -= hh
+            fd[i, c] = (T.energy_col(xp, y, KC, hit, p, grad=False)[0] - T.energy_col(xm, y, KC, hit, p, grad=False)[0]) / (2 * hh)
+    assert np.linalg.norm(g - fd) <= 1e-6 * np.linalg.norm(g)
+
+
+def test_collision_step_converges_to_newtons_law(O, rbc):
+    # M (v1 - v0)/h = F_int(x1) + F_ext (zero at contaminated vertices) + kc (p - x1)
+    mt, T = rbc
+    xn, vn, f = seeded_cell(mt, 53, amp=5.0)
+    rng = np.random.default_rng(54)
+    hit = (rng.uniform(size=mt.nV) < 0.2).astype(np.int32)
+    p = xn + 0.05 * rng.standard_normal(xn.shape)
+    x1, v1 = T.step_cells_col(xn[None], vn[None], f[None], KC, hit[None], p[None], K=40)
+    x1, v1 = x1[0], v1[0]
+    h, m = mt.material.dt, 1.0 / mt.nV
+    _, gint, _ = T.energy(x1, x1, mask=30)
+    fext = f * (1 - hit)[:, None]
+    fcol = KC * (p - x1) * hit[:, None]
+    resid = m * (v1 - vn) / h - (-gint + fext + fcol)
+    assert np.abs(resid).max() < 1e-7 * np.abs(m * (v1 - vn) / h).max()
+    assert np.abs(fcol).max() > 1e-2 * np.abs(m * (v1 - vn) / h).max()
+
+
+def test_pik_without_contact_is_the_plain_step(O, rbc):
+    mt, T = rbc
+    g = I.materialise(I.Group(mt, 2, 55, amp=0.3))
+    g.x0[1] += 50.0
+    cells = [(T, g.x0[c], g.v0[c]) for c in range(2)]
+    out = O.pik_step(cells, [g.f_ext[0], g.f_ext[1]], RK, KC)
+    for c in range(2):
+        x1, v1 = T.step(g.x0[c], g.v0[c], g.f_ext[c])
+        assert np.array_equal(out[c][0], x1) and np.array_equal(out[c][1], v1)
+
+
+def test_collisions_keep_approaching_cells_apart(O):
+    unit, tris = I.icosphere(2)
+    rest = unit * 1.0
+    T = O.OracleType(rest, tris, 1.0, 5.0, 0.05, 10.0, 1e-3)
+    xa, xb = rest.copy(), rest + np.array([2.3, 0.0, 0.0])
+    va, vb = np.tile([20.0, 0, 0], (len(rest), 1)), np.tile([-20.0, 0, 0], (len(rest), 1))
+    zero = np.zeros_like(rest)
+
+    def gap(col):
+        cells = [(T, xa.copy(), va.copy()), (T, xb.copy(), vb.copy())]
+        for _ in range(15):
+            if col:
+                out = O.pik_step(cells, [zero, zero], RK, 5000.0)
+            else:
+                out = [T.step(x, v, zero) for _, x, v in cells]
+            cells = [(T, o[0], o[1]) for o in out]
+        return cells[1][1][:, 0].min() - cells[0][1][:, 0].max()
+
+    assert gap(False) < 0.0          # without collisions the surfaces pass through each other
+    assert gap(True) > 0.1           # with them they stay apart
+
+
+def test_pik_ties_and_kernel_boundary(O):
+    # exact ties go to the lower cell index; a foreign vertex exactly rk away is outside
+    v, t = octahedron()
+    T = O.OracleType(v, t, 1.0, 5.0, 0.05, 10.0, 1e-3)
+    turn = np.array([1.0, -1.0, -1.0])          # B's vertex 4 becomes its lowest point
+    xa = v.copy()
+    xb = v * turn + np.array([0.25, 0.0, 2.25])   # vertex 4 at (0.25, 0, 1.25)
+    xc = v * turn + np.array([-0.25, 0.0, 2.25])  # vertex 4 at (-0.25, 0, 1.25): same distance to A's top
+    (hca, hva, _), (hcb, _, _), (hcc, _, _) = O.pik([(T, xa), (T, xb), (T, xc)], RK)
+    assert hca[4] == 1 and hva[4] == 4
+    assert hcb[4] == 0 and hcc[4] == 0            # B and C tops are exactly rk apart: not each other's
+    xd = v * turn + np.array([0.0, 0.0, 2.0 + RK])  # vertex 4 exactly rk above A's top
+    (hca, _, _), (hcd, _, _) = O.pik([(T, xa), (T, xd)], RK)
+    assert (hca >= 0).sum() == 0 and (hcd >= 0).sum() == 0
