@@ -149,6 +149,49 @@ def with_damping(groups, alpha, beta):
     return groups
 
 
+def oracle_step_sampled(groups, xn, vn, args, K=10):
+    """One FP64 oracle step of sampled cells from the given state (public layout
+    arrays), with the force median and, when --pik-radius is set, the particle-in-
+    kernel search over each sampled cell and the cells whose bounding spheres come
+    within the kernel radius of it (every vertex that can be in its kernels).
+    Returns [(idx, x1)] per group."""
+    from oracle import oracle as O
+    shapes, offs, off = [], [], 0
+    for g in groups:
+        shapes.append((g.n_cells, g.mtype.nV, 3))
+        offs.append(off)
+        off += g.n_cells * g.mtype.nV * 3
+    X = [xn[o:o + np.prod(sh)].reshape(sh) for o, sh in zip(offs, shapes)]
+    V = [vn[o:o + np.prod(sh)].reshape(sh) for o, sh in zip(offs, shapes)]
+    Ts = [O.OracleType.from_mesh_type(g.mtype) for g in groups]
+    out = []
+    if args.pik_radius > 0:
+        cen = np.concatenate([x.mean(axis=1) for x in X])
+        rad = np.concatenate([np.linalg.norm(x - x.mean(axis=1, keepdims=True), axis=2).max(axis=1) for x in X])
+        gid = np.concatenate([np.full(g.n_cells, gi) for gi, g in enumerate(groups)])
+        cid = np.concatenate([np.arange(g.n_cells) for g in groups])
+        base = np.cumsum([0] + [g.n_cells for g in groups])
+    for gi, g in enumerate(groups):
+        idx = np.unique(np.linspace(0, g.n_cells - 1, PARITY_CELLS).astype(int))
+        T = Ts[gi]
+        fs = O.force_median(T, g.f_ext[idx]) if args.force_median else g.f_ext[idx]
+        if args.pik_radius <= 0:
+            xo, _ = T.step_cells(X[gi][idx].copy(), V[gi][idx].copy(), fs, K=K, m=5, threads=os.cpu_count() or 4)
+            out.append((idx, xo))
+            continue
+        xo = np.empty((len(idx), g.mtype.nV, 3))
+        for k, c in enumerate(idx):
+            a = base[gi] + c
+            near = np.flatnonzero(np.linalg.norm(cen - cen[a], axis=1) < rad + rad[a] + args.pik_radius)
+            cells = [(Ts[gid[b]], X[gid[b]][cid[b]]) for b in near]          # global (public) order
+            hc, _, p = O.pik(cells, args.pik_radius)[int(np.flatnonzero(near == a)[0])]
+            x1, _ = T.step_cells_col(X[gi][c][None], V[gi][c][None], fs[k][None], args.collision_k,
+                                     (hc >= 0).astype(np.int32)[None], p[None], K=K, m=5)
+            xo[k] = x1[0]
+        out.append((idx, xo))
+    return out
+
+
 # ---------------------------------------------------------------- reference
 def run_reference(args, workload):
     """The FP64 CPU oracle timed on the host cores (the reference arm)."""
@@ -226,6 +269,8 @@ def main():
     ap.add_argument("--pbd-kappa", type=float, default=0.0, help="PBD velocity damping after each step (0: off)")
     ap.add_argument("--rayleigh-alpha", type=float, default=0.0, help="Rayleigh damping C = alpha M + beta L")
     ap.add_argument("--rayleigh-beta", type=float, default=0.0, help="(the paper's table: alpha 0, beta 0.01)")
+    ap.add_argument("--pik-radius", type=float, default=0.0, help="particle-in-kernel collision kernel radius (0: off)")
+    ap.add_argument("--collision-k", type=float, default=200.0, help="collision stiffness (with --pik-radius)")
     args = ap.parse_args()
     rank, world, local = env_rank()
 
@@ -270,7 +315,7 @@ def main():
 
     def make(prec):
         s = Solver(precision=prec, stream=stream, force_median=args.force_median, u_max=args.u_max,
-                   pbd_kappa=args.pbd_kappa)
+                   pbd_kappa=args.pbd_kappa, pik_radius=args.pik_radius, collision_k=args.collision_k)
         for g in groups:
             s.add_cells(s.create_type(g.mtype), g.x0, g.v0)
         return s
@@ -322,20 +367,26 @@ def main():
         s.step(f_dev)
         s.sync()
         x1 = s.positions()
+        contacts = s.stats()["contacts"]
         errs, off = [], 0
-        for g in groups:
+        for g, (idx, xo) in zip(groups, oracle_step_sampled(groups, xn, vn, args, K)):
             n = g.n_cells * g.mtype.nV * 3
             shape = (g.n_cells, g.mtype.nV, 3)
-            idx = np.unique(np.linspace(0, g.n_cells - 1, PARITY_CELLS).astype(int))
-            T = O.OracleType.from_mesh_type(g.mtype)
-            fs = O.force_median(T, g.f_ext[idx]) if args.force_median else g.f_ext[idx]
-            xo, _ = T.step_cells(xn[off:off + n].reshape(shape)[idx].copy(), vn[off:off + n].reshape(shape)[idx].copy(),
-                                 fs, K=K, m=5, threads=os.cpu_count() or 4)
             errs.append(float(np.linalg.norm(x1[off:off + n].reshape(shape)[idx] - xo, axis=2).max() / g.mtype.radius))
             off += n
         parity = {"rel_pos_err": max(errs), "sampled_cells": PARITY_CELLS * len(groups),
                   "measure": f"one step from the GPU state after {total_steps} steps, GPU vs FP64 oracle",
                   "tolerance": 1e-6 if precision != "fp64" else 1e-10}
+        if args.pik_radius > 0:
+            # contacts make the step map less well conditioned: the oracle against itself
+            # from the same state perturbed by 1e-13 (absolute, random) shows how much
+            rng = np.random.default_rng(0)
+            pert = oracle_step_sampled(groups, xn + 1e-13 * rng.standard_normal(xn.shape), vn, args, K)
+            base = oracle_step_sampled(groups, xn, vn, args, K)
+            parity["contacts_in_step"] = contacts
+            parity["oracle_self_sensitivity"] = max(
+                float(np.linalg.norm(a[1] - b[1], axis=2).max() / g.mtype.radius)
+                for g, a, b in zip(groups, base, pert))
 
     # ---- per-kernel CUDA-event times (same steps, events around every launch)
     s.profile(True)
@@ -383,7 +434,21 @@ def main():
         t64 = max_over_ranks(ea.elapsed_time(eb) / 1e3)
         fp64 = {"value": world * ncells * K * args.fp64_steps / t64, "unit": UNIT, "steps": args.fp64_steps,
                 "ms_per_step": t64 / args.fp64_steps * 1e3}
-        if rank == 0:
+        if rank == 0 and args.pik_radius > 0:
+            # contacts couple the cells: the step map from the FP64 state, sampled cells
+            xn, vn = s64.positions(), s64.velocities()
+            s64.step(f_dev)
+            x = s64.positions()
+            errs, off = [], 0
+            for g, (idx, xo) in zip(groups, oracle_step_sampled(groups, xn, vn, args, K)):
+                n = g.n_cells * g.mtype.nV * 3
+                errs.append(float(np.linalg.norm(x[off:off + n].reshape(g.n_cells, g.mtype.nV, 3)[idx] - xo,
+                                                 axis=2).max() / g.mtype.radius))
+                off += n
+            fp64["rel_pos_err"] = max(errs)
+            fp64["measure"] = f"one step from the FP64 GPU state after {args.fp64_steps} steps, sampled cells"
+            fp64["mixed_over_fp64"] = value / fp64["value"]
+        elif rank == 0:
             from oracle import oracle as O
             x = s64.positions()
             errs, off = [], 0
@@ -451,7 +516,8 @@ def main():
                        "l2": "inputs larger than L2 (state + forces ~1.6 GB), no flush",
                        "parallelism": f"{world} independent ranks" if world > 1 else "1 GPU",
                        "force_median": bool(args.force_median), "u_max": args.u_max, "pbd_kappa": args.pbd_kappa,
-                       "rayleigh_alpha": args.rayleigh_alpha, "rayleigh_beta": args.rayleigh_beta},
+                       "rayleigh_alpha": args.rayleigh_alpha, "rayleigh_beta": args.rayleigh_beta,
+                       "pik_radius": args.pik_radius, "collision_k": args.collision_k if args.pik_radius > 0 else 0.0},
             "clocks": clk, "gpu_launches": launches, "parity": parity, "fp64_gpu": fp64, "e2e": e2e,
             "roofline": roof, "kernels": kernels, "solver": solver}
     if not args.no_cpu:

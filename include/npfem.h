@@ -92,6 +92,16 @@ typedef struct {
                                field (centre-of-mass velocity + omega x r, omega = I^{-1} L) is kept,
                                the rest scaled by 1 - pbd_kappa; paper Sec. 2.1 (kappa_damping),
                                Mueller et al. 2007.  Default 0 (off). */
+    double pik_radius;      /* > 0: particle-in-kernel collisions (paper Sec. 2.2, supplementary PIK
+                               section), kernel radius rk.  At the start of each step every vertex
+                               whose sphere of radius rk holds vertices of other cells takes the
+                               closest one (ties: lower public cell, then vertex index) as its
+                               colliding neighbour j: its external force is dropped for the step and
+                               g gains collision_k/2 |x_i - p_i|^2, p_i = x_i + (rk - s) n_j,
+                               s = (x_i - x_j).n_j, n_j the area-weighted vertex normal of j, all at
+                               the start-of-step positions.  P is unchanged (the term's curvature
+                               enters through the L-BFGS pairs).  Default 0 (off). */
+    double collision_k;     /* stiffness of the collision energy; > 0 when pik_radius > 0 */
 } npfem_options;
 
 /* Material and time step of one mesh type.  Element weights follow the
@@ -121,6 +131,7 @@ typedef struct {
     double max_refine_residual;/* largest final |q - P z|/|q| seen (mixed forms) */
     double energy_sum;         /* sum over cells of g(x_{n+1}) */
     int64_t launches_per_step; /* kernels one npfem_step launches */
+    int64_t contacts;          /* vertices that found a colliding neighbour (pik_radius > 0) */
 } npfem_step_stats;
 
 /* Kernel classes of the per-kernel timing (npfem_profile_read). */
@@ -131,8 +142,9 @@ typedef struct {
 #define NPFEM_K_GEMM_REFINE 4    /* refinement correction applies */
 #define NPFEM_K_RESIDUAL 5       /* FP64 refinement residuals */
 #define NPFEM_K_FALLBACK_APPLY 6 /* P^{-1} grad for non-descent cells */
-#define NPFEM_K_FILTER 7         /* force median filter and velocity cap */
-#define NPFEM_KCLASSES 8
+#define NPFEM_K_FILTER 7         /* force median filter, velocity cap, PBD damping */
+#define NPFEM_K_CONTACT 8        /* particle-in-kernel search and collision targets */
+#define NPFEM_KCLASSES 9
 
 typedef struct {
     double ms[NPFEM_KCLASSES];         /* summed CUDA-event time per class */

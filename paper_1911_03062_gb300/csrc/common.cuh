@@ -17,6 +17,7 @@ struct DevStatus {
     unsigned long long capped;
     unsigned long long fallbacks;
     unsigned long long refine_sweeps;
+    unsigned long long contacts;  // vertices with a foreign vertex in their kernel (PIK)
     unsigned int max_resid_bits; // float bits of the largest final refinement ratio
     unsigned int pad;
     double energy_sum;

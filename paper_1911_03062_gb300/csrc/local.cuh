@@ -404,6 +404,14 @@ __device__ __forceinline__ void volume_pass(const TypeConst<T> &tc, const T *pos
     }
 }
 
+// PIK collision term of one cell: kc[v] (0: no contact) and c = p - y ([3][nVp]);
+// the local step adds kc/2 |x - p|^2 = kc/2 |delta - c|^2.  Null pointers: none.
+template <typename T>
+struct Contact {
+    const T *kc;
+    const T *c;
+};
+
 // -------------------------------------------------------- the local step
 // dt: this thread's elements of delta (x = y_rel + delta); gr receives the
 // gradient.  After the final reduction thread 0 calls done(g, allow) with
@@ -411,8 +419,8 @@ __device__ __forceinline__ void volume_pass(const TypeConst<T> &tc, const T *pos
 // (8 u sum_i w_i |A_i x - p_i| |A_i x| + u * inertia); done writes what the
 // caller needs into S.bc before the closing barrier.
 template <typename T, int EPT, typename Done>
-__device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, const T (&dt)[EPT], T (&gr)[EPT],
-                           const Smem<T> &S, int stash_T, Done &&done) {
+__device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, const Contact<T> &ct,
+                           const T (&dt)[EPT], T (&gr)[EPT], const Smem<T> &S, int stash_T, Done &&done) {
     const int B = blockDim.x, tid = threadIdx.x;
     const int nVp = tc.nVp, nV = tc.nV, n3 = 3 * nVp;
     T *pos = S.pos, *gsh = S.gsh, *gva = S.gva, *stash = S.stash;
@@ -436,6 +444,20 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                     xv[i] = yr4[i] + dj;
                     gv[i] = mh4[i] * dj;
                     T q = T(0.5) * mh4[i] * dj * dj;
+                    en += q;
+                    al += q;
+                }
+            }
+            if (ct.kc) {                                // collision term (contact vertices only)
+                T kc4[4], c4[4];
+                ld4(ct.kc + v0, kc4);
+                ld4(ct.c + e0, c4);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (v0 + i >= nV || kc4[i] == T(0)) continue;
+                    const T r = dt[4 * g4 + i] - c4[i];
+                    gv[i] += kc4[i] * r;
+                    const T q = T(0.5) * kc4[i] * r * r;
                     en += q;
                     al += q;
                 }

@@ -89,6 +89,8 @@ struct MeshTypeImpl {
     void *yrel = nullptr, *delta = nullptr, *grad = nullptr, *q = nullptr, *z = nullptr;
     void *S = nullptr, *Y = nullptr, *rlo = nullptr;
     void *zp = nullptr;                          // Rayleigh-damped type: Mt^{-1}(M v_n + h F_ext), kept for the step
+    void *kcol = nullptr, *ccol = nullptr;       // PIK: [cell][nVp] stiffness (0: no contact), [cell][3][nVp] p - y
+    int *ring_bc = nullptr;                      // vertex -> triangle incidences: the other two vertices
     __nv_bfloat16 *rlo_lo = nullptr;             // split corrections: BF16 low part of r
     __nv_bfloat16 *q16 = nullptr;
     double *origin = nullptr, *rho = nullptr, *alpha = nullptr, *M = nullptr, *g = nullptr, *allow = nullptr;
@@ -110,6 +112,13 @@ struct npfem_ctx {
     double **d_fslot = nullptr;          // device slot: base of the forces read by the step
     double *d_stage = nullptr;           // staging for get/set (public layout)
     double *d_ffilt = nullptr;           // median-filtered forces (public layout), force_median only
+    // particle-in-kernel search (pik_radius > 0): buckets, binned vertices, result per flat vertex
+    unsigned *d_pik_cnt = nullptr, *d_pik_start = nullptr, *d_pik_fill = nullptr, *d_pik_key = nullptr;
+    unsigned *d_pik_bsum = nullptr;
+    PikEntry *d_pik_ent = nullptr;
+    double *d_pik_pos = nullptr;         // FP64 positions of the binned vertices [pos][3]
+    int *d_pik_hit = nullptr;
+    long long pik_n = 0, pik_h = 0;
     DevStatus *d_st = nullptr;
     DevStatus *h_st = nullptr;           // pinned
     int *d_any = nullptr;
@@ -266,6 +275,8 @@ IterArgs<T> make_args(npfem_ctx *ctx, MeshTypeImpl *t) {
     else a.tc = t->tc32;
     a.ncells = t->ncells;
     a.zpred = (const T *)t->zp;
+    a.kcol = (const T *)t->kcol;
+    a.ccol = (T *)t->ccol;
     a.m = ctx->opt.history;
     a.max_bt = ctx->opt.max_backtracks;
     a.use_allow = mixed(ctx) ? 1 : 0;
@@ -605,6 +616,99 @@ void fallback_apply(npfem_ctx *ctx, MeshTypeImpl *t) {
 
 __global__ void k_set_ptr(double **slot, const double *p) { *slot = const_cast<double *>(p); }
 
+// Particle-in-kernel buffers for the current cells: buckets (a power of two >= 2x the
+// vertices), binned vertices and the per-vertex result.
+void pik_alloc(npfem_ctx *ctx) {
+    long long n = 0;
+    for (auto *t : ctx->types) n += (long long)t->ncells * t->nV;
+    if (n > (1ll << 30)) fail(ctx, NPFEM_EINVAL, "%lld vertices exceed the collision search's 2^30", n);
+    long long h = 1024;
+    while (h < 2 * n) h <<= 1;
+    void **bufs[] = {(void **)&ctx->d_pik_cnt, (void **)&ctx->d_pik_start, (void **)&ctx->d_pik_fill,
+                     (void **)&ctx->d_pik_key, (void **)&ctx->d_pik_bsum, (void **)&ctx->d_pik_ent,
+                     (void **)&ctx->d_pik_pos, (void **)&ctx->d_pik_hit};
+    for (void **b : bufs) dfree(*b);
+    const long long nb = (h + 1 + SCAN_B * SCAN_ITEMS - 1) / (SCAN_B * SCAN_ITEMS);
+    ctx->d_pik_cnt = dalloc<unsigned>(ctx, h + 1);
+    ctx->d_pik_start = dalloc<unsigned>(ctx, h + 1);
+    ctx->d_pik_fill = dalloc<unsigned>(ctx, h);
+    ctx->d_pik_key = dalloc<unsigned>(ctx, std::max(1ll, n));
+    ctx->d_pik_bsum = dalloc<unsigned>(ctx, nb);
+    ctx->d_pik_ent = dalloc<PikEntry>(ctx, std::max(1ll, n));
+    ctx->d_pik_pos = dalloc<double>(ctx, 3 * std::max(1ll, n));
+    ctx->d_pik_hit = dalloc<int>(ctx, std::max(1ll, n));
+    ctx->pik_n = n;
+    ctx->pik_h = h;
+}
+
+// The collision search and targets of one step (positions at the start of the step):
+// bin, scan, scatter, query, targets; see contact.cuh.
+void pik_search(npfem_ctx *ctx) {
+    PikTypes pt{};
+    std::vector<MeshTypeImpl *> tl;
+    int vb = 0, cb = 0;
+    for (auto *t : ctx->types) {
+        if (!t->ncells) continue;
+        if (pt.ntypes == PIK_MAX_TYPES) fail(ctx, NPFEM_EINVAL, "collision search takes at most %d mesh types", PIK_MAX_TYPES);
+        PikType &P = pt.t[pt.ntypes++];
+        P.xn = t->xn;
+        P.pub_off = t->pub_off;
+        P.vpub = t->vpub;
+        P.ring_ptr = mixed(ctx) ? t->tc32.vt_ptr : t->tc64.vt_ptr;
+        P.ring_bc = t->ring_bc;
+        P.nV = t->nV;
+        P.nVp = t->nVp;
+        P.ncells = t->ncells;
+        P.vbase = vb;
+        P.cbase = cb;
+        vb += t->ncells * t->nV;
+        cb += t->ncells;
+        tl.push_back(t);
+    }
+    if (vb != ctx->pik_n) fail(ctx, NPFEM_ESTATE, "collision search buffers out of date");
+    const double rk = ctx->opt.pik_radius;
+    int kb = 0;
+    while ((1ll << kb) < ctx->pik_h) ++kb;
+    const int bx = (kb + 2) / 3, by = (kb - bx + 1) / 2;
+    const PikGrid g{1.0 / (rk * (1.0 + 1e-9)), bx, by, (unsigned)(ctx->pik_h - 1)};
+    const long long H = ctx->pik_h, N = ctx->pik_n;
+    CK(cudaMemsetAsync(ctx->d_pik_cnt, 0, (H + 1) * sizeof(unsigned), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_pik_fill, 0, H * sizeof(unsigned), ctx->stream));
+    auto launch = [&](auto &&fn) {
+        prof_begin(ctx, NPFEM_K_CONTACT);
+        fn();
+        CK(cudaGetLastError());
+        prof_end(ctx);
+    };
+    for (int ti = 0; ti < pt.ntypes; ++ti) {
+        const long long n = (long long)pt.t[ti].ncells * pt.t[ti].nV;
+        launch([&] { k_pik_bin<<<grid_for(n, 256, 16 * ctx->nsm), 256, 0, ctx->stream>>>(pt, ti, g, ctx->d_pik_cnt,
+                                                                                      ctx->d_pik_key); });
+    }
+    const int nb = (int)((H + 1 + SCAN_B * SCAN_ITEMS - 1) / (SCAN_B * SCAN_ITEMS));
+    launch([&] { k_scan_blocks<<<nb, SCAN_B, 0, ctx->stream>>>(ctx->d_pik_cnt, ctx->d_pik_start, ctx->d_pik_bsum, H + 1); });
+    launch([&] { k_scan_sums<<<1, SCAN_B, 0, ctx->stream>>>(ctx->d_pik_bsum, nb); });
+    launch([&] { k_scan_add<<<nb, SCAN_B, 0, ctx->stream>>>(ctx->d_pik_start, ctx->d_pik_bsum, H + 1); });
+    for (int ti = 0; ti < pt.ntypes; ++ti) {
+        const long long n = (long long)pt.t[ti].ncells * pt.t[ti].nV;
+        launch([&] { k_pik_scatter<<<grid_for(n, 256, 16 * ctx->nsm), 256, 0, ctx->stream>>>(
+                         pt, ti, ctx->d_pik_key, ctx->d_pik_start, ctx->d_pik_fill, ctx->d_pik_ent, ctx->d_pik_pos); });
+    }
+    if (N > 0)
+        launch([&] { k_pik_query<<<grid_for(N, 256, 16 * ctx->nsm), 256, 0, ctx->stream>>>(
+                         ctx->d_pik_ent, ctx->d_pik_pos, ctx->d_pik_start, N, g, rk, ctx->d_pik_hit, ctx->d_st); });
+    for (int ti = 0; ti < pt.ntypes; ++ti) {
+        MeshTypeImpl *t = tl[ti];
+        const long long n = (long long)t->ncells * t->nVp;
+        if (mixed(ctx))
+            launch([&] { k_pik_target<float><<<grid_for(n, 256, 16 * ctx->nsm), 256, 0, ctx->stream>>>(
+                             pt, ti, ctx->d_pik_hit, rk, ctx->opt.collision_k, (float *)t->kcol, (float *)t->ccol); });
+        else
+            launch([&] { k_pik_target<double><<<grid_for(n, 256, 16 * ctx->nsm), 256, 0, ctx->stream>>>(
+                             pt, ti, ctx->d_pik_hit, rk, ctx->opt.collision_k, (double *)t->kcol, (double *)t->ccol); });
+    }
+}
+
 // Rayleigh-damped types: zp = Mt^{-1}(M v_n + h F_ext) for every cell, read by the
 // predictor (y = x_n + h zp) and again where the last iteration re-forms y in FP64.
 // FP64 form: SIMT FP64 apply; mixed forms: one grouped tensor-core apply of operands
@@ -620,11 +724,12 @@ void damped_predictor_rhs(npfem_ctx *ctx) {
             k_damp_rhs<float><<<grid, 256, 0, ctx->stream>>>(t->ncells, t->nV, t->nVp, t->mass, t->vn, ctx->d_fslot,
                                                              t->pub_off, t->vpub, t->h, (float *)t->q,
                                                              bf16(ctx) ? t->q16 : nullptr, t->rlo_lo,
-                                                             bf16(ctx) ? nullptr : (float *)t->rlo);
+                                                             bf16(ctx) ? nullptr : (float *)t->rlo,
+                                                             (const float *)t->kcol);
         else
             k_damp_rhs<double><<<grid, 256, 0, ctx->stream>>>(t->ncells, t->nV, t->nVp, t->mass, t->vn, ctx->d_fslot,
                                                               t->pub_off, t->vpub, t->h, (double *)t->q, nullptr,
-                                                              nullptr, nullptr);
+                                                              nullptr, nullptr, (const double *)t->kcol);
         CK(cudaGetLastError());
         prof_end(ctx);
         if (!mixed(ctx)) {
@@ -667,6 +772,7 @@ void enqueue_step(npfem_ctx *ctx) {
         CK(cudaGetLastError());
         prof_end(ctx);
     }
+    if (ctx->opt.pik_radius > 0) pik_search(ctx);
     damped_predictor_rhs(ctx);
     for (auto *t : ctx->types)
         if (t->ncells) run_predict(ctx, t);
@@ -981,11 +1087,13 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
     c.hc = upload(ctx, cvt<T>(H.hc), t->owned);
     c.hrest = upload(ctx, cvt<T>(H.hrest), t->owned);
     std::vector<TriInc<T>> vt(H.vt_inc.size());
+    std::vector<int> ring(H.vt_inc.size());
     for (size_t k = 0; k < vt.size(); ++k) {
         const int tt = H.vt_inc[k] >> 2, corner = H.vt_inc[k] & 3;
         const int vb = H.tri[3 * tt + (corner + 1) % 3], vc = H.tri[3 * tt + (corner + 2) % 3];
         vt[k].t = tt;
         vt[k].bc = vb | (vc << 16);
+        ring[k] = vt[k].bc;
         vt[k].g0 = (T)H.vt_g[2 * k];
         vt[k].g1 = (T)H.vt_g[2 * k + 1];
     }
@@ -1030,6 +1138,7 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
     }
     c.vt_ptr = upload(ctx, H.vt_ptr, t->owned);
     c.vt = upload(ctx, vt, t->owned);
+    t->ring_bc = upload(ctx, ring, t->owned);
     c.vh_ptr = upload(ctx, H.vh_ptr, t->owned);
     c.vh = upload(ctx, vh, t->owned);
     c.mh2 = upload(ctx, cvt<T>(mh2), t->owned);
@@ -1194,7 +1303,7 @@ void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
 
 void free_cells(MeshTypeImpl *t) {
     void **bufs[] = {(void **)&t->pub_off, (void **)&t->xn, (void **)&t->vn, &t->yrel, &t->delta, &t->grad, &t->q,
-                     &t->z, &t->zp, &t->S, &t->Y, &t->rlo, (void **)&t->rlo_lo, (void **)&t->q16, (void **)&t->origin, (void **)&t->rho,
+                     &t->z, &t->zp, &t->kcol, &t->ccol, &t->S, &t->Y, &t->rlo, (void **)&t->rlo_lo, (void **)&t->q16, (void **)&t->origin, (void **)&t->rho,
                      (void **)&t->alpha, (void **)&t->M, (void **)&t->g, (void **)&t->allow, (void **)&t->hcount,
                      (void **)&t->hhead, (void **)&t->conv, (void **)&t->fb_list, (void **)&t->fb_count};
     for (void **b : bufs) dfree(*b);
@@ -1210,6 +1319,12 @@ void alloc_cells(npfem_ctx *ctx, MeshTypeImpl *t, int cap) {
     auto vec = [&](void *&p) { p = dalloc<unsigned char>(ctx, cap * n3 * es); };
     vec(t->yrel); vec(t->delta); vec(t->grad); vec(t->q); vec(t->z);
     if (t->damped) vec(t->zp);
+    if (ctx->opt.pik_radius > 0) {
+        vec(t->ccol);
+        t->kcol = dalloc<unsigned char>(ctx, cap * (size_t)t->nVp * es);
+        CK(cudaMemsetAsync(t->kcol, 0, cap * (size_t)t->nVp * es, ctx->stream));
+        CK(cudaMemsetAsync(t->ccol, 0, cap * n3 * es, ctx->stream));
+    }
     t->S = dalloc<unsigned char>(ctx, cap * n3 * es * m);
     t->Y = dalloc<unsigned char>(ctx, cap * n3 * es * m);
     t->q16 = bf16(ctx) ? dalloc<__nv_bfloat16>(ctx, cap * n3) : nullptr;
@@ -1300,7 +1415,8 @@ int npfem_create(const npfem_options *opt, npfem_ctx **out) {
         if (o.precision < 0 || o.precision > 2 || o.iters < 1 || o.history < 0 || o.history > NPFEM_MAX_HISTORY ||
             o.max_backtracks < 0 || !(o.armijo_c1 > 0 && o.armijo_c1 < 1) || o.refine_max < 0 || !(o.refine_tol > 0) ||
             o.force_median < 0 || o.force_median > 1 || !(o.u_max >= 0) || !std::isfinite(o.u_max) ||
-            !(o.pbd_kappa >= 0 && o.pbd_kappa <= 1))
+            !(o.pbd_kappa >= 0 && o.pbd_kappa <= 1) || !(o.pik_radius >= 0) || !std::isfinite(o.pik_radius) ||
+            (o.pik_radius > 0 && !(o.collision_k > 0 && std::isfinite(o.collision_k))))
             fail(ctx, NPFEM_EINVAL, "invalid option value");
         CK(cudaSetDevice(o.device));
         ctx->device = o.device;
@@ -1343,7 +1459,9 @@ void npfem_destroy(npfem_ctx *ctx) {
         for (void *p : t->owned) cudaFree(p);
         delete t;
     }
-    void *bufs[] = {ctx->d_f, ctx->d_fslot, ctx->d_stage, ctx->d_st, ctx->d_any, ctx->d_ffilt};
+    void *bufs[] = {ctx->d_f, ctx->d_fslot, ctx->d_stage, ctx->d_st, ctx->d_any, ctx->d_ffilt,
+                    ctx->d_pik_cnt, ctx->d_pik_start, ctx->d_pik_fill, ctx->d_pik_key, ctx->d_pik_bsum,
+                    ctx->d_pik_ent, ctx->d_pik_pos, ctx->d_pik_hit};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
@@ -1602,6 +1720,7 @@ int npfem_add_cells(npfem_ctx *ctx, int type_id, int n_cells, const double *x0, 
         ctx->d_f = dalloc<double>(ctx, ctx->ndofs);
         ctx->d_stage = dalloc<double>(ctx, ctx->ndofs);
         if (ctx->opt.force_median) ctx->d_ffilt = dalloc<double>(ctx, ctx->ndofs);
+        if (ctx->opt.pik_radius > 0) pik_alloc(ctx);
         invalidate_graph(ctx);
     });
 }
@@ -1718,6 +1837,7 @@ int npfem_stats(npfem_ctx *ctx, npfem_step_stats *out) {
         out->max_refine_residual = r;
         out->energy_sum = s.energy_sum;
         out->launches_per_step = ctx->launches_per_step;
+        out->contacts = (int64_t)s.contacts;
     });
 }
 

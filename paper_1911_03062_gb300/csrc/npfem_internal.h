@@ -9,3 +9,4 @@
 #include "gemm_grouped.cuh"
 #include "residual_ell.cuh"
 #include "filters.cuh"
+#include "contact.cuh"

@@ -27,6 +27,8 @@ struct IterArgs {
     const int *vpub;              // [nV] the caller's index of internal vertex v
     const double *minv;           // [nV] 1 / m_v
     const T *zpred;               // Rayleigh-damped type: Mt^{-1}(M v_n + h F_ext) per cell (SoA), else null
+    const T *kcol;                // PIK collisions: [cell][nVp] stiffness (0: no contact), else null
+    T *ccol;                      // PIK: [cell][3][nVp] push p - x_n, turned into p - y by k_predict
     T *yrel;                      // y - origin
     double *origin;               // [cell][3]
     T *delta, *grad, *q, *z;
@@ -113,12 +115,15 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
             continue;
         }
         ld4(a.vn + base + e0, vv);
+        T kc4[4] = {T(0), T(0), T(0), T(0)};
+        if (a.kcol) ld4(a.kcol + (long long)cell * nVp + v0, kc4);   // contact: the fluid force is dropped
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int v = v0 + i;
             if (v >= nV) continue;
             xo[4 * g + i] = xv[i];
-            y[4 * g + i] = xv[i] + a.h * vv[i] + a.h * a.h * a.minv[v] * f[3 * a.vpub[v] + c];
+            const double fv = kc4[i] != T(0) ? 0.0 : f[3 * a.vpub[v] + c];
+            y[4 * g + i] = xv[i] + a.h * vv[i] + a.h * a.h * a.minv[v] * fv;
         }
     }
 }
@@ -167,7 +172,7 @@ template <typename T>
 __global__ void k_damp_rhs(int ncells, int nV, int nVp, const double *__restrict__ mass, const double *__restrict__ vn,
                            const double *const *fptr, const long long *__restrict__ pub_off,
                            const int *__restrict__ vpub, double h, T *__restrict__ q, __nv_bfloat16 *__restrict__ hi,
-                           __nv_bfloat16 *__restrict__ lo, float *__restrict__ lo32) {
+                           __nv_bfloat16 *__restrict__ lo, float *__restrict__ lo32, const T *__restrict__ kcol) {
     const long long n3 = 3ll * nVp, total = (long long)ncells * n3;
     const double *f = *fptr;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -175,7 +180,10 @@ __global__ void k_damp_rhs(int ncells, int nV, int nVp, const double *__restrict
         const long long cell = i / n3;
         const int e = (int)(i - cell * n3), c = e / nVp, v = e - c * nVp;
         double b = 0.0;
-        if (v < nV) b = mass[v] * vn[i] + h * f[pub_off[cell] + 3 * vpub[v] + c];
+        if (v < nV) {
+            const bool contact = kcol && kcol[cell * nVp + v] != T(0);   // PIK: fluid force dropped
+            b = mass[v] * vn[i] + (contact ? 0.0 : h * f[pub_off[cell] + 3 * vpub[v] + c]);
+        }
         q[i] = (T)b;
         if (lo32) {
             const float bh = tf32_hi((float)b);
@@ -207,6 +215,18 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         }
         double y[EPT], xo[EPT];
         predictor64<T, EPT>(a, cell, y, xo);
+        if (a.ccol) {
+            // collision targets relative to y: p - y = (p - x_n) - (y - x_n)
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                const int e = elem_of(j);
+                int v;
+                if (e >= n3) continue;
+                elem_cv(e, nVp, v);
+                if (v >= a.tc.nV) continue;
+                a.ccol[base + e] = T((double)a.ccol[base + e] - (y[j] - xo[j]));
+            }
+        }
         // centroid of y, per component
         Acc<double> s[3];
         s[0].zero(); s[1].zero(); s[2].zero();
@@ -241,7 +261,8 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         store_vec<T, EPT>(a.yrel + base, yr, n3);
         store_vec<T, EPT>(a.delta + base, dl, n3);
         __syncthreads();
-        local_eval<T, EPT>(a.tc, a.yrel + base, dl, gr, S, a.stash_T, [&](double g, double allow) {
+        const Contact<T> ct{a.kcol ? a.kcol + (long long)cell * nVp : nullptr, a.ccol ? a.ccol + base : nullptr};
+        local_eval<T, EPT>(a.tc, a.yrel + base, ct, dl, gr, S, a.stash_T, [&](double g, double allow) {
             a.g[cell] = g;
             a.allow[cell] = allow;
             a.hcount[cell] = 0;
@@ -374,7 +395,8 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         for (;;) {
 #pragma unroll
             for (int j = 0; j < EPT; ++j) dt[j] = dl[j] + alpha * d[j];
-            local_eval<T, EPT>(a.tc, a.yrel + base, dt, gt, S, a.stash_T, [&](double g, double allow) {
+            const Contact<T> ct{a.kcol ? a.kcol + (long long)cell * nVp : nullptr, a.ccol ? a.ccol + base : nullptr};
+            local_eval<T, EPT>(a.tc, a.yrel + base, ct, dt, gt, S, a.stash_T, [&](double g, double allow) {
                 const double al = S.bc->d[2], gd = S.bc->d[1];
                 const double slack = a.use_allow ? (S.bc->d[6] + allow) : 0.0;
                 S.bc->d[3] = g;

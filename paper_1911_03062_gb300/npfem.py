@@ -40,7 +40,7 @@ class Options(C.Structure):
                 ("refine_max", C.c_int), ("use_graph", C.c_int), ("device", C.c_int),
                 ("cuda_stream", C.c_void_p), ("autotune_cache", C.c_char_p), ("residual_fp64", C.c_int),
                 ("refine_split", C.c_int), ("force_median", C.c_int), ("u_max", C.c_double),
-                ("pbd_kappa", C.c_double)]
+                ("pbd_kappa", C.c_double), ("pik_radius", C.c_double), ("collision_k", C.c_double)]
 
 
 class Material(C.Structure):
@@ -53,14 +53,15 @@ class StepStats(C.Structure):
     _fields_ = [("cell_iterations", C.c_int64), ("backtracks", C.c_int64),
                 ("capped_searches", C.c_int64), ("fallbacks", C.c_int64),
                 ("refine_sweeps", C.c_int64), ("max_refine_residual", C.c_double),
-                ("energy_sum", C.c_double), ("launches_per_step", C.c_int64)]
+                ("energy_sum", C.c_double), ("launches_per_step", C.c_int64), ("contacts", C.c_int64)]
 
 
-KCLASSES = ["predict", "iterate", "fallback", "gemm", "gemm_refine", "residual", "fallback_apply", "filter"]
+KCLASSES = ["predict", "iterate", "fallback", "gemm", "gemm_refine", "residual", "fallback_apply", "filter",
+            "contact"]
 
 
 class KernelTimes(C.Structure):
-    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_int64 * 8)]
+    _fields_ = [("ms", C.c_double * 9), ("launches", C.c_int64 * 9)]
 
 
 _lib = None
@@ -136,7 +137,8 @@ class Solver:
 
     def __init__(self, precision="fp64", iters=10, history=5, armijo_c1=1e-4, max_backtracks=8,
                  refine_tol=1e-6, refine_max=3, use_graph=True, device=0, stream=None, residual_fp64=False,
-                 refine_split=True, force_median=False, u_max=0.0, pbd_kappa=0.0):
+                 refine_split=True, force_median=False, u_max=0.0, pbd_kappa=0.0, pik_radius=0.0,
+                 collision_k=0.0):
         self._L = load()
         o = default_options()
         o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -148,6 +150,8 @@ class Solver:
         o.force_median = int(bool(force_median))
         o.u_max = float(u_max)
         o.pbd_kappa = float(pbd_kappa)
+        o.pik_radius = float(pik_radius)
+        o.collision_k = float(collision_k)
         if stream is not None:
             o.cuda_stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         self.precision = o.precision
