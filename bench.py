@@ -36,11 +36,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) per k_iterate launch on rbc50k_plt5k in the BF16 form,
-# averaged over the RBC and platelet launches of one step, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, one pass, launches of one timed step).
+# Measured DRAM traffic of k_iterate on rbc50k_plt5k (BF16 form), bytes per launch:
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture (one pass) of the
+# 40 k_iterate launches of one step, averaged over the 20 launches that process all
+# cells (the fallback-list launches, ~0.1 MB each, excluded like their times).
 # Set to None whenever k_iterate changes until it is captured again.
-ITERATE_TRAFFIC = 2.1418e9
+ITERATE_TRAFFIC = 3.508e9
 PARITY_CELLS = 16        # cells per mesh type compared with the oracle (evenly spaced)
 METRIC = "cell-iterations/sec at 50k cells, mixed vs FP64 GPU at ≤1e-6 rel pos error"
 UNIT = "cell-iterations/s"
