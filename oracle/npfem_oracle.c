@@ -25,6 +25,8 @@
  *   contact : optional particle-in-kernel (PIK) collisions: brute-force search
  *             of the closest foreign vertex inside the kernel, its fluid force
  *             dropped, kc/2 |x - p|^2 toward a plane projection p (fixed per step).
+ *   IBM     : multi-direct forcing with Peskin's four-point kernel (the producer
+ *             of F_ext), brute force over each point's 4 x 4 x 4 lattice stencil.
  * The global solves use this file's own sparse (RCM + envelope) Cholesky.
  *
  * Public layout: positions, velocities, forces are [nV][3] doubles per cell.
@@ -1128,5 +1130,129 @@ int orc_pik(int ncells, const int *nV, const double *const *x, const double *con
             }
         }
     }
+    return ORC_OK;
+}
+
+/* --------------------------------------------- immersed boundary (IBM) forces
+ * Multi-direct forcing of the supplementary IBM section (after Wang et al. and
+ * Ota et al.) on a lattice of nx x ny x nz nodes at x0 + (i, j, k) dx, fluid
+ * velocity u [3][nz][ny][nx].  Interpolation u(X) = sum_x u(x) W(x - X) dx^3,
+ * W(r) = phi4(rx/dx) phi4(ry/dx) phi4(rz/dx) / dx^3.  Readings: a Lagrangian
+ * point stands for the shell volume A_k dx, so the spread force density is
+ * F(x) = sum_k f_k W(x - X_k) dx; nodes outside the lattice are left out.
+ *   f_0 = (U - u*(X)) A / dt
+ *   cycle c = 1..C: F = spread(f_{c-1}); u_c = u* + F dt at the nodes;
+ *                   f_c = f_{c-1} + (U - u_c(X)) A / dt
+ *   outputs: f_C per point ([N][3]) and F_imm = spread(f_C) ([3][nz][ny][nx]).
+ * Peskin's four-point function:
+ *   phi4(r) = (3 - 2|r| + sqrt(1 + 4|r| - 4 r^2)) / 8,   |r| <= 1
+ *           = (5 - 2|r| - sqrt(-7 + 12|r| - 4 r^2)) / 8, 1 <= |r| <= 2,  0 beyond. */
+double orc_phi4(double r) {
+    double a = fabs(r);
+    if (a <= 1.0) return (3.0 - 2.0*a + sqrt(1.0 + 4.0*a - 4.0*a*a)) / 8.0;
+    if (a <= 2.0) return (5.0 - 2.0*a - sqrt(-7.0 + 12.0*a - 4.0*a*a)) / 8.0;
+    return 0.0;
+}
+
+/* Vertex areas: a third of the areas of the incident triangles.  x: [nV][3]. */
+void orc_vertex_areas(const orc_type *T, const double *x, double *a) {
+    memset(a, 0, sizeof(double)*T->nV);
+    for (int t = 0; t < T->nT; ++t) {
+        const int *v = T->tri + 3*t;
+        double e1[3], e2[3], cr[3];
+        sub3(x + 3*v[1], x + 3*v[0], e1);
+        sub3(x + 3*v[2], x + 3*v[0], e2);
+        cross3(e1, e2, cr);
+        double ar = 0.5*sqrt(dot3(cr, cr));
+        for (int k = 0; k < 3; ++k) a[v[k]] += ar / 3.0;
+    }
+}
+
+typedef struct { int nx, ny, nz; double dx, x0, y0, z0; } orc_lattice;
+
+/* the 4 x 4 x 4 stencil of point X: first node index per axis and weights phi4 */
+static void ibm_stencil(const orc_lattice *L, const double *X, int first[3], double w[3][4]) {
+    const double o[3] = {L->x0, L->y0, L->z0};
+    for (int d = 0; d < 3; ++d) {
+        double s = (X[d] - o[d]) / L->dx;
+        int i0 = (int)floor(s) - 1;
+        first[d] = i0;
+        for (int j = 0; j < 4; ++j) w[d][j] = orc_phi4(s - (double)(i0 + j));
+    }
+}
+
+static void ibm_interp(const orc_lattice *L, const double *u, const double *F, double dt, const double *X,
+                       double out[3]) {
+    int f[3];
+    double w[3][4];
+    long nn = (long)L->nx*L->ny*L->nz;
+    ibm_stencil(L, X, f, w);
+    out[0] = out[1] = out[2] = 0;
+    for (int k = 0; k < 4; ++k) {
+        int iz = f[2] + k;
+        if (iz < 0 || iz >= L->nz) continue;
+        for (int j = 0; j < 4; ++j) {
+            int iy = f[1] + j;
+            if (iy < 0 || iy >= L->ny) continue;
+            for (int i = 0; i < 4; ++i) {
+                int ix = f[0] + i;
+                if (ix < 0 || ix >= L->nx) continue;
+                long n = ((long)iz*L->ny + iy)*L->nx + ix;
+                double wt = w[0][i]*w[1][j]*w[2][k];
+                for (int c = 0; c < 3; ++c) {
+                    double uv = u[c*nn + n];
+                    if (F) uv += F[c*nn + n]*dt;
+                    out[c] += uv*wt;
+                }
+            }
+        }
+    }
+}
+
+static void ibm_spread(const orc_lattice *L, int N, const double *X, const double *f, double *F) {
+    long nn = (long)L->nx*L->ny*L->nz;
+    double sc = 1.0 / (L->dx*L->dx);           /* W dx = phi phi phi / dx^2 */
+    memset(F, 0, sizeof(double)*3*nn);
+    for (int p = 0; p < N; ++p) {
+        int fi[3];
+        double w[3][4];
+        ibm_stencil(L, X + 3*p, fi, w);
+        for (int k = 0; k < 4; ++k) {
+            int iz = fi[2] + k;
+            if (iz < 0 || iz >= L->nz) continue;
+            for (int j = 0; j < 4; ++j) {
+                int iy = fi[1] + j;
+                if (iy < 0 || iy >= L->ny) continue;
+                for (int i = 0; i < 4; ++i) {
+                    int ix = fi[0] + i;
+                    if (ix < 0 || ix >= L->nx) continue;
+                    long n = ((long)iz*L->ny + iy)*L->nx + ix;
+                    double wt = w[0][i]*w[1][j]*w[2][k]*sc;
+                    for (int c = 0; c < 3; ++c) F[c*nn + n] += f[3*p + c]*wt;
+                }
+            }
+        }
+    }
+}
+
+/* N Lagrangian points X, U ([N][3]), areas A ([N]); see the block comment above. */
+int orc_ibm(int N, const double *X, const double *U, const double *A, int nx, int ny, int nz, double dx,
+            double x0, double y0, double z0, const double *u, double dt, int cycles, double *f, double *Fimm) {
+    if (N < 0 || nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dt > 0) || cycles < 0) return ORC_EINVAL;
+    orc_lattice L = {nx, ny, nz, dx, x0, y0, z0};
+    for (int p = 0; p < N; ++p) {
+        double ui[3];
+        ibm_interp(&L, u, NULL, dt, X + 3*p, ui);
+        for (int c = 0; c < 3; ++c) f[3*p + c] = (U[3*p + c] - ui[c]) * A[p] / dt;
+    }
+    for (int cyc = 0; cyc < cycles; ++cyc) {
+        ibm_spread(&L, N, X, f, Fimm);
+        for (int p = 0; p < N; ++p) {
+            double ui[3];
+            ibm_interp(&L, u, Fimm, dt, X + 3*p, ui);
+            for (int c = 0; c < 3; ++c) f[3*p + c] += (U[3*p + c] - ui[c]) * A[p] / dt;
+        }
+    }
+    ibm_spread(&L, N, X, f, Fimm);
     return ORC_OK;
 }

@@ -84,6 +84,12 @@ def lib():
             L.orc_step_cells_col.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, C.c_int, C.c_double,
                                              C.c_int, C.c_double, vp, vp, vp, vp]
             L.orc_step_cells_col.restype = C.c_int
+            L.orc_phi4.argtypes = [C.c_double]
+            L.orc_phi4.restype = C.c_double
+            L.orc_vertex_areas.argtypes = [vp, dp, dp]
+            L.orc_ibm.argtypes = [C.c_int, dp, dp, dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                  C.c_double, C.c_double, dp, C.c_double, C.c_int, dp, dp]
+            L.orc_ibm.restype = C.c_int
             _lib = L
     return _lib
 
@@ -182,6 +188,12 @@ class OracleType:
         n = np.empty_like(x)
         lib().orc_vertex_normals(self._h, x, n)
         return n
+
+    def vertex_areas(self, x):
+        """A third of the incident triangles' areas per vertex ([nV])."""
+        a = np.empty(self.nV)
+        lib().orc_vertex_areas(self._h, _c(x).reshape(self.nV, 3), a)
+        return a
 
     def volume(self, p):
         return lib().orc_volume(self._h, _c(p).reshape(self.nV, 3))
@@ -338,3 +350,24 @@ def pik_step(cells, f, rk, kc, K=10, m=5):
                                   K=K, m=m)
         out.append((xo[0], vo[0]))
     return out
+
+
+def phi4(r):
+    """Peskin's four-point kernel function."""
+    return lib().orc_phi4(float(r))
+
+
+def ibm(X, U, A, u, origin, dx, dt, cycles):
+    """Multi-direct forcing (supplementary IBM section): Lagrangian points X, U [N, 3],
+    areas A [N]; fluid velocity u [3, nz, ny, nx] on nodes origin + (i, j, k) dx.
+    Returns (f [N, 3], F_imm [3, nz, ny, nx])."""
+    X, U, A = _c(X).reshape(-1, 3), _c(U).reshape(-1, 3), _c(A).ravel()
+    u = _c(u)
+    _, nz, ny, nx = u.shape
+    f = np.empty_like(X)
+    F = np.empty_like(u)
+    rc = lib().orc_ibm(X.shape[0], X, U, A, nx, ny, nz, float(dx), float(origin[0]), float(origin[1]),
+                       float(origin[2]), u.ravel(), float(dt), int(cycles), f, F.ravel())
+    if rc != 0:
+        raise ValueError(f"orc_ibm failed ({rc})")
+    return f, F

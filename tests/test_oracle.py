@@ -743,3 +743,61 @@ def test_pik_ties_and_kernel_boundary(O):
     xd = v * turn + np.array([0.0, 0.0, 2.0 + RK])  # vertex 4 exactly rk above A's top
     (hca, _, _), (hcd, _, _) = O.pik([(T, xa), (T, xd)], RK)
     assert (hca >= 0).sum() == 0 and (hcd >= 0).sum() == 0
+
+
+# ------------------------------------------------------------------ IBM (multi-direct forcing)
+def test_phi4_is_peskins_four_point_function(O):
+    # textbook values and moments: partition of unity, zero first moment, sum of squares 3/8
+    assert (O.phi4(0.0), O.phi4(1.0), O.phi4(2.0), O.phi4(2.5)) == (0.5, 0.25, 0.0, 0.0)
+    assert O.phi4(-0.7) == O.phi4(0.7)
+    for r in np.random.default_rng(60).uniform(0.0, 1.0, 25):
+        w = np.array([O.phi4(r - j) for j in (-1, 0, 1, 2)])
+        assert w.sum() == pytest.approx(1.0, abs=1e-15)
+        assert (w * (r - np.array([-1, 0, 1, 2]))).sum() == pytest.approx(0.0, abs=1e-15)
+        assert (w ** 2).sum() == pytest.approx(3.0 / 8.0, abs=1e-15)
+    for a in (1.0 - 1e-9, 1.0 + 1e-9):                        # continuous where the branches meet
+        assert O.phi4(a) == pytest.approx(0.25, abs=1e-8)
+
+
+def test_vertex_areas(O, rbc):
+    v, t = octahedron()
+    T = O.OracleType(v, t, 1.0, 5.0, 0.05, 10.0, 1e-3)
+    assert np.allclose(T.vertex_areas(v), 4 * (np.sqrt(3) / 2) / 3, atol=1e-15)
+    mt, Tr = rbc
+    x = seeded_cell(mt, 61, amp=2.0)[0]
+    e1, e2 = x[mt.tris[:, 1]] - x[mt.tris[:, 0]], x[mt.tris[:, 2]] - x[mt.tris[:, 0]]
+    assert Tr.vertex_areas(x).sum() == pytest.approx(0.5 * np.linalg.norm(np.cross(e1, e2), axis=1).sum(), rel=1e-13)
+
+
+def _lattice(n=12, dx=0.5, origin=(-3.0, -2.0, -1.0)):
+    return n, dx, np.array(origin)
+
+
+def test_ibm_interpolates_linear_fields_exactly_and_conserves_force(O):
+    n, dx, o = _lattice()
+    idx = np.indices((n, n, n))[::-1].astype(float)             # (x, y, z) index of node [z][y][x]
+    nodes = o[:, None, None, None] + dx * idx
+    a, B = np.array([0.3, -0.2, 0.1]), np.random.default_rng(62).standard_normal((3, 3))
+    u = a[:, None, None, None] + np.einsum("cd,dzyx->czyx", B, nodes)
+    rng = np.random.default_rng(63)
+    X = o + dx * rng.uniform(2.0, n - 3.0, (40, 3))             # stencils inside the lattice
+    A = rng.uniform(0.1, 0.3, 40)
+    f, F = O.ibm(X, np.zeros_like(X), A, u, o, dx, dt=0.5, cycles=0)
+    assert np.allclose(f, -(a + X @ B.T) * A[:, None] / 0.5, rtol=1e-12, atol=1e-12)
+    # spread: sum_x F dx^3 = sum_k f_k dx
+    assert np.allclose(F.reshape(3, -1).sum(axis=1) * dx ** 3, f.sum(axis=0) * dx, rtol=1e-12)
+
+
+def test_ibm_single_point_cycle_closed_form(O):
+    # uniform u0: a cycle sees u_c(X) = u0 + dt f_{c-1} (3/8)^3 / dx^2, so with
+    # g = 1 - A (3/8)^3 / dx^2, f_c = g f_{c-1} + f0 = f0 (1 + g + ... + g^c),
+    # for any position of the point
+    n, dx, o = _lattice()
+    u0, U, A, dt = np.array([0.2, -0.1, 0.05]), np.array([[0.5, 0.3, -0.2]]), np.array([0.7]), 0.25
+    u = np.broadcast_to(u0[:, None, None, None], (3, n, n, n)).copy()
+    for X in (o + dx * np.array([[5.0, 6.0, 5.0]]), o + dx * np.array([[5.3, 6.71, 4.2]])):
+        f0 = (U - u0) * A / dt
+        g = 1 - A * (3 / 8) ** 3 / dx ** 2
+        for c in (1, 2, 3):
+            fc, _ = O.ibm(X, U, A, u, o, dx, dt, cycles=c)
+            assert np.allclose(fc, f0 * sum(g ** i for i in range(c + 1)), rtol=1e-13, atol=1e-14), c
