@@ -272,6 +272,7 @@ def main():
     ap.add_argument("--rayleigh-beta", type=float, default=0.0, help="(the paper's table: alpha 0, beta 0.01)")
     ap.add_argument("--pik-radius", type=float, default=0.0, help="particle-in-kernel collision kernel radius (0: off)")
     ap.add_argument("--collision-k", type=float, default=200.0, help="collision stiffness (with --pik-radius)")
+    ap.add_argument("--ibm-cycles", type=int, default=0, help="also time the immersed-boundary forces (0: skip)")
     args = ap.parse_args()
     rank, world, local = env_rank()
 
@@ -415,6 +416,37 @@ def main():
         barrier()
         e2e = {"value": world * ncells * K * args.steps / te, "unit": UNIT,
                "h2d_bytes_per_step": ndofs * 8, "d2h_bytes_per_step": ndofs * 8}
+
+    # ---- immersed-boundary forces on every vertex (a separate measurement): a lattice of
+    # spacing 0.5 over the cells' bounding box, a synthetic shear flow with a perturbation
+    ibm = None
+    if args.ibm_cycles > 0:
+        x = s.positions().reshape(-1, 3)
+        dx = 0.5
+        lo, hi = x.min(axis=0) - 2 * dx, x.max(axis=0) + 2 * dx
+        n = np.ceil((hi - lo) / dx).astype(int) + 1
+        zz, yy, xx = (torch.arange(int(m), dtype=torch.float64, device="cuda") * dx + float(o)
+                      for m, o in zip(n[::-1], lo[::-1]))
+        u = torch.zeros((3, int(n[2]), int(n[1]), int(n[0])), dtype=torch.float64, device="cuda")
+        u[0] += 1e-3 * (yy - yy.mean())[None, :, None]
+        u[1] += 1e-3 * torch.sin(0.1 * xx)[None, None, :]
+        u[2] += 1e-3 * torch.cos(0.1 * zz)[:, None, None]
+        torch.cuda.synchronize()                 # u is written on torch's stream, read on the solver's
+        fl, fg = s.ibm_forces(u, lo, dx, 1e-3, args.ibm_cycles)
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ea.record(stream)
+        for _ in range(args.steps):
+            s.ibm_forces(u, lo, dx, 1e-3, args.ibm_cycles, fl, fg)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        ti = ea.elapsed_time(eb) / 1e3 / args.steps
+        npts = ndofs // 3
+        ibm = {"cycles": args.ibm_cycles, "ms_per_call": ti * 1e3, "points": npts,
+               "points_per_s": npts / ti, "lattice": [int(v) for v in n], "dx": dx,
+               "fields_gb": 2 * 3 * int(np.prod(n)) * 8 / 1e9}
+        del u, fl, fg
     s.close()
     del s
     torch.cuda.empty_cache()
@@ -521,6 +553,8 @@ def main():
                        "pik_radius": args.pik_radius, "collision_k": args.collision_k if args.pik_radius > 0 else 0.0},
             "clocks": clk, "gpu_launches": launches, "parity": parity, "fp64_gpu": fp64, "e2e": e2e,
             "roofline": roof, "kernels": kernels, "solver": solver}
+    if ibm:
+        line["ibm"] = ibm
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.workload, alpha=args.rayleigh_alpha, beta=args.rayleigh_beta)
     print(json.dumps(line), flush=True)

@@ -251,6 +251,38 @@ int npfem_apply_pinv(npfem_ctx *ctx, int type_id, const double *q, double *z, in
 #define NPFEM_NOALLOC_MAX_ELEMS (1 << 21)
 int npfem_apply_pinv_noalloc(npfem_ctx *ctx, int type_id, const double *q, double *z, int n_cols);
 
+/* Lattice of a fluid velocity field for npfem_ibm_forces: nx x ny x nz nodes at
+ * (x0 + i dx, y0 + j dx, z0 + k dx); fields are component-major [3][nz][ny][nx]
+ * doubles (x fastest). */
+typedef struct {
+    int nx, ny, nz;
+    double dx, x0, y0, z0;
+} npfem_lattice;
+
+/* Immersed-boundary forces on every vertex of every cell by multi-direct
+ * forcing (supplementary IBM section, after Wang et al. and Ota et al.), the
+ * producer of F_ext in the coupled method.  The Lagrangian points are the
+ * vertices at the current state: positions X and velocities U (those of the last
+ * step), areas A = a third of the incident triangles' areas.  With Peskin's
+ * four-point function phi4 (support 4 dx per axis):
+ *   u(X) = sum_x u(x) phi4 phi4 phi4,   spread F(x) = sum_k f_k phi4 phi4 phi4 / dx^2
+ *   f_0 = (U - u*(X)) A / dt;  per cycle: F = spread(f), f += (U - (u* + F dt)(X)) A / dt
+ *   F_imm = spread(f_cycles)
+ * (a point stands for the shell volume A dx; lattice nodes outside the lattice
+ * are left out of every sum).
+ *   u_fluid : device, 3 nx ny nz doubles, the fluid velocity u*
+ *   dt      : > 0;  cycles >= 0
+ *   f_lagr  : device, npfem_num_dofs doubles (public layout), receives f_cycles
+ *   f_grid  : device, 3 nx ny nz doubles, receives F_imm (also the call's scratch)
+ * Enqueued on the context's stream (FP64; the spreading uses atomic additions,
+ * so F's last bits depend on their order); device errors surface at the next
+ * synchronising call.  The call keeps each point's stencil (about 108 bytes per
+ * vertex) in context memory for reuse by later calls.
+ * Errors: EINVAL (null pointer, empty lattice, dx or dt not > 0, cycles < 0),
+ * ESTATE (no cells), ENOMEM, ECUDA. */
+int npfem_ibm_forces(npfem_ctx *ctx, const npfem_lattice *lat, const double *u_fluid, double dt, int cycles,
+                     double *f_lagr, double *f_grid);
+
 /* Per-kernel timing: when enabled, every kernel launch of a step is
  * bracketed by CUDA events on the context stream (recorded into the step's
  * graph) and npfem_step waits for the step to finish to accumulate the

@@ -31,6 +31,7 @@ namespace npfem {
 // One mesh type's cells, as the search and the target kernel see them.
 struct PikType {
     const double *xn;            // state SoA [cell][3][nVp], internal vertex order
+    const double *vn;            // velocities, same layout
     const long long *pub_off;    // [cell] offset of the cell in the public arrays (doubles)
     const int *vpub;             // [nV] public index of internal vertex v
     const int *ring_ptr;         // [nV + 1] vertex -> incident triangles

@@ -119,6 +119,10 @@ struct npfem_ctx {
     double *d_pik_pos = nullptr;         // FP64 positions of the binned vertices [pos][3]
     int *d_pik_hit = nullptr;
     long long pik_n = 0, pik_h = 0;
+    // immersed-boundary forces: per-point stencils and areas of the last call
+    IbmPoint *d_ibm_pts = nullptr;
+    double *d_ibm_area = nullptr;
+    long long ibm_cap = 0;
     DevStatus *d_st = nullptr;
     DevStatus *h_st = nullptr;           // pinned
     int *d_any = nullptr;
@@ -641,17 +645,19 @@ void pik_alloc(npfem_ctx *ctx) {
     ctx->pik_h = h;
 }
 
-// The collision search and targets of one step (positions at the start of the step):
-// bin, scan, scatter, query, targets; see contact.cuh.
-void pik_search(npfem_ctx *ctx) {
-    PikTypes pt{};
-    std::vector<MeshTypeImpl *> tl;
-    int vb = 0, cb = 0;
+// Descriptors of the types that hold cells (flat vertex ids: types in order, cells,
+// internal vertices); returns the number of vertices.
+long long point_types(npfem_ctx *ctx, PikTypes &pt, std::vector<MeshTypeImpl *> &tl) {
+    pt = PikTypes{};
+    tl.clear();
+    long long vb = 0;
+    int cb = 0;
     for (auto *t : ctx->types) {
         if (!t->ncells) continue;
-        if (pt.ntypes == PIK_MAX_TYPES) fail(ctx, NPFEM_EINVAL, "collision search takes at most %d mesh types", PIK_MAX_TYPES);
+        if (pt.ntypes == PIK_MAX_TYPES) fail(ctx, NPFEM_EINVAL, "at most %d mesh types with cells", PIK_MAX_TYPES);
         PikType &P = pt.t[pt.ntypes++];
         P.xn = t->xn;
+        P.vn = t->vn;
         P.pub_off = t->pub_off;
         P.vpub = t->vpub;
         P.ring_ptr = mixed(ctx) ? t->tc32.vt_ptr : t->tc64.vt_ptr;
@@ -659,12 +665,22 @@ void pik_search(npfem_ctx *ctx) {
         P.nV = t->nV;
         P.nVp = t->nVp;
         P.ncells = t->ncells;
-        P.vbase = vb;
+        P.vbase = (int)vb;
         P.cbase = cb;
-        vb += t->ncells * t->nV;
+        vb += (long long)t->ncells * t->nV;
         cb += t->ncells;
         tl.push_back(t);
     }
+    if (vb > (1ll << 30)) fail(ctx, NPFEM_EINVAL, "%lld vertices exceed 2^30", vb);
+    return vb;
+}
+
+// The collision search and targets of one step (positions at the start of the step):
+// bin, scan, scatter, query, targets; see contact.cuh.
+void pik_search(npfem_ctx *ctx) {
+    PikTypes pt{};
+    std::vector<MeshTypeImpl *> tl;
+    const long long vb = point_types(ctx, pt, tl);
     if (vb != ctx->pik_n) fail(ctx, NPFEM_ESTATE, "collision search buffers out of date");
     const double rk = ctx->opt.pik_radius;
     int kb = 0;
@@ -1461,7 +1477,7 @@ void npfem_destroy(npfem_ctx *ctx) {
     }
     void *bufs[] = {ctx->d_f, ctx->d_fslot, ctx->d_stage, ctx->d_st, ctx->d_any, ctx->d_ffilt,
                     ctx->d_pik_cnt, ctx->d_pik_start, ctx->d_pik_fill, ctx->d_pik_key, ctx->d_pik_bsum,
-                    ctx->d_pik_ent, ctx->d_pik_pos, ctx->d_pik_hit};
+                    ctx->d_pik_ent, ctx->d_pik_pos, ctx->d_pik_hit, ctx->d_ibm_pts, ctx->d_ibm_area};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
@@ -1861,6 +1877,50 @@ int npfem_profile_read(npfem_ctx *ctx, npfem_kernel_times *out, int reset) {
                 ctx->prof_n[i] = 0;
             }
         }
+    });
+}
+
+int npfem_ibm_forces(npfem_ctx *ctx, const npfem_lattice *lat, const double *u_fluid, double dt, int cycles,
+                     double *f_lagr, double *f_grid) {
+    if (!ctx) return NPFEM_EINVAL;
+    return guard(ctx, [&] {
+        if (!lat || !u_fluid || !f_lagr || !f_grid) fail(ctx, NPFEM_EINVAL, "null argument");
+        if (lat->nx < 1 || lat->ny < 1 || lat->nz < 1 || !(lat->dx > 0) || !std::isfinite(lat->dx) ||
+            !std::isfinite(lat->x0) || !std::isfinite(lat->y0) || !std::isfinite(lat->z0) || !(dt > 0) ||
+            !std::isfinite(dt) || cycles < 0)
+            fail(ctx, NPFEM_EINVAL, "bad lattice, dt or cycles");
+        const long long nn = (long long)lat->nx * lat->ny * lat->nz;
+        if (nn > (1ll << 40)) fail(ctx, NPFEM_EINVAL, "lattice too large");
+        if (ctx->ndofs == 0) fail(ctx, NPFEM_ESTATE, "no cells");
+        PikTypes pt{};
+        std::vector<MeshTypeImpl *> tl;
+        const long long N = point_types(ctx, pt, tl);
+        if (N > ctx->ibm_cap) {
+            dfree((void *&)ctx->d_ibm_pts);
+            dfree((void *&)ctx->d_ibm_area);
+            ctx->ibm_cap = 0;
+            ctx->d_ibm_pts = dalloc<IbmPoint>(ctx, N);
+            ctx->d_ibm_area = dalloc<double>(ctx, N);
+            ctx->ibm_cap = N;
+        }
+        const IbmLattice L{lat->nx, lat->ny, lat->nz, lat->dx, lat->x0, lat->y0, lat->z0};
+        auto grid = [&](int ti) { return grid_for((long long)pt.t[ti].ncells * pt.t[ti].nV, 256, 16 * ctx->nsm); };
+        auto spread = [&] {
+            CK(cudaMemsetAsync(f_grid, 0, 3 * nn * sizeof(double), ctx->stream));
+            for (int ti = 0; ti < pt.ntypes; ++ti)
+                k_ibm_spread<<<grid(ti), 256, 0, ctx->stream>>>(pt, ti, L, ctx->d_ibm_pts, f_lagr, f_grid);
+        };
+        for (int ti = 0; ti < pt.ntypes; ++ti)
+            k_ibm_init<<<grid(ti), 256, 0, ctx->stream>>>(pt, ti, L, u_fluid, dt, ctx->d_ibm_pts, ctx->d_ibm_area,
+                                                          f_lagr);
+        for (int c = 0; c < cycles; ++c) {
+            spread();
+            for (int ti = 0; ti < pt.ntypes; ++ti)
+                k_ibm_update<<<grid(ti), 256, 0, ctx->stream>>>(pt, ti, L, u_fluid, f_grid, dt, ctx->d_ibm_pts,
+                                                                ctx->d_ibm_area, f_lagr);
+        }
+        spread();
+        CK(cudaGetLastError());
     });
 }
 

@@ -10,3 +10,4 @@
 #include "residual_ell.cuh"
 #include "filters.cuh"
 #include "contact.cuh"
+#include "ibm.cuh"

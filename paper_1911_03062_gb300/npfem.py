@@ -43,6 +43,11 @@ class Options(C.Structure):
                 ("pbd_kappa", C.c_double), ("pik_radius", C.c_double), ("collision_k", C.c_double)]
 
 
+class Lattice(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("x0", C.c_double),
+                ("y0", C.c_double), ("z0", C.c_double)]
+
+
 class Material(C.Structure):
     _fields_ = [("k_strain", C.c_double), ("k_area", C.c_double), ("k_bend", C.c_double),
                 ("k_vol", C.c_double), ("dt", C.c_double), ("rayleigh_alpha", C.c_double),
@@ -99,12 +104,14 @@ def load(path: str = LIB_PATH):
     L.npfem_apply_pinv.argtypes = [vp, ip, vp, vp, ip]
     L.npfem_apply_pinv_noalloc.argtypes = [vp, ip, vp, vp, ip]
     L.npfem_profile.argtypes = [vp, ip]
+    L.npfem_ibm_forces.argtypes = [vp, C.POINTER(Lattice), vp, C.c_double, ip, vp, vp]
     L.npfem_profile_read.argtypes = [vp, C.POINTER(KernelTimes), ip]
     L.npfem_last_error.argtypes = [vp]
     L.npfem_last_error.restype = C.c_char_p
     for name in ("npfem_create", "npfem_create_mesh_type", "npfem_add_cells", "npfem_step", "npfem_sync",
                  "npfem_get_positions", "npfem_get_velocities", "npfem_set_state", "npfem_stats",
-                 "npfem_apply_pinv", "npfem_apply_pinv_noalloc", "npfem_profile", "npfem_profile_read"):
+                 "npfem_apply_pinv", "npfem_apply_pinv_noalloc", "npfem_profile", "npfem_profile_read",
+                 "npfem_ibm_forces"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -259,6 +266,23 @@ class Solver:
         n_cols = q.shape[0]
         self._check(self._L.npfem_apply_pinv_noalloc(self._ctx, type_id, _dev_ptr(q), _dev_ptr(z), n_cols))
         return z
+
+    def ibm_forces(self, u, origin, dx, dt, cycles=1, f_lagr=None, f_grid=None):
+        """Immersed-boundary forces (multi-direct forcing) of every vertex from the fluid
+        velocity u (torch float64 on the device, [3, nz, ny, nx], nodes origin + (i, j, k) dx).
+        Returns (f_lagr [num_dofs], f_grid like u), both device tensors, after the
+        context's stream has finished them (the call synchronises it)."""
+        import torch
+        _, nz, ny, nx = u.shape
+        if f_lagr is None:
+            f_lagr = torch.empty(self.num_dofs, dtype=torch.float64, device=u.device)
+        if f_grid is None:
+            f_grid = torch.empty_like(u)
+        lat = Lattice(nx, ny, nz, float(dx), float(origin[0]), float(origin[1]), float(origin[2]))
+        self._check(self._L.npfem_ibm_forces(self._ctx, C.byref(lat), _dev_ptr(u), float(dt), int(cycles),
+                                             _dev_ptr(f_lagr), _dev_ptr(f_grid)))
+        self._check(self._L.npfem_sync(self._ctx))
+        return f_lagr, f_grid
 
     def profile(self, enable: bool):
         self._check(self._L.npfem_profile(self._ctx, int(bool(enable))))
