@@ -413,6 +413,12 @@ void set_kernel_attrs(npfem_ctx *ctx) {
         CK(cudaFuncGetAttributes(&fa, fn));
         CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes));
     };
+    {
+        cudaFuncAttributes fa;
+        CK(cudaFuncGetAttributes(&fa, k_ibm_spread_box));
+        CK(cudaFuncSetAttribute(k_ibm_spread_box, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(IBM_BOX_DOUBLES * sizeof(double))));
+    }
     if (mixed(ctx)) {
         all(k_predict<float, 4, 256>); all(k_predict<float, 8, 256>); all(k_predict<float, 16, 512>);
         all(k_iterate<float, 4, 256>); all(k_iterate<float, 8, 256>); all(k_iterate<float, 16, 512>);
@@ -1908,15 +1914,17 @@ int npfem_ibm_forces(npfem_ctx *ctx, const npfem_lattice *lat, const double *u_f
         auto spread = [&] {
             CK(cudaMemsetAsync(f_grid, 0, 3 * nn * sizeof(double), ctx->stream));
             for (int ti = 0; ti < pt.ntypes; ++ti)
-                k_ibm_spread<<<grid(ti), 256, 0, ctx->stream>>>(pt, ti, L, ctx->d_ibm_pts, f_lagr, f_grid);
+                k_ibm_spread_box<<<grid(ti), 256, IBM_BOX_DOUBLES * sizeof(double), ctx->stream>>>(
+                    pt, ti, L, ctx->d_ibm_pts, f_lagr, f_grid);
         };
         for (int ti = 0; ti < pt.ntypes; ++ti)
             k_ibm_init<<<grid(ti), 256, 0, ctx->stream>>>(pt, ti, L, u_fluid, dt, ctx->d_ibm_pts, ctx->d_ibm_area,
                                                           f_lagr);
         for (int c = 0; c < cycles; ++c) {
             spread();
+            k_ibm_correct<<<grid_for(3 * nn, 256, 16 * ctx->nsm), 256, 0, ctx->stream>>>(3 * nn, u_fluid, f_grid, dt);
             for (int ti = 0; ti < pt.ntypes; ++ti)
-                k_ibm_update<<<grid(ti), 256, 0, ctx->stream>>>(pt, ti, L, u_fluid, f_grid, dt, ctx->d_ibm_pts,
+                k_ibm_update<<<grid(ti), 256, 0, ctx->stream>>>(pt, ti, L, f_grid, dt, ctx->d_ibm_pts,
                                                                 ctx->d_ibm_area, f_lagr);
         }
         spread();
