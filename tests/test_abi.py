@@ -1,6 +1,6 @@
 """CPU checks of the C-ABI library: it builds for sm_103a, exports every
-function include/npfem.h declares, and refuses to run without a GPU (no CPU
-fallback)."""
+function include/npfem.h declares, the Python binding's struct mirrors have the
+header's layouts, and it refuses to run without a GPU (no CPU fallback)."""
 import ctypes
 
 import pytest
@@ -41,3 +41,30 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(N, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         N.load(str(tmp_path / "libnpfem.so"))
+
+
+def test_struct_layouts_match_header(tmp_path):
+    # the ctypes mirrors of the header's structs: size and every field offset, as a C
+    # compiler lays them out
+    import os
+    import subprocess
+    structs = {"npfem_options": N.Options, "npfem_material": N.Material, "npfem_step_stats": N.StepStats,
+               "npfem_kernel_times": N.KernelTimes, "npfem_lattice": N.Lattice}
+    inc = os.path.join(os.path.dirname(B.LIB), os.pardir, "include")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "npfem.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines))
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.abspath(inc), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
