@@ -187,7 +187,9 @@ __global__ void k_pik_scatter(const PikTypes T, int ti, const unsigned *__restri
 
 // 4. closest foreign vertex inside the kernel, one binned vertex per thread in bucket order;
 //    hit[flat] = flat id of the neighbour or -1; the number of contaminated vertices is
-//    added to st->contacts.  Screen: |d_f32| against rk + tol, tol = 1e-6 (|x|+|y|+|z|+rk)
+//    added to st->contacts.  Screen: |d_f32| against rk + tol, tol = 1e-6 (|x|+|y|+|z|+rk),
+//    and, once a neighbour is found, against its distance + tol (FP64 only for candidates
+//    that can still win)
 //    (the FP32 copies are within 2^-24 |coordinate| of the FP64 values); the FP64 test
 //    |d|^2 < rk^2 then decides.
 __global__ void k_pik_query(const PikEntry *__restrict__ ent, const double *__restrict__ pos64,
@@ -205,6 +207,7 @@ __global__ void k_pik_query(const PikEntry *__restrict__ ent, const double *__re
             const float rs = (float)rk + tol, rs2 = rs * rs;
             double best = r2;
             int bpub = INT_MAX, bflat = -1;
+            float thr2 = rs2;       // screen: FP32 |d|^2 above it cannot be inside rk nor beat the best
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy) {
                     const unsigned b0 = pik_key(cx - 1, cy + dy, cz + dz, g), b1 = pik_key(cx, cy + dy, cz + dz, g),
@@ -226,12 +229,16 @@ __global__ void k_pik_query(const PikEntry *__restrict__ ent, const double *__re
                         for (unsigned k = lo[r]; k < hi[r]; ++k) {
                             const PikEntry c = ent[k];
                             const float fx = c.x - e.x, fy = c.y - e.y, fz = c.z - e.z;
-                            if (c.owner == e.owner || fx * fx + fy * fy + fz * fz > rs2) continue;
+                            if (c.owner == e.owner || fx * fx + fy * fy + fz * fz > thr2) continue;
                             const double d2 = dist2_rn(ex, ey, ez, pos64[3ll * k], pos64[3ll * k + 1], pos64[3ll * k + 2]);
                             if (d2 < r2 && (d2 < best || (d2 == best && c.pub < bpub))) {
                                 best = d2;
                                 bpub = c.pub;
                                 bflat = c.flat;
+                                // later candidates need |d| <= sqrt(best): screen at (sqrt(best) + tol)^2,
+                                // widened by 1e-6 twice for this bound's own FP32 roundings
+                                const float sb = sqrtf((float)best) * (1.0f + 1e-6f) + tol;
+                                thr2 = fminf(rs2, sb * sb * (1.0f + 1e-6f));
                             }
                         }
                 }
