@@ -178,3 +178,14 @@ def test_sampled_cells_rbc10k_plt1500_tf32():
     xo, _ = run_oracle(groups, 1, sample=[[0, 5000, 9999], [0, 1499]])
     assert rel_pos_err(xg, xo, groups) <= TOL_MIXED
     assert st["max_refine_residual"] <= 1e-6
+
+
+def test_sampled_cells_hetero20k_full_bf16():
+    # the full 20000-cell, 12-type batch in one grouped launch per global step, 1 step,
+    # the first and last cell of every type vs the oracle
+    groups = [I.materialise(g) for g in I.workload_groups("hetero20k")]
+    assert sum(g.n_cells for g in groups) == 20000
+    xg, _, st = run_gpu(groups, 1, precision="bf16")
+    xo, _ = run_oracle(groups, 1, sample=[[0, g.n_cells - 1] for g in groups])
+    assert rel_pos_err(xg, xo, groups) <= TOL_MIXED
+    assert st["max_refine_residual"] <= 1e-6
