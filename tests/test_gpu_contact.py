@@ -131,3 +131,39 @@ def test_contact_option_validation():
     with pytest.raises(NpfemError) as e:
         Solver(precision="fp64", pik_radius=0.5, collision_k=0.0)
     assert e.value.code == EINVAL
+
+
+def test_all_optional_parts_together_fp64():
+    # median filter, collisions, Rayleigh damping, PBD damping and the velocity cap in one
+    # step, composed in the oracle in the library's order: median of the given forces ->
+    # search on x_n -> damped step with the contact term -> PBD -> cap
+    import dataclasses
+    from oracle import oracle as O
+    from paper_1911_03062_gb300.npfem import Solver
+    damp = lambda mt: dataclasses.replace(mt, material=dataclasses.replace(mt.material, rayleigh_alpha=1.0,
+                                                                           rayleigh_beta=0.01))
+    groups = [I.materialise(I.Group(damp(I.rbc_type()), 3, 510, amp=0.3, box=6.0)),
+              I.materialise(I.Group(damp(I.plt_type()), 2, 511, amp=0.3, box=6.0))]
+    kc, kappa, umax = KC_FP64, 0.7, 0.4
+    s = Solver(precision="fp64", force_median=True, u_max=umax, pbd_kappa=kappa, pik_radius=RK, collision_k=kc)
+    for g in groups:
+        s.add_cells(s.create_type(g.mtype), g.x0, g.v0)
+    s.step(public(groups, "f_ext"))
+    x1, v1, st = split(s.positions(), groups), split(s.velocities(), groups), s.stats()
+    s.close()
+    Ts = [O.OracleType.from_mesh_type(g.mtype) for g in groups]
+    res = O.pik([(Ts[gi], g.x0[c]) for gi, g in enumerate(groups) for c in range(g.n_cells)], RK)
+    k, contacts = 0, 0
+    for gi, g in enumerate(groups):
+        T = Ts[gi]
+        for c in range(g.n_cells):
+            hc, _, p = res[k]
+            k += 1
+            hit = (hc >= 0).astype(np.int32)
+            contacts += int(hit.sum())
+            f = O.force_median(T, g.f_ext[c][None])
+            xo, vo = T.step_cells_col(g.x0[c][None], g.v0[c][None], f, kc, hit[None], p[None])
+            vo = O.velocity_cap(O.pbd_damping(T, xo, vo, kappa), umax)
+            assert np.linalg.norm(x1[gi][c] - xo[0], axis=1).max() / g.mtype.radius <= 1e-10, (gi, c)
+            assert np.abs(v1[gi][c] - vo[0]).max() <= 1e-5 * umax, (gi, c)
+    assert st["contacts"] == contacts and contacts > 100
