@@ -801,3 +801,23 @@ def test_ibm_single_point_cycle_closed_form(O):
         for c in (1, 2, 3):
             fc, _ = O.ibm(X, U, A, u, o, dx, dt, cycles=c)
             assert np.allclose(fc, f0 * sum(g ** i for i in range(c + 1)), rtol=1e-13, atol=1e-14), c
+
+
+def test_damped_collision_step_converges_to_newtons_law(O, rbc):
+    # both optional terms at once: M (v1 - v0)/h + C v1 = F_int(x1) + F_ext (zero at
+    # contaminated vertices) + kc (p - x1), C = alpha M + beta L
+    mt, T = rbc
+    xn, vn, f = seeded_cell(mt, 64, amp=5.0)
+    vn = vn + np.random.default_rng(65).standard_normal(vn.shape)
+    rng = np.random.default_rng(66)
+    hit = (rng.uniform(size=mt.nV) < 0.2).astype(np.int32)
+    p = xn + 0.05 * rng.standard_normal(xn.shape)
+    Td = damped(mt, O)
+    x1, v1 = Td.step_cells_col(xn[None], vn[None], f[None], KC, hit[None], p[None], K=60)
+    x1, v1 = x1[0], v1[0]
+    h, m = mt.material.dt, 1.0 / mt.nV
+    L = T.P_dense() - np.eye(mt.nV) * m / h ** 2
+    _, gint, _ = T.energy(x1, x1, mask=30)
+    lhs = m * (v1 - vn) / h + ALPHA * m * v1 + BETA * (L @ v1)
+    rhs = -gint + f * (1 - hit)[:, None] + KC * (p - x1) * hit[:, None]
+    assert np.abs(lhs - rhs).max() < 1e-7 * np.abs(m * (v1 - vn) / h).max()
