@@ -638,6 +638,8 @@ void pik_alloc(npfem_ctx *ctx) {
                      (void **)&ctx->d_pik_key, (void **)&ctx->d_pik_bsum, (void **)&ctx->d_pik_ent,
                      (void **)&ctx->d_pik_pos, (void **)&ctx->d_pik_hit};
     for (void **b : bufs) dfree(*b);
+    ctx->pik_n = -1;                     // until every buffer is in place: a search refuses to run
+    ctx->pik_h = 0;
     const long long nb = (h + 1 + SCAN_B * SCAN_ITEMS - 1) / (SCAN_B * SCAN_ITEMS);
     ctx->d_pik_cnt = dalloc<unsigned>(ctx, h + 1);
     ctx->d_pik_start = dalloc<unsigned>(ctx, h + 1);
