@@ -273,11 +273,15 @@ class Solver:
         Returns (f_lagr [num_dofs], f_grid like u), both device tensors, after the
         context's stream has finished them (the call synchronises it)."""
         import torch
+        if u.dim() != 4 or u.shape[0] != 3:
+            raise ValueError("u must be [3, nz, ny, nx]")
         _, nz, ny, nx = u.shape
         if f_lagr is None:
             f_lagr = torch.empty(self.num_dofs, dtype=torch.float64, device=u.device)
         if f_grid is None:
             f_grid = torch.empty_like(u)
+        if f_lagr.numel() != self.num_dofs or tuple(f_grid.shape) != tuple(u.shape):
+            raise ValueError("f_lagr must hold num_dofs values and f_grid the shape of u")
         lat = Lattice(nx, ny, nz, float(dx), float(origin[0]), float(origin[1]), float(origin[2]))
         self._check(self._L.npfem_ibm_forces(self._ctx, C.byref(lat), _dev_ptr(u), float(dt), int(cycles),
                                              _dev_ptr(f_lagr), _dev_ptr(f_grid)))
