@@ -798,6 +798,15 @@ static double vdot(const double *a, const double *b, int n) {
     return s;
 }
 
+/* Optional per-iteration record of one step (every array nullable):
+ *   x, g : [K+1][n3] the iterates x^0 (= y) .. x^K and the gradients at them
+ *   d    : [K][n3]   the direction taken at iteration k (after the descent test)
+ *   kept : [K]       1 where the pair (x^{k+1} - x^k, g^{k+1} - g^k) entered the history */
+typedef struct {
+    double *x, *g, *d;
+    int *kept;
+} orc_trace;
+
 /*
  * One implicit-Euler step of one cell (Eqs. vel, Newton2nd via the
  * minimisation of g):
@@ -816,13 +825,28 @@ static double vdot(const double *a, const double *b, int n) {
 static int step_impl(const orc_type *T, const double *xn, const double *vn, const double *f_in,
                      int K, int m, double c1, int max_bt, const orc_coll *cc,
                      double *x_out, double *v_out,
-                     double *g_tr, double *a_tr, int *bt_tr, int *fb_tr);
+                     double *g_tr, double *a_tr, int *bt_tr, int *fb_tr,
+                     double curv_tol, const orc_trace *tr);
 
 int orc_step(const orc_type *T, const double *xn, const double *vn, const double *f,
              int K, int m, double c1, int max_bt,
              double *x_out, double *v_out,
              double *g_tr, double *a_tr, int *bt_tr, int *fb_tr) {
-    return step_impl(T, xn, vn, f, K, m, c1, max_bt, NULL, x_out, v_out, g_tr, a_tr, bt_tr, fb_tr);
+    return step_impl(T, xn, vn, f, K, m, c1, max_bt, NULL, x_out, v_out, g_tr, a_tr, bt_tr, fb_tr,
+                     CURV_TOL, NULL);
+}
+
+/* orc_step with the per-iteration record (orc_trace) and the curvature threshold
+ * of the history as a parameter (CURV_TOL = 1e-12 is the method's; a test that
+ * needs indefinite updates to reach the descent fallback passes -INFINITY). */
+int orc_step_trace(const orc_type *T, const double *xn, const double *vn, const double *f,
+                   int K, int m, double c1, int max_bt, double curv_tol,
+                   double *x_out, double *v_out,
+                   double *g_tr, double *a_tr, int *bt_tr, int *fb_tr,
+                   double *xs, double *gs, double *ds, int *kept) {
+    orc_trace tr = {xs, gs, ds, kept};
+    return step_impl(T, xn, vn, f, K, m, c1, max_bt, NULL, x_out, v_out, g_tr, a_tr, bt_tr, fb_tr,
+                     curv_tol, &tr);
 }
 
 /* The step with the PIK collision framework (Sec. 2.2, Supp. PIK): the
@@ -832,13 +856,15 @@ int orc_step_col(const orc_type *T, const double *xn, const double *vn, const do
                  int K, int m, double c1, int max_bt, double kc, const int *hit, const double *p,
                  double *x_out, double *v_out) {
     orc_coll cc = {kc, hit, p};
-    return step_impl(T, xn, vn, f, K, m, c1, max_bt, &cc, x_out, v_out, NULL, NULL, NULL, NULL);
+    return step_impl(T, xn, vn, f, K, m, c1, max_bt, &cc, x_out, v_out, NULL, NULL, NULL, NULL,
+                     CURV_TOL, NULL);
 }
 
 static int step_impl(const orc_type *T, const double *xn, const double *vn, const double *f_in,
                      int K, int m, double c1, int max_bt, const orc_coll *cc,
                      double *x_out, double *v_out,
-                     double *g_tr, double *a_tr, int *bt_tr, int *fb_tr) {
+                     double *g_tr, double *a_tr, int *bt_tr, int *fb_tr,
+                     double curv_tol, const orc_trace *tr) {
     int nV = T->nV, n3 = 3*nV;
     double h = T->h;
     int mm = m > 0 ? m : 1;
@@ -870,6 +896,8 @@ static int step_impl(const orc_type *T, const double *xn, const double *vn, cons
     memcpy(x, y, sizeof(double)*n3);
     double g = energy_impl(T, x, y, TERM_ALL, gr, NULL, cc);
     if (g_tr) g_tr[0] = g;
+    if (tr && tr->x) memcpy(tr->x, x, sizeof(double)*n3);
+    if (tr && tr->g) memcpy(tr->g, gr, sizeof(double)*n3);
     int cnt = 0, head = 0, caps = 0;    /* ring: newest at (head-1) mod m */
     for (int k = 0; k < K; ++k) {
         int fb = 0;
@@ -898,6 +926,7 @@ static int step_impl(const orc_type *T, const double *xn, const double *vn, cons
             for (int i = 0; i < n3; ++i) d[i] = -d[i];
             gd = vdot(gr, d, n3);
         }
+        if (tr && tr->d) memcpy(tr->d + (long)k*n3, d, sizeof(double)*n3);
         double alpha = 1.0, gtv;
         int bt = 0;
         for (;;) {
@@ -914,7 +943,11 @@ static int step_impl(const orc_type *T, const double *xn, const double *vn, cons
         memcpy(x, xt, sizeof(double)*n3);
         memcpy(gr, gt, sizeof(double)*n3);
         g = gtv;
-        if (m > 0 && sy > CURV_TOL*ns*ny) {
+        const int keep = m > 0 && sy > curv_tol*ns*ny;
+        if (tr && tr->kept) tr->kept[k] = keep;
+        if (tr && tr->x) memcpy(tr->x + (long)(k+1)*n3, x, sizeof(double)*n3);
+        if (tr && tr->g) memcpy(tr->g + (long)(k+1)*n3, gr, sizeof(double)*n3);
+        if (keep) {
             memcpy(S + (long)head*n3, s_new, sizeof(double)*n3);
             memcpy(Y + (long)head*n3, y_new, sizeof(double)*n3);
             rho[head] = 1.0/sy;

@@ -66,6 +66,9 @@ def lib():
             L.orc_step.argtypes = [vp, dp, dp, dp, C.c_int, C.c_int, C.c_double, C.c_int,
                                    dp, dp, vp, vp, vp, vp]
             L.orc_step.restype = C.c_int
+            L.orc_step_trace.argtypes = [vp, dp, dp, dp, C.c_int, C.c_int, C.c_double, C.c_int, C.c_double,
+                                         dp, dp, dp, dp, ip, ip, dp, dp, dp, ip]
+            L.orc_step_trace.restype = C.c_int
             L.orc_step_cells.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, C.c_int, C.c_double,
                                          C.c_int, vp, vp]
             L.orc_step_cells.restype = C.c_int
@@ -221,6 +224,21 @@ class OracleType:
             return xo, vo, dict(g=gt, alpha=at, backtracks=bt, fallback=fb, caps=caps)
         lib().orc_step(self._h, xn, vn, f, K, m, c1, max_bt, xo, vo, None, None, None, None)
         return xo, vo
+
+    def step_trace(self, xn, vn, f, K=10, m=5, c1=1e-4, max_bt=8, curv_tol=1e-12):
+        """One step with the full per-iteration record: iterates x [K+1, nV, 3] (x[0] = y),
+        gradients g [K+1, nV, 3], directions d [K, nV, 3], kept [K] (the pair of iteration
+        k entered the history), energies, alphas, halvings, fallbacks and the cap count.
+        ``curv_tol`` is the history's curvature threshold (the method's is 1e-12)."""
+        xn, vn, f = (_c(a).reshape(self.nV, 3) for a in (xn, vn, f))
+        xo, vo = np.empty_like(xn), np.empty_like(xn)
+        gt, at = np.empty(K + 1), np.empty(K)
+        bt, fb, kept = np.empty(K, np.int32), np.empty(K, np.int32), np.empty(K, np.int32)
+        xs, gs, ds = np.empty((K + 1, self.nV, 3)), np.empty((K + 1, self.nV, 3)), np.empty((K, self.nV, 3))
+        caps = lib().orc_step_trace(self._h, xn, vn, f, K, m, c1, max_bt, float(curv_tol), xo, vo,
+                                    gt, at, bt, fb, xs, gs, ds, kept)
+        return xo, vo, dict(g=gt, alpha=at, backtracks=bt, fallback=fb, caps=caps, x=xs, grad=gs, d=ds,
+                            kept=kept)
 
     def step_cells_col(self, xn, vn, f, kc, hit, p, K=10, m=5, c1=1e-4, max_bt=8):
         """Step n cells with the PIK collision term: hit [n, nV] (nonzero = contaminated

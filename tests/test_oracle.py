@@ -409,6 +409,154 @@ def test_tetrahedron_matches_brute_force_newton(O):
     assert np.abs(x - y).max() > 1e-3             # a non-trivial minimiser
 
 
+# ------------------------------------------- quasi-Newton control flow
+# The update after Eq. (genericOptimizationNewton), x^{k+1} = x^k - alpha H grad g,
+# with H the L-BFGS operator of initial matrix P^{-1}.  The oracle evaluates H grad g
+# by the two-loop recursion; these tests rebuild H densely by the BFGS inverse update
+# (Nocedal & Wright, Numerical Optimization, Eq. 6.17):
+#     H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T,   rho = 1 / (s . y),
+# from H_0 = P^{-1} (per component: kron(P^{-1}, I_3) in the [nV][3] layout) over the
+# last min(k, m) kept pairs, oldest first, and check every iteration's direction,
+# the history's curvature rule, the descent fallback and the Armijo acceptance
+# against the step's own record (orc_step_trace).
+
+def slow_cell(O, seed=5, dt=0.05, mirror=False):
+    """A level-1 RBC at dt = 0.05 (inertia no longer dominant, so the iterations stay
+    far from convergence for K > 15) in a deformed state with velocities and forces."""
+    unit, tris = I.icosphere(1)
+    rest = I.rbc_shape(unit)
+    T = O.OracleType(rest, tris, k_strain=1.0, k_area=5.0, k_bend=0.5, k_vol=10.0, dt=dt)
+    rng = np.random.default_rng(seed)
+    if mirror:        # inside out: large non-convex projections, a negative-curvature pair
+        xn = rest * np.array([1, 1, -1]) + 0.1 * rng.standard_normal(rest.shape)
+    else:
+        xn = rest @ rot(seed).T + 0.3 * rng.standard_normal(rest.shape)
+    vn = rng.standard_normal(rest.shape)
+    f = rng.standard_normal(rest.shape)
+    return T, xn, vn, f
+
+
+def bfgs_directions(T, tr, m, curv_tol=1e-12):
+    """Per iteration k of a traced step: (the direction the method prescribes, whether
+    the descent fallback applies, the L-BFGS direction before that test), from the
+    dense BFGS inverse update over the pairs of the recorded iterates."""
+    n3 = 3 * T.nV
+    H0 = np.kron(np.linalg.inv(T.P_dense()), np.eye(3))
+    pairs, out = [], []
+    for k in range(len(tr["d"])):
+        g = tr["grad"][k].ravel()
+        H = H0
+        for s, y in pairs[-m:]:
+            rho = 1.0 / (s @ y)
+            V = np.eye(n3) - rho * np.outer(y, s)
+            H = V.T @ H @ V + rho * np.outer(s, s)
+        d_lbfgs = -H @ g
+        fallback = bool(pairs) and g @ d_lbfgs >= 0
+        if fallback:
+            pairs = []
+        out.append((-H0 @ g if fallback else d_lbfgs, fallback, d_lbfgs))
+        s = (tr["x"][k + 1] - tr["x"][k]).ravel()
+        y = (tr["grad"][k + 1] - tr["grad"][k]).ravel()
+        if m > 0 and s @ y > curv_tol * np.linalg.norm(s) * np.linalg.norm(y):
+            pairs.append((s, y))
+    return out
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("m", [1, 3, 5])
+def test_lbfgs_direction_is_the_dense_bfgs_inverse_update(O, m):
+    T, xn, vn, f = slow_cell(O)
+    K = 18
+    x1, _, tr = T.step_trace(xn, vn, f, K=K, m=m)
+    assert tr["kept"].all() and not tr["fallback"].any()
+    dirs = bfgs_directions(T, tr, m)
+    for k, (d, fb, _) in enumerate(dirs):
+        assert rel(tr["d"][k], d) < 1e-10, (k, rel(tr["d"][k], d))
+    # far from convergence to the end: the ring wraps with meaningful pairs
+    assert np.linalg.norm(tr["d"][-1]) > 1e-5 * np.linalg.norm(tr["d"][0])
+    # the history matters: a step with another m is a different step
+    x1b, _ = T.step(xn, vn, f, K=K, m=m + 1)
+    assert np.abs(x1 - x1b).max() > 1e-8
+    # and the recorded iterates chain: x^{k+1} = x^k + alpha_k d_k, x_{n+1} = x^K
+    for k in range(K):
+        assert np.allclose(tr["x"][k + 1], tr["x"][k] + tr["alpha"][k] * tr["d"][k], rtol=0, atol=1e-13)
+    assert np.array_equal(x1, tr["x"][K])
+
+
+def test_curvature_rule_and_descent_fallback(O):
+    T, xn, vn, f = slow_cell(O, seed=23, mirror=True)
+    K, m = 22, 3
+    # the method's threshold (s.y > 1e-12 |s||y|) rejects the negative-curvature pair
+    _, _, tr = T.step_trace(xn, vn, f, K=K, m=m)
+    sy = np.array([np.dot((tr["x"][k + 1] - tr["x"][k]).ravel(), (tr["grad"][k + 1] - tr["grad"][k]).ravel())
+                   for k in range(K)])
+    assert (sy < 0).sum() == 1 and not tr["kept"][sy < 0].any() and tr["kept"][sy > 0].all()
+    for k, (d, fb, _) in enumerate(bfgs_directions(T, tr, m)):
+        assert not fb and rel(tr["d"][k], d) < 1e-10, k
+    # with every pair kept, the update after the indefinite one is not a descent
+    # direction: the step clears its history and takes -P^{-1} grad instead
+    _, _, tr = T.step_trace(xn, vn, f, K=K, m=m, curv_tol=-np.inf)
+    dirs = bfgs_directions(T, tr, m, curv_tol=-np.inf)
+    fbs = [fb for _, fb, _ in dirs]
+    assert fbs == [bool(b) for b in tr["fallback"]] and sum(fbs) == 1
+    k_fb = fbs.index(True)
+    g = tr["grad"][k_fb].ravel()
+    d_l = dirs[k_fb][2]
+    assert g @ d_l > 0.05 * np.linalg.norm(g) * np.linalg.norm(d_l)      # decisively uphill
+    assert rel(tr["d"][k_fb], -T.solve(tr["grad"][k_fb])) < 1e-12
+    for k, (d, _, _) in enumerate(dirs):
+        assert rel(tr["d"][k], d) < 1e-10, k
+    # after the reset the history restarts from the fallback's own pair
+    assert k_fb + 3 < K and all(tr["kept"][k_fb:])
+
+
+def armijo_trials(T, tr, k, c1):
+    """(energy at each halving j = 0..bt of iteration k, the Armijo right-hand sides)."""
+    y = tr["x"][0]                      # x^0 = y, the inertia term's centre
+    x, d, g0 = tr["x"][k], tr["d"][k], tr["g"][k]
+    gd = float(np.dot(tr["grad"][k].ravel(), d.ravel()))
+    e, rhs = [], []
+    for j in range(tr["backtracks"][k] + 1):
+        a = 0.5 ** j
+        e.append(T.energy(x + a * d, y, grad=False)[0])
+        rhs.append(g0 + c1 * a * gd)
+    return np.array(e), np.array(rhs), gd
+
+
+def test_armijo_takes_the_first_sufficient_halving(O):
+    T, xn, vn, f = slow_cell(O, seed=7)
+    K, c1 = 12, 0.9                     # c1 = 0.9: alpha = 1 rarely suffices
+    x1, _, tr = T.step_trace(xn, vn, f, K=K, m=3, c1=c1, max_bt=8)
+    assert tr["caps"] == 0 and tr["backtracks"].sum() >= K and tr["backtracks"].max() >= 2
+    for k in range(K):
+        e, rhs, gd = armijo_trials(T, tr, k, c1)
+        assert gd < 0
+        assert np.all(e[:-1] > rhs[:-1]), k            # every earlier halving fails
+        assert e[-1] <= rhs[-1], k                     # the accepted one satisfies it
+        assert tr["alpha"][k] == 0.5 ** tr["backtracks"][k]
+        assert tr["g"][k + 1] == e[-1]                 # the energy of the accepted trial
+    assert np.all(np.diff(tr["g"]) < 0)
+
+
+def test_armijo_cap_takes_the_last_trial(O):
+    T, xn, vn, f = slow_cell(O, seed=7)
+    K, c1, cap = 8, 0.9, 2
+    _, _, tr = T.step_trace(xn, vn, f, K=K, m=3, c1=c1, max_bt=cap)
+    capped = 0
+    for k in range(K):
+        e, rhs, _ = armijo_trials(T, tr, k, c1)
+        assert np.all(e[:-1] > rhs[:-1]), k
+        assert tr["g"][k + 1] == e[-1]                 # the last trial evaluated is the one taken
+        if e[-1] > rhs[-1]:                            # no trial met the condition: the cap
+            capped += 1
+            assert tr["backtracks"][k] == cap and tr["alpha"][k] == 0.5 ** cap
+            assert np.allclose(tr["x"][k + 1], tr["x"][k] + 0.25 * tr["d"][k], rtol=0, atol=1e-13)
+    assert capped == tr["caps"] and capped >= K - 2
+
+
 def test_dynamics_amplify_rounding_level_perturbations(O):
     # The stepped dynamics of the amplitude-0.3 suspension amplify a 1e-12 R
     # perturbation of the initial positions by more than 100x within 40 steps, so two
