@@ -102,6 +102,12 @@ typedef struct {
                                the start-of-step positions.  P is unchanged (the term's curvature
                                enters through the L-BFGS pairs).  Default 0 (off). */
     double collision_k;     /* stiffness of the collision energy; > 0 when pik_radius > 0 */
+    double curvature_tol;   /* an iteration's pair (s, y) enters the L-BFGS history only if
+                               s.y > curvature_tol |s| |y| (default 1e-12, which keeps every H
+                               positive definite).  A negative value also admits pairs of
+                               negative curvature (-INFINITY: every pair); the descent test then
+                               catches an uphill direction, clears the history and takes
+                               -P^{-1} grad g.  NaN is rejected (EINVAL). */
 } npfem_options;
 
 /* Material and time step of one mesh type.  Element weights follow the
@@ -192,8 +198,13 @@ size_t npfem_num_dofs(const npfem_ctx *ctx);
 
 /* Advance every cell by one time step of its type's h under the external
  * forces f_ext (npfem_num_dofs doubles, public layout).  f_ext_on_device != 0
- * means f_ext is a device pointer readable on the context's stream (no copy);
- * otherwise it is host memory, copied to the device during the call.
+ * means f_ext is a device pointer read on the context's stream (no copy): the
+ * caller's writes of it must be complete before that stream reaches the step
+ * (e.g. the same stream, or an event the stream waits on), and it must stay
+ * valid and unchanged until the step has run (npfem_sync, or an event recorded
+ * on the stream after the call).  Otherwise it is host memory, copied to the
+ * device in the call; for page-locked memory that copy runs asynchronously on
+ * the stream, so keep the buffer unchanged until the next synchronising call.
  * The call enqueues the work and returns; device errors are reported by the
  * next call that synchronises (get_*, stats, npfem_sync).
  * Errors: EINVAL, ESTATE (no cells), ECUDA. */
@@ -220,7 +231,10 @@ int npfem_stats(npfem_ctx *ctx, npfem_step_stats *out);
 /* Global-step building block: z = P^{-1} q for n_cols right-hand sides of
  * mesh type type_id, through the same apply (and, in the mixed forms, the
  * same refinement) as npfem_step.  q, z: device pointers, n_cols x nV
- * doubles (one column = one component of one cell, vertex contiguous).
+ * doubles (one column = one component of one cell, vertex contiguous), read
+ * and written on the context's stream: q must be complete before that stream
+ * reaches the call.  The call synchronises the stream before it returns, so z
+ * is complete on return (this holds for npfem_apply_pinv_noalloc too).
  * Errors: EINVAL, ENOMEM, ECUDA. */
 int npfem_apply_pinv(npfem_ctx *ctx, int type_id, const double *q, double *z, int n_cols);
 
@@ -282,6 +296,14 @@ typedef struct {
  * ESTATE (no cells), ENOMEM, ECUDA. */
 int npfem_ibm_forces(npfem_ctx *ctx, const npfem_lattice *lat, const double *u_fluid, double dt, int cycles,
                      double *f_lagr, double *f_grid);
+
+/* Self-check of device failure detection: enqueues one kernel that waits, through
+ * the same bounded mbarrier wait as the tensor-core kernels, on a barrier that
+ * nothing arrives on (no copy is in flight) for limit_ms milliseconds (1..2000),
+ * then records an expired wait in the context's error word.  The next
+ * synchronising call (npfem_sync, get_*, stats) returns NPFEM_ETIMEOUT and clears
+ * the word; the context stays usable.  Errors: EINVAL, ECUDA. */
+int npfem_check_wait(npfem_ctx *ctx, int limit_ms);
 
 /* Per-kernel timing: when enabled, every kernel launch of a step is
  * bracketed by CUDA events on the context stream (recorded into the step's

@@ -56,16 +56,31 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Bounded wait: false after WAIT_NS of wall time (the longest legitimate wait
-// in these kernels is one tile's work, microseconds).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait: false after limit_ns of wall time.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
         for (int i = 0; i < 64; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > WAIT_NS) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
+}
+
+// The kernels' waits: WAIT_NS (the longest legitimate wait in these kernels is one
+// tile's work, microseconds).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) { return mbar_wait_for(bar, parity, WAIT_NS); }
+
+// Self-check of the failure path: one thread waits, through the same bounded wait,
+// on an mbarrier that nothing arrives on and no copy targets, and on expiry records
+// NPFEM_ETIMEOUT (site 90) in the status word like any expired wait of the kernels.
+__global__ void k_wait_selftest(DevStatus *st, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait_for(&bar, 0, limit_ns)) dev_raise(st, DEV_ETIMEOUT, 90);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {

@@ -288,6 +288,8 @@ IterArgs<T> make_args(npfem_ctx *ctx, MeshTypeImpl *t) {
     a.h = t->h;
     a.inv_h = 1.0 / t->h;
     a.c1 = ctx->opt.armijo_c1;
+    a.curv_tol = ctx->opt.curvature_tol;
+    a.curv_tol2 = ctx->opt.curvature_tol * ctx->opt.curvature_tol;
     a.xn = t->xn;
     a.vn = t->vn;
     a.fptr = ctx->d_fslot;
@@ -1325,6 +1327,8 @@ void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
     }
 }
 
+void fill_cells(npfem_ctx *ctx, MeshTypeImpl *t, const MeshTypeImpl *old_t, int cap);
+
 void free_cells(MeshTypeImpl *t) {
     void **bufs[] = {(void **)&t->pub_off, (void **)&t->xn, (void **)&t->vn, &t->yrel, &t->delta, &t->grad, &t->q,
                      &t->z, &t->zp, &t->kcol, &t->ccol, &t->S, &t->Y, &t->rlo, (void **)&t->rlo_lo, (void **)&t->q16, (void **)&t->origin, (void **)&t->rho,
@@ -1333,9 +1337,33 @@ void free_cells(MeshTypeImpl *t) {
     for (void **b : bufs) dfree(*b);
 }
 
-// (Re)allocate the per-cell arrays of a type for `cap` cells, keeping the state.
-void alloc_cells(npfem_ctx *ctx, MeshTypeImpl *t, int cap) {
-    MeshTypeImpl old = *t;
+// (Re)allocate the per-cell arrays of a type for `cap` cells, keeping the state.  Every
+// new array is allocated before the type changes: if one allocation fails, the new
+// ones are freed and the type keeps its old arrays and state.
+void alloc_cells(npfem_ctx *ctx, MeshTypeImpl *cur, int cap) {
+    MeshTypeImpl nt = *cur;
+    void **cell_ptrs[] = {(void **)&nt.pub_off, (void **)&nt.xn, (void **)&nt.vn, &nt.yrel, &nt.delta, &nt.grad,
+                          &nt.q, &nt.z, &nt.zp, &nt.kcol, &nt.ccol, &nt.S, &nt.Y, &nt.rlo, (void **)&nt.rlo_lo,
+                          (void **)&nt.q16, (void **)&nt.origin, (void **)&nt.rho, (void **)&nt.alpha,
+                          (void **)&nt.M, (void **)&nt.g, (void **)&nt.allow, (void **)&nt.hcount,
+                          (void **)&nt.hhead, (void **)&nt.conv, (void **)&nt.fb_list, (void **)&nt.fb_count};
+    for (void **b : cell_ptrs) *b = nullptr;
+    try {
+        fill_cells(ctx, &nt, cur, cap);
+    } catch (...) {
+        cudaStreamSynchronize(ctx->stream);
+        free_cells(&nt);
+        throw;
+    }
+    MeshTypeImpl old = *cur;
+    *cur = nt;
+    free_cells(&old);
+}
+
+// The arrays of alloc_cells for type t (per-cell pointers null on entry), the state
+// of the cells of `old` copied over.
+void fill_cells(npfem_ctx *ctx, MeshTypeImpl *t, const MeshTypeImpl *old_t, int cap) {
+    const MeshTypeImpl &old = *old_t;
     const size_t n3 = 3 * (size_t)t->nVp, es = esize(ctx), m = std::max(1, ctx->opt.history);
     t->pub_off = dalloc<long long>(ctx, cap);
     t->xn = dalloc<double>(ctx, cap * n3);
@@ -1371,7 +1399,6 @@ void alloc_cells(npfem_ctx *ctx, MeshTypeImpl *t, int cap) {
         CK(cudaMemcpyAsync(t->vn, old.vn, old.ncells * n3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     }
-    free_cells(&old);
     if (mixed(ctx)) {
         t->mapQ = make_map(ctx, bf16(ctx) ? (const void *)t->q16 : t->q, bf16(ctx), t->nV, 3ll * cap, t->nVp, tc::BM);
         t->mapR = make_map(ctx, t->rlo, bf16(ctx), t->nV, 3ll * cap, t->nVp, tc::BM);
@@ -1425,6 +1452,7 @@ void npfem_default_options(npfem_options *o) {
     o->autotune_cache = nullptr;
     o->residual_fp64 = 0;
     o->refine_split = 1;
+    o->curvature_tol = 1e-12;
 }
 
 int npfem_create(const npfem_options *opt, npfem_ctx **out) {
@@ -1440,7 +1468,8 @@ int npfem_create(const npfem_options *opt, npfem_ctx **out) {
             o.max_backtracks < 0 || !(o.armijo_c1 > 0 && o.armijo_c1 < 1) || o.refine_max < 0 || !(o.refine_tol > 0) ||
             o.force_median < 0 || o.force_median > 1 || !(o.u_max >= 0) || !std::isfinite(o.u_max) ||
             !(o.pbd_kappa >= 0 && o.pbd_kappa <= 1) || !(o.pik_radius >= 0) || !std::isfinite(o.pik_radius) ||
-            (o.pik_radius > 0 && !(o.collision_k > 0 && std::isfinite(o.collision_k))))
+            (o.pik_radius > 0 && !(o.collision_k > 0 && std::isfinite(o.collision_k))) ||
+            std::isnan(o.curvature_tol))
             fail(ctx, NPFEM_EINVAL, "invalid option value");
         CK(cudaSetDevice(o.device));
         ctx->device = o.device;
@@ -1710,14 +1739,39 @@ int npfem_add_cells(npfem_ctx *ctx, int type_id, int n_cells, const double *x0, 
         if (first_cell) *first_cell = first;
         if (n_cells == 0) return;
         if (t->ncells + n_cells > t->cap) alloc_cells(ctx, t, std::max(t->ncells + n_cells, 2 * t->cap));
-        for (int c = 0; c < n_cells; ++c) t->pub_off_h.push_back(ctx->ndofs + per * c);
-        CK(cudaMemcpyAsync(t->pub_off, t->pub_off_h.data(), t->pub_off_h.size() * sizeof(long long),
-                           cudaMemcpyHostToDevice, ctx->stream));
-        // stage x0 / v0 in the public layout and scatter into SoA
+        // everything the grown context needs is allocated before anything is committed: on a
+        // failure (ENOMEM) the context keeps its cells, sizes and buffers (a grown capacity
+        // holds the same state)
+        const long long ndofs_new = ctx->ndofs + total;
         std::vector<void *> tmp;
-        double *sx = dalloc<double>(ctx, total, &tmp), *sv = dalloc<double>(ctx, total, &tmp);
-        long long *offs = dalloc<long long>(ctx, n_cells, &tmp);
+        std::vector<long long> pub_new = t->pub_off_h;
+        for (int c = 0; c < n_cells; ++c) pub_new.push_back(ctx->ndofs + per * c);
+        double *f_new = nullptr, *stage_new = nullptr, *ffilt_new = nullptr;
         try {
+            f_new = dalloc<double>(ctx, ndofs_new, &tmp);
+            stage_new = dalloc<double>(ctx, ndofs_new, &tmp);
+            if (ctx->opt.force_median) ffilt_new = dalloc<double>(ctx, ndofs_new, &tmp);
+        } catch (...) {
+            cudaStreamSynchronize(ctx->stream);
+            for (void *p : tmp) cudaFree(p);
+            throw;
+        }
+        const std::vector<void *> keep = tmp;     // the new public-layout buffers
+        tmp.clear();
+        auto drop_new = [&] {
+            cudaStreamSynchronize(ctx->stream);
+            for (void *p : keep) cudaFree(p);
+            for (void *p : tmp) cudaFree(p);
+        };
+        // stage x0 / v0 in the public layout and scatter into SoA (beyond the current cells)
+        double *sx = nullptr, *sv = nullptr;
+        long long *offs = nullptr;
+        try {
+            sx = dalloc<double>(ctx, total, &tmp);
+            sv = dalloc<double>(ctx, total, &tmp);
+            offs = dalloc<long long>(ctx, n_cells, &tmp);
+            CK(cudaMemcpyAsync(t->pub_off, pub_new.data(), pub_new.size() * sizeof(long long),
+                               cudaMemcpyHostToDevice, ctx->stream));
             std::vector<long long> lo(n_cells);
             for (int c = 0; c < n_cells; ++c) lo[c] = per * c;
             CK(cudaMemcpyAsync(offs, lo.data(), n_cells * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
@@ -1731,21 +1785,22 @@ int npfem_add_cells(npfem_ctx *ctx, int type_id, int n_cells, const double *x0, 
             CK(cudaGetLastError());
             CK(cudaStreamSynchronize(ctx->stream));
         } catch (...) {
-            for (void *p : tmp) cudaFree(p);
+            drop_new();
             throw;
         }
         for (void *p : tmp) cudaFree(p);
+        // commit: the cells, the public layout and its buffers
+        t->pub_off_h.swap(pub_new);
         t->ncells += n_cells;
-        ctx->ndofs += total;
-        // the public layout grew: re-stage buffers
+        ctx->ndofs = ndofs_new;
         dfree((void *&)ctx->d_f);
         dfree((void *&)ctx->d_stage);
         dfree((void *&)ctx->d_ffilt);
-        ctx->d_f = dalloc<double>(ctx, ctx->ndofs);
-        ctx->d_stage = dalloc<double>(ctx, ctx->ndofs);
-        if (ctx->opt.force_median) ctx->d_ffilt = dalloc<double>(ctx, ctx->ndofs);
-        if (ctx->opt.pik_radius > 0) pik_alloc(ctx);
+        ctx->d_f = f_new;
+        ctx->d_stage = stage_new;
+        ctx->d_ffilt = ffilt_new;
         invalidate_graph(ctx);
+        if (ctx->opt.pik_radius > 0) pik_alloc(ctx);   // on failure the search refuses to run (ESTATE)
     });
 }
 
@@ -1930,6 +1985,15 @@ int npfem_ibm_forces(npfem_ctx *ctx, const npfem_lattice *lat, const double *u_f
                                                                 ctx->d_ibm_area, f_lagr);
         }
         spread();
+        CK(cudaGetLastError());
+    });
+}
+
+int npfem_check_wait(npfem_ctx *ctx, int limit_ms) {
+    if (!ctx) return NPFEM_EINVAL;
+    return guard(ctx, [&] {
+        if (limit_ms < 1 || limit_ms > 2000) fail(ctx, NPFEM_EINVAL, "limit_ms must be in [1, 2000]");
+        tc::k_wait_selftest<<<1, 32, 0, ctx->stream>>>(ctx->d_st, (unsigned long long)limit_ms * 1000000ull);
         CK(cudaGetLastError());
     });
 }

@@ -21,6 +21,7 @@ struct IterArgs {
     int ncells, m, max_bt, last, use_allow, stash_T;
     int pf_dist;                  // k_predict: L2 prefetch of cell + pf_dist (one resident wave ahead), 0: off
     double h, inv_h, c1;
+    double curv_tol, curv_tol2;   // history admits a pair if s.y > curv_tol |s||y| (and its square)
     double *xn, *vn;              // state, FP64 SoA
     const double *const *fptr;    // device slot holding the f_ext base (public layout)
     const long long *pub_off;     // [cell] offset of the cell in the public arrays (doubles)
@@ -484,8 +485,11 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         block_sum_many<T, 2 * MH + 4>(pc, 2 * cnt, 2 * MH, S.pos, out);
         if (threadIdx.x == 0) {
             const double sy = out[2 * MH], ss = out[2 * MH + 1], yy = out[2 * MH + 2], sg = out[2 * MH + 3];
-            // curvature test sy > 1e-12 |s| |y|, squared (no FP64 square roots)
-            const int keep = m > 0 && sy > 0.0 && sy * sy > 1e-24 * ss * yy;
+            // curvature test sy > tol |s| |y|, squared (no FP64 square roots): for tol >= 0 it
+            // needs sy > 0 and sy^2 > tol^2 |s|^2 |y|^2; for tol < 0 a pair with sy <= 0 passes
+            // when sy^2 < tol^2 |s|^2 |y|^2 (tol = -inf: any pair with s, y != 0)
+            const int keep = m > 0 && (a.curv_tol >= 0.0 ? (sy > 0.0 && sy * sy > a.curv_tol2 * ss * yy)
+                                                         : (sy > 0.0 || sy * sy < a.curv_tol2 * ss * yy));
             const double gtv = S.bc->d[3];
             a.g[cell] = gtv;
             a.allow[cell] = S.bc->d[4];

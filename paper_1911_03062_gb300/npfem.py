@@ -40,7 +40,8 @@ class Options(C.Structure):
                 ("refine_max", C.c_int), ("use_graph", C.c_int), ("device", C.c_int),
                 ("cuda_stream", C.c_void_p), ("autotune_cache", C.c_char_p), ("residual_fp64", C.c_int),
                 ("refine_split", C.c_int), ("force_median", C.c_int), ("u_max", C.c_double),
-                ("pbd_kappa", C.c_double), ("pik_radius", C.c_double), ("collision_k", C.c_double)]
+                ("pbd_kappa", C.c_double), ("pik_radius", C.c_double), ("collision_k", C.c_double),
+                ("curvature_tol", C.c_double)]
 
 
 class Lattice(C.Structure):
@@ -104,6 +105,7 @@ def load(path: str = LIB_PATH):
     L.npfem_apply_pinv.argtypes = [vp, ip, vp, vp, ip]
     L.npfem_apply_pinv_noalloc.argtypes = [vp, ip, vp, vp, ip]
     L.npfem_profile.argtypes = [vp, ip]
+    L.npfem_check_wait.argtypes = [vp, ip]
     L.npfem_ibm_forces.argtypes = [vp, C.POINTER(Lattice), vp, C.c_double, ip, vp, vp]
     L.npfem_profile_read.argtypes = [vp, C.POINTER(KernelTimes), ip]
     L.npfem_last_error.argtypes = [vp]
@@ -111,7 +113,7 @@ def load(path: str = LIB_PATH):
     for name in ("npfem_create", "npfem_create_mesh_type", "npfem_add_cells", "npfem_step", "npfem_sync",
                  "npfem_get_positions", "npfem_get_velocities", "npfem_set_state", "npfem_stats",
                  "npfem_apply_pinv", "npfem_apply_pinv_noalloc", "npfem_profile", "npfem_profile_read",
-                 "npfem_ibm_forces"):
+                 "npfem_ibm_forces", "npfem_check_wait"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -123,8 +125,11 @@ def default_options() -> Options:
     return o
 
 
-def _host(a):
+def _host(a, n=None, what="array"):
+    """Contiguous float64 copy (or view) of a host array and its pointer; n: required size."""
     a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"{what} has {a.size} values, expected {n}")
     return a, a.ctypes.data_as(C.c_void_p)
 
 
@@ -132,20 +137,37 @@ def _is_device(a) -> bool:
     return hasattr(a, "is_cuda") and a.is_cuda
 
 
-def _dev_ptr(t):
-    import torch
-    if t.dtype != torch.float64 or not t.is_contiguous():
-        raise ValueError("device arrays must be contiguous float64 CUDA tensors")
+def _dev_ptr(t, device, numel=None, shape=None, what="tensor"):
+    """Pointer of a device tensor after checking what the library will assume of it:
+    a contiguous float64 CUDA tensor on the context's device, of the given size or shape.
+    Raises ValueError before any pointer reaches the library."""
+    if not _is_device(t):
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if str(t.dtype) != "torch.float64" or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous float64 CUDA tensor")
+    if t.device.index != device:
+        raise ValueError(f"{what} is on cuda:{t.device.index}, the context on cuda:{device}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what} has {t.numel()} values, expected {numel}")
     return C.c_void_p(t.data_ptr())
 
 
 class Solver:
-    """One npFEM context: mesh types, cells, and the time step on one GPU."""
+    """One npFEM context: mesh types, cells, and the time step on one GPU.
+
+    Stream order: the context runs on one CUDA stream (``stream``, or a stream this
+    object creates).  Every call that takes caller device tensors first makes that
+    stream wait for the caller's current torch stream (so tensors written there are
+    complete) and afterwards makes the current torch stream wait for the context's
+    stream (so later torch work on those tensors, or their release to the caching
+    allocator, comes after the library's reads and writes)."""
 
     def __init__(self, precision="fp64", iters=10, history=5, armijo_c1=1e-4, max_backtracks=8,
                  refine_tol=1e-6, refine_max=3, use_graph=True, device=0, stream=None, residual_fp64=False,
                  refine_split=True, force_median=False, u_max=0.0, pbd_kappa=0.0, pik_radius=0.0,
-                 collision_k=0.0):
+                 collision_k=0.0, curvature_tol=1e-12, autotune_cache=None):
         self._L = load()
         o = default_options()
         o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -159,18 +181,41 @@ class Solver:
         o.pbd_kappa = float(pbd_kappa)
         o.pik_radius = float(pik_radius)
         o.collision_k = float(collision_k)
+        o.curvature_tol = float(curvature_tol)
+        self._cache_path = None if autotune_cache is None else os.fsencode(autotune_cache)
+        o.autotune_cache = self._cache_path
+        self.device = int(device)
+        self._stream = None
+        import torch
         if stream is not None:
-            o.cuda_stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+            self._stream = stream if hasattr(stream, "cuda_stream") else \
+                torch.cuda.ExternalStream(int(stream), device=torch.device("cuda", self.device))
+        elif torch.cuda.is_available():
+            self._stream = torch.cuda.Stream(device=self.device)
+        if self._stream is not None:
+            o.cuda_stream = C.c_void_p(self._stream.cuda_stream)
         self.precision = o.precision
         self._ctx = C.c_void_p()
         self._check(self._L.npfem_create(C.byref(o), C.byref(self._ctx)), ctx=False)
         self.types = []
 
-    # -- errors ---------------------------------------------------------------
+    # -- errors and stream order ------------------------------------------------
     def _check(self, rc, ctx=True):
         if rc != OK:
             msg = self._L.npfem_last_error(self._ctx if ctx else None).decode()
             raise NpfemError(rc, msg)
+
+    def _torch_stream(self):
+        import torch
+        return torch.cuda.current_stream(self.device)
+
+    def _enter(self):
+        """The context stream waits for the caller's work on the current torch stream."""
+        self._stream.wait_stream(self._torch_stream())
+
+    def _leave(self):
+        """The current torch stream waits for the context stream's work so far."""
+        self._torch_stream().wait_stream(self._stream)
 
     def close(self):
         if getattr(self, "_ctx", None):
@@ -186,11 +231,11 @@ class Solver:
     # -- set-up -----------------------------------------------------------------
     def create_mesh_type(self, rest, tris, k_strain, k_area, k_bend, k_vol, dt, mass=None,
                          rayleigh_alpha=0.0, rayleigh_beta=0.0) -> int:
-        rest, rp = _host(np.asarray(rest).reshape(-1, 3))
+        rest, rp = _host(np.asarray(rest, dtype=np.float64).reshape(-1, 3))
         tris = np.ascontiguousarray(np.asarray(tris).reshape(-1, 3), dtype=np.int32)
         mp = None
         if mass is not None:
-            mass, mp = _host(mass)
+            mass, mp = _host(mass, rest.shape[0], "mass")
         mat = Material(k_strain, k_area, k_bend, k_vol, dt, rayleigh_alpha, rayleigh_beta)
         tid = C.c_int()
         self._check(self._L.npfem_create_mesh_type(self._ctx, rest.shape[0], rp, tris.shape[0],
@@ -206,12 +251,20 @@ class Solver:
                                      m.dt, mtype.mass, getattr(m, "rayleigh_alpha", 0.0),
                                      getattr(m, "rayleigh_beta", 0.0))
 
+    def _nV(self, type_id):
+        if not 0 <= type_id < len(self.types):
+            raise ValueError(f"unknown mesh type {type_id}")
+        return self.types[type_id]
+
     def add_cells(self, type_id, x0, v0=None) -> int:
+        per = 3 * self._nV(type_id)
         x0, xp = _host(x0)
-        n = x0.size // (3 * self.types[type_id])
+        if x0.size % per:
+            raise ValueError(f"x0 has {x0.size} values, not a multiple of 3 nV = {per}")
+        n = x0.size // per
         vp = None
         if v0 is not None:
-            v0, vp = _host(v0)
+            v0, vp = _host(v0, x0.size, "v0")
         first = C.c_int64()
         self._check(self._L.npfem_add_cells(self._ctx, type_id, n, xp, vp, C.byref(first)))
         return first.value
@@ -222,12 +275,16 @@ class Solver:
 
     # -- stepping ---------------------------------------------------------------
     def step(self, f_ext):
+        """One time step under f_ext (num_dofs values): a host array (copied during the
+        call) or a device tensor read on the context's stream after the caller's
+        current-stream work; the call returns once the step is enqueued."""
         if _is_device(f_ext):
-            self._check(self._L.npfem_step(self._ctx, _dev_ptr(f_ext), 1))
+            p = _dev_ptr(f_ext, self.device, numel=self.num_dofs, what="f_ext")
+            self._enter()
+            self._check(self._L.npfem_step(self._ctx, p, 1))
+            self._leave()
         else:
-            f, fp = _host(f_ext)
-            if f.size != self.num_dofs:
-                raise ValueError(f"f_ext has {f.size} values, expected {self.num_dofs}")
+            f, fp = _host(f_ext, self.num_dofs, "f_ext")
             self._check(self._L.npfem_step(self._ctx, fp, 0))
 
     def sync(self):
@@ -236,11 +293,17 @@ class Solver:
     def _get(self, fn, out):
         n = self.num_dofs
         if out is not None and _is_device(out):
-            self._check(fn(self._ctx, _dev_ptr(out), n, 1))
+            p = _dev_ptr(out, self.device, numel=n, what="out")
+            self._enter()
+            self._check(fn(self._ctx, p, n, 1))
+            self._leave()
             return out
         if out is None:
             out = np.empty(n)
-        self._check(fn(self._ctx, out.ctypes.data_as(C.c_void_p), n, 0))
+        if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+                and out.size == n):
+            raise ValueError(f"out must be a contiguous float64 numpy array or CUDA tensor of {n} values")
+        self._check(fn(self._ctx, out.ctypes.data_as(C.c_void_p), out.size, 0))
         return out
 
     def positions(self, out=None):
@@ -250,10 +313,10 @@ class Solver:
         return self._get(self._L.npfem_get_velocities, out)
 
     def set_state(self, x, v=None):
-        x, xp = _host(x)
+        x, xp = _host(x, self.num_dofs, "x")
         vp = None
         if v is not None:
-            v, vp = _host(v)
+            v, vp = _host(v, x.size, "v")
         self._check(self._L.npfem_set_state(self._ctx, xp, vp, x.size))
 
     def stats(self) -> dict:
@@ -261,10 +324,30 @@ class Solver:
         self._check(self._L.npfem_stats(self._ctx, C.byref(s)))
         return {k: getattr(s, k) for k, _ in StepStats._fields_}
 
+    def _apply_args(self, type_id, q, z):
+        nV = self._nV(type_id)
+        if getattr(q, "dim", lambda: 0)() != 2:
+            raise ValueError("q must be a 2-D [n_cols, nV] tensor")
+        shape = (q.shape[0], nV)
+        pq = _dev_ptr(q, self.device, shape=shape, what="q")
+        pz = _dev_ptr(z, self.device, shape=shape, what="z")
+        return pq, pz, q.shape[0]
+
+    def apply_pinv(self, type_id, q, z):
+        """z = P^{-1} q on the device (float64 CUDA tensors [n_cols, nV]); returns z,
+        complete on the caller's current stream."""
+        pq, pz, n_cols = self._apply_args(type_id, q, z)
+        self._enter()
+        self._check(self._L.npfem_apply_pinv(self._ctx, type_id, pq, pz, n_cols))
+        self._leave()
+        return z
+
     def apply_pinv_noalloc(self, type_id, q, z):
         """As apply_pinv, with the library's static scratch instead of allocations."""
-        n_cols = q.shape[0]
-        self._check(self._L.npfem_apply_pinv_noalloc(self._ctx, type_id, _dev_ptr(q), _dev_ptr(z), n_cols))
+        pq, pz, n_cols = self._apply_args(type_id, q, z)
+        self._enter()
+        self._check(self._L.npfem_apply_pinv_noalloc(self._ctx, type_id, pq, pz, n_cols))
+        self._leave()
         return z
 
     def ibm_forces(self, u, origin, dx, dt, cycles=1, f_lagr=None, f_grid=None):
@@ -273,20 +356,27 @@ class Solver:
         Returns (f_lagr [num_dofs], f_grid like u), both device tensors, after the
         context's stream has finished them (the call synchronises it)."""
         import torch
-        if u.dim() != 4 or u.shape[0] != 3:
-            raise ValueError("u must be [3, nz, ny, nx]")
+        if not _is_device(u) or u.dim() != 4 or u.shape[0] != 3:
+            raise ValueError("u must be a [3, nz, ny, nx] CUDA tensor")
         _, nz, ny, nx = u.shape
         if f_lagr is None:
             f_lagr = torch.empty(self.num_dofs, dtype=torch.float64, device=u.device)
         if f_grid is None:
             f_grid = torch.empty_like(u)
-        if f_lagr.numel() != self.num_dofs or tuple(f_grid.shape) != tuple(u.shape):
-            raise ValueError("f_lagr must hold num_dofs values and f_grid the shape of u")
+        pu = _dev_ptr(u, self.device, what="u")
+        pl = _dev_ptr(f_lagr, self.device, numel=self.num_dofs, what="f_lagr")
+        pg = _dev_ptr(f_grid, self.device, shape=tuple(u.shape), what="f_grid")
         lat = Lattice(nx, ny, nz, float(dx), float(origin[0]), float(origin[1]), float(origin[2]))
-        self._check(self._L.npfem_ibm_forces(self._ctx, C.byref(lat), _dev_ptr(u), float(dt), int(cycles),
-                                             _dev_ptr(f_lagr), _dev_ptr(f_grid)))
+        self._enter()
+        self._check(self._L.npfem_ibm_forces(self._ctx, C.byref(lat), pu, float(dt), int(cycles), pl, pg))
         self._check(self._L.npfem_sync(self._ctx))
+        self._leave()
         return f_lagr, f_grid
+
+    def check_wait(self, limit_ms=50):
+        """Enqueue the failure-path self-check: a bounded device wait that expires; the
+        next synchronising call raises NpfemError(ETIMEOUT)."""
+        self._check(self._L.npfem_check_wait(self._ctx, int(limit_ms)))
 
     def profile(self, enable: bool):
         self._check(self._L.npfem_profile(self._ctx, int(bool(enable))))
@@ -295,9 +385,3 @@ class Solver:
         k = KernelTimes()
         self._check(self._L.npfem_profile_read(self._ctx, C.byref(k), int(bool(reset))))
         return {n: (k.ms[i], k.launches[i]) for i, n in enumerate(KCLASSES) if k.launches[i]}
-
-    def apply_pinv(self, type_id, q, z):
-        """z = P^{-1} q on the device (torch float64 tensors, [n_cols, nV])."""
-        n_cols = q.shape[0]
-        self._check(self._L.npfem_apply_pinv(self._ctx, type_id, _dev_ptr(q), _dev_ptr(z), n_cols))
-        return z

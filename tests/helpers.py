@@ -95,3 +95,31 @@ def one_step_parity(groups, steps_before, sample, precision="fp64", **opts):
         xo, _ = T.step_cells(xn[gi][idx].copy(), vn[gi][idx].copy(), g.f_ext[idx], K=10, m=5, threads=4)
         err = max(err, float(np.linalg.norm(x1[gi][idx] - xo, axis=2).max() / g.mtype.radius))
     return err, st
+
+
+def branch_cell(seed=5, dt=0.05, mirror=False):
+    """A level-1 RBC (42 vertices) at dt = 0.05, where the inertia term no longer
+    dominates and the quasi-Newton iterations stay far from convergence for K > 15,
+    in a deformed state with velocities and forces.  mirror: the cell inside out
+    (large non-convex projections; seed 23 gives one negative-curvature pair).
+    Returns (MeshType, x_n, v_n, f_ext), each array [nV, 3]."""
+    unit, tris = I.icosphere(1)
+    rest = I.rbc_shape(unit)
+    mt = I.MeshType("rbc-l1", rest, tris, I.Material(1.0, 5.0, 0.5, 10.0, dt), I.RBC_R0)
+    rng = np.random.default_rng(seed)
+    if mirror:
+        xn = rest * np.array([1, 1, -1]) + 0.1 * rng.standard_normal(rest.shape)
+    else:
+        R = I.random_rotations(np.random.default_rng(seed), 1)[0]
+        xn = rest @ R.T + 0.3 * rng.standard_normal(rest.shape)
+    vn = rng.standard_normal(rest.shape)
+    f = rng.standard_normal(rest.shape)
+    return mt, xn, vn, f
+
+
+def group_of(mt, x0, v0, f):
+    """A Group holding the given cells ([n, nV, 3] arrays, or one [nV, 3] cell)."""
+    x0, v0, f = (np.asarray(a, dtype=np.float64).reshape(-1, mt.nV, 3) for a in (x0, v0, f))
+    g = I.Group(mt, x0.shape[0], seed=0)
+    g.x0, g.v0, g.f_ext = x0.copy(), v0.copy(), f.copy()
+    return g

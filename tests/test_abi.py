@@ -68,3 +68,69 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+class _FakeCuda:
+    """Stands in for a CUDA tensor (no GPU here): what the binding's checks read."""
+    is_cuda = True
+
+    def __init__(self, shape, dtype="torch.float64", device=0, contiguous=True):
+        import types
+        self.shape, self.dtype, self._c = tuple(shape), dtype, contiguous
+        self.device = types.SimpleNamespace(index=device)
+
+    def is_contiguous(self):
+        return self._c
+
+    def numel(self):
+        import numpy as np
+        return int(np.prod(self.shape))
+
+    def dim(self):
+        return len(self.shape)
+
+    def data_ptr(self):
+        return 0
+
+
+def test_binding_checks_device_arguments_before_the_library():
+    import numpy as np
+    import torch
+    F = _FakeCuda
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        N._dev_ptr(torch.zeros(4, dtype=torch.float64), 0)
+    for bad in (F((4,), dtype="torch.float32"), F((4,), contiguous=False), F((4,), device=1)):
+        with pytest.raises(ValueError):
+            N._dev_ptr(bad, 0, numel=4)
+    with pytest.raises(ValueError):
+        N._dev_ptr(F((5,)), 0, numel=4)
+    with pytest.raises(ValueError):
+        N._dev_ptr(F((3, 4)), 0, shape=(3, 5))
+    assert N._dev_ptr(F((3, 4)), 0, shape=(3, 4)).value is None      # accepted (null pointer of the fake)
+    with pytest.raises(ValueError):
+        N._host(np.zeros(5), 6, "f_ext")
+    # the Solver's own checks, without a context: apply shapes and type ids, step sizes
+    s = N.Solver.__new__(N.Solver)
+    s.device, s.types = 0, [642]
+
+    class _Lib:
+        @staticmethod
+        def npfem_num_dofs(ctx):
+            return 3 * 642
+    s._L, s._ctx = _Lib(), None
+    with pytest.raises(ValueError):
+        s._apply_args(0, F((6, 641)), F((6, 641)))
+    with pytest.raises(ValueError):
+        s._apply_args(0, F((6, 642)), F((5, 642)))
+    with pytest.raises(ValueError):
+        s._apply_args(1, F((6, 642)), F((6, 642)))
+    with pytest.raises(ValueError):
+        s._apply_args(0, F((6 * 642,)), F((6 * 642,)))
+    with pytest.raises(ValueError):
+        s.step(F((3 * 642 + 3,)))
+    with pytest.raises(ValueError):
+        s.step(np.zeros(3 * 642 - 1))
+    with pytest.raises(ValueError):
+        s.add_cells(0, np.zeros(3 * 642 + 1))
+    with pytest.raises(ValueError):
+        s.add_cells(0, np.zeros(3 * 642), np.zeros(3))

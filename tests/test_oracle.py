@@ -422,18 +422,11 @@ def test_tetrahedron_matches_brute_force_newton(O):
 
 def slow_cell(O, seed=5, dt=0.05, mirror=False):
     """A level-1 RBC at dt = 0.05 (inertia no longer dominant, so the iterations stay
-    far from convergence for K > 15) in a deformed state with velocities and forces."""
-    unit, tris = I.icosphere(1)
-    rest = I.rbc_shape(unit)
-    T = O.OracleType(rest, tris, k_strain=1.0, k_area=5.0, k_bend=0.5, k_vol=10.0, dt=dt)
-    rng = np.random.default_rng(seed)
-    if mirror:        # inside out: large non-convex projections, a negative-curvature pair
-        xn = rest * np.array([1, 1, -1]) + 0.1 * rng.standard_normal(rest.shape)
-    else:
-        xn = rest @ rot(seed).T + 0.3 * rng.standard_normal(rest.shape)
-    vn = rng.standard_normal(rest.shape)
-    f = rng.standard_normal(rest.shape)
-    return T, xn, vn, f
+    far from convergence for K > 15) in a deformed state with velocities and forces;
+    mirror: inside out (large non-convex projections, a negative-curvature pair)."""
+    from helpers import branch_cell
+    mt, xn, vn, f = branch_cell(seed, dt, mirror)
+    return O.OracleType.from_mesh_type(mt), xn, vn, f
 
 
 def bfgs_directions(T, tr, m, curv_tol=1e-12):
