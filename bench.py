@@ -193,6 +193,68 @@ def oracle_step_sampled(groups, xn, vn, args, K=10):
     return out
 
 
+# ---------------------------------------------------------------- peaks
+def measure_peaks(local):
+    """Arithmetic peaks the roofline needs beyond MEASURED_PEAKS.json: FP32 FMA and
+    FP64 FMA on the SIMT pipes (libnpfem_peaks.so probes: 16 independent FMA chains
+    per thread, 8 blocks of 256 threads per SM), and TF32 / BF16 dense tensor
+    throughput through cuBLAS (torch.matmul, 8192^3).  Each figure is the best of
+    several launches timed with CUDA events; SM clocks are sampled meanwhile."""
+    import ctypes
+    import torch
+    from paper_1911_03062_gb300 import build as B
+    B.build()
+    L = ctypes.CDLL(B.PEAKS_LIB)
+    L.npfem_peak_fma.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    L.npfem_peak_fma.restype = ctypes.c_double
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    blocks = 8 * nsm
+    clocks = Clocks(local)
+    clocks.start()
+    out = {}
+
+    def timed(fn, reps):
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            work = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        return work, best
+
+    buf = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    for name, fp64, iters in (("fp32_fma_tflops", 0, 20000), ("fp64_fma_tflops", 1, 200)):
+        run = lambda it: L.npfem_peak_fma(fp64, ctypes.c_void_p(stream.cuda_stream), blocks, it,
+                                          ctypes.c_void_p(buf.data_ptr()))
+        _, t = timed(lambda: run(iters), 2)                 # calibrate to ~0.2 s per launch
+        iters = max(1, int(iters * 0.2 / t))
+        flops, t = timed(lambda: run(iters), 5)
+        if flops < 0:
+            raise RuntimeError("peak probe launch failed")
+        out[name] = flops / t / 1e12
+    n = 8192
+    with torch.cuda.stream(stream):
+        for name, dt, tf32 in (("tf32_tensor_tflops", torch.float32, True), ("bf16_tensor_tflops", torch.bfloat16, False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device="cuda", dtype=dt)
+            b = torch.randn(n, n, device="cuda", dtype=dt)
+            c = torch.empty(n, n, device="cuda", dtype=dt)
+            _, t = timed(lambda: torch.matmul(a, b, out=c), 10)
+            out[name] = 2.0 * n ** 3 / t / 1e12
+            del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = False
+    clk = clocks.stop()
+    line = {"peaks": out, "clocks": clk, "gpu": torch.cuda.get_device_name(local), "sms": nsm,
+            "how": "FMA probes: 16 FMA chains/thread, 8x256 threads/SM, best of 5 (CUDA events); "
+                   "tensor: torch.matmul 8192^3 (cuBLAS), best of 10"}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- reference
 def run_reference(args, workload):
     """The FP64 CPU oracle timed on the host cores (the reference arm)."""
@@ -271,10 +333,17 @@ def main():
     ap.add_argument("--rayleigh-alpha", type=float, default=0.0, help="Rayleigh damping C = alpha M + beta L")
     ap.add_argument("--rayleigh-beta", type=float, default=0.0, help="(the paper's table: alpha 0, beta 0.01)")
     ap.add_argument("--pik-radius", type=float, default=0.0, help="particle-in-kernel collision kernel radius (0: off)")
-    ap.add_argument("--collision-k", type=float, default=200.0, help="collision stiffness (with --pik-radius)")
+    ap.add_argument("--collision-k", type=float, default=2.0,
+                    help="collision stiffness (with --pik-radius; at 200 the BF16 form misses 1e-6 in deep overlaps)")
     ap.add_argument("--ibm-cycles", type=int, default=0, help="also time the immersed-boundary forces (0: skip)")
+    ap.add_argument("--peaks", action="store_true", help="measure FP32/FP64 FMA and TF32/BF16 tensor peaks, exit")
     args = ap.parse_args()
     rank, world, local = env_rank()
+
+    if args.peaks:
+        if rank == 0:
+            measure_peaks(local)
+        return
 
     if args.impl == "reference":
         if rank == 0:
@@ -285,6 +354,7 @@ def main():
     from paper_1911_03062_gb300 import inputs as I
     from paper_1911_03062_gb300.npfem import Solver
     from paper_1911_03062_gb300 import build as B
+    from paper_1911_03062_gb300.shard import shard_groups
     B.build()
 
     torch.cuda.set_device(local)
@@ -306,10 +376,9 @@ def main():
 
     wl = I.WORKLOADS[args.workload]
     precision = args.precision or wl["precision"]
-    groups = with_damping(I.workload_groups(args.workload), args.rayleigh_alpha, args.rayleigh_beta)
-    for g in groups:
-        g.seed += 7919 * rank           # each rank steps its own suspension
-        I.materialise(g)
+    # each rank steps its own suspension (weak scaling; the partition of shard.py)
+    groups = with_damping(shard_groups(args.workload, rank, world, "weak"), args.rayleigh_alpha,
+                          args.rayleigh_beta)
     ncells = sum(g.n_cells for g in groups)
     K = 10
     f_host = np.concatenate([g.f_ext.ravel() for g in groups])
@@ -538,6 +607,20 @@ def main():
                 "frac": ach / hbm, "traffic": None, "peak_source": peak_src}
     kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / total_ms if total_ms else None}
                for k, v in names.items()}
+    # the global step's first apply (grouped tensor-core launch, all types): bytes of its
+    # operand streams (read q, write z; P^{-1} stays in L2) and its flops, per launch
+    roof_gemm = None
+    if "gemm" in prof and precision != "fp64":
+        byts = sum(algorithmic_gemm(g.mtype.nV, g.n_cells, bf16)[0] for g in groups)
+        flops = sum(algorithmic_gemm(g.mtype.nV, g.n_cells, bf16)[1] for g in groups)
+        avg_s = prof["gemm"][0] / prof["gemm"][1] / 1e3
+        tpeak = bf_sust if bf16 else bf_sust / 2.0
+        roof_gemm = {"kernel": "k_gemm_grouped (first apply)", "bound": "hbm",
+                     "achieved_gbs": byts / avg_s / 1e9, "hbm_frac": byts / avg_s / 1e9 / hbm,
+                     "achieved_tflops": flops / avg_s / 1e12, "tensor_peak_tflops": tpeak,
+                     "tensor_frac": flops / avg_s / 1e12 / tpeak, "ms_per_launch": avg_s * 1e3,
+                     "peak_source": peak_src + (" (BF16 sustained)" if bf16 else
+                                                " (TF32 = BF16 sustained x nominal 1/2)")}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
@@ -552,7 +635,7 @@ def main():
                        "rayleigh_alpha": args.rayleigh_alpha, "rayleigh_beta": args.rayleigh_beta,
                        "pik_radius": args.pik_radius, "collision_k": args.collision_k if args.pik_radius > 0 else 0.0},
             "clocks": clk, "gpu_launches": launches, "parity": parity, "fp64_gpu": fp64, "e2e": e2e,
-            "roofline": roof, "kernels": kernels, "solver": solver}
+            "roofline": roof, "roofline_gemm": roof_gemm, "kernels": kernels, "solver": solver}
     if ibm:
         line["ibm"] = ibm
     if not args.no_cpu:

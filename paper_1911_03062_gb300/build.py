@@ -1,7 +1,8 @@
 """Build libnpfem.so (the C-ABI CUDA library) in-tree for sm_103a.
 
 Plain nvcc, no cmake: the translation units are compiled in parallel and
-linked into ``paper_1911_03062_gb300/libnpfem.so``.
+linked into ``paper_1911_03062_gb300/libnpfem.so``; the arithmetic-throughput
+probes of the benchmark's peaks leg go into ``libnpfem_peaks.so``.
 """
 from __future__ import annotations
 
@@ -15,11 +16,13 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libnpfem.so")
+PEAKS_LIB = os.path.join(HERE, "libnpfem_peaks.so")
 BUILD = os.path.join(ROOT, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-prec-div=false", "-prec-sqrt=false", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 SOURCES = ["npfem.cu"]
+PEAKS_SOURCES = ["peaks.cu"]
 
 
 def nvcc() -> str:
@@ -36,7 +39,8 @@ def _deps():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
+    dep = _deps()
+    if not force and all(os.path.exists(p) and os.path.getmtime(p) >= dep for p in (LIB, PEAKS_LIB)):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -49,11 +53,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         subprocess.check_call(cmd)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=max(1, len(SOURCES))) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
+    srcs = SOURCES + PEAKS_SOURCES
+    with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+        objs = list(ex.map(compile_one, srcs))
+    for lib, o in ((LIB, objs[:len(SOURCES)]), (PEAKS_LIB, objs[len(SOURCES):])):
+        tmp = lib + f".{os.getpid()}.tmp"
+        subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *o])
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -389,9 +389,12 @@ __device__ __forceinline__ void hinge_local(const T *pos, const T *__restrict__ 
     }
 }
 
-// Signed volume of the current positions in pos (relative to vertex 0), partial per thread.
+// Signed volume (x 6) of the current positions in pos (relative to vertex 0): this
+// thread's partial sum over its triangles (plain arithmetic of T; the block combines
+// the partials in float-float / FP64).
 template <typename T>
-__device__ __forceinline__ void volume_pass(const TypeConst<T> &tc, const T *pos, int nVp, Acc<T> &aV) {
+__device__ __forceinline__ T volume_pass(const TypeConst<T> &tc, const T *pos, int nVp) {
+    T aV = T(0);
     const T o0 = pos[0], o1 = pos[nVp], o2 = pos[2 * nVp];
     int4 tv_n = threadIdx.x < tc.nT ? __ldg(tc.tri + threadIdx.x) : make_int4(0, 0, 0, 0);
     for (int t = threadIdx.x; t < tc.nT; t += blockDim.x) {
@@ -400,8 +403,9 @@ __device__ __forceinline__ void volume_pass(const TypeConst<T> &tc, const T *pos
         T ax = pos[tv.x] - o0, ay = pos[nVp + tv.x] - o1, az = pos[2 * nVp + tv.x] - o2;
         T e1x = pos[tv.y] - pos[tv.x], e1y = pos[nVp + tv.y] - pos[nVp + tv.x], e1z = pos[2 * nVp + tv.y] - pos[2 * nVp + tv.x];
         T e2x = pos[tv.z] - pos[tv.x], e2y = pos[nVp + tv.z] - pos[nVp + tv.x], e2z = pos[2 * nVp + tv.z] - pos[2 * nVp + tv.x];
-        aV.add(ax * (e1y * e2z - e1z * e2y) + ay * (e1z * e2x - e1x * e2z) + az * (e1x * e2y - e1y * e2x));
+        aV += ax * (e1y * e2z - e1z * e2y) + ay * (e1z * e2x - e1x * e2z) + az * (e1x * e2y - e1y * e2x);
     }
+    return aV;
 }
 
 // PIK collision term of one cell: kc[v] (0: no contact) and c = p - y ([3][nVp]);
@@ -414,13 +418,18 @@ struct Contact {
 
 // -------------------------------------------------------- the local step
 // dt: this thread's elements of delta (x = y_rel + delta); gr receives the
-// gradient.  After the final reduction thread 0 calls done(g, allow) with
-// g(x) and the rounding-error bound of g for the FP32 path
-// (8 u sum_i w_i |A_i x - p_i| |A_i x| + u * inertia); done writes what the
-// caller needs into S.bc before the closing barrier.
+// gradient.  After the final reduction thread 0 calls done(g, allow, extra)
+// with g(x), the rounding-error bound of g for the FP32 path
+// (8 u sum_i w_i |A_i x - p_i| |A_i x| + u * inertia) and the block sum of the
+// callers' `extra` partials (reduced with the energy, e.g. a dot product the
+// caller needs at the same barrier); done writes what the caller needs into
+// S.bc before the closing barrier.
+// Per-thread partial sums (energy, volume, |gV|^2, the Gauss-Newton dots) are
+// plain arithmetic of T over the thread's few terms; the block combines them in
+// float-float (FP32 path) or FP64.
 template <typename T, int EPT, typename Done>
 __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, const Contact<T> &ct,
-                           const T (&dt)[EPT], T (&gr)[EPT], const Smem<T> &S, int stash_T, Done &&done) {
+                           const T (&dt)[EPT], T (&gr)[EPT], const Smem<T> &S, int stash_T, T extra, Done &&done) {
     const int B = blockDim.x, tid = threadIdx.x;
     const int nVp = tc.nVp, nV = tc.nV, n3 = 3 * nVp;
     T *pos = S.pos, *gsh = S.gsh, *gva = S.gva, *stash = S.stash;
@@ -471,9 +480,7 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
         for (int i = 0; i < 4; ++i) x[4 * g4 + i] = xv[i];
     }
     __syncthreads();
-    Acc<T> aV, ag2;      // signed 6V of x; |gV(x)|^2 (over the vertices this thread gathers)
-    aV.zero();
-    ag2.zero();
+    T aV = T(0), ag2 = T(0);   // signed 6V of x; |gV(x)|^2 (over the vertices this thread gathers)
     const T o[3] = {pos[0], pos[nVp], pos[2 * nVp]};
     // 2. triangles (strain + area, the volume of x and its gradient), chunked through the stash
     {
@@ -487,7 +494,7 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                 ld4(tc.dinv + 4 * t, Di);
                 ld2(tc.wtri + 2 * t, w);
                 T R[6], N[3];
-                aV.add(tri_local(pos, yrel, nVp, tv, Di, w[0], w[1], tc.cd, o, R, N, en, al));
+                aV += tri_local(pos, yrel, nVp, tv, Di, w[0], w[1], tc.cd, o, R, N, en, al);
                 T *st = stash + 9 * (t - t0);
 #pragma unroll
                 for (int i = 0; i < 6; ++i) st[i] = R[i];
@@ -524,9 +531,9 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                     gva[v] = n0;                        // single chunk: the complete gradient
                     gva[nVp + v] = n1;
                     gva[2 * nVp + v] = n2;
-                    ag2.add_prod(n0, n0);
-                    ag2.add_prod(n1, n1);
-                    ag2.add_prod(n2, n2);
+                    ag2 = fma(n0, n0, ag2);
+                    ag2 = fma(n1, n1, ag2);
+                    ag2 = fma(n2, n2, ag2);
                 }
                 __syncthreads();
                 continue;
@@ -551,9 +558,9 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                 gsh[2 * nVp + v] += g2;
                 const T f0 = (gva[v] += n0), f1 = (gva[nVp + v] += n1), f2 = (gva[2 * nVp + v] += n2);
                 if (t1 == tc.nT) {                      // last chunk: the complete gradient
-                    ag2.add_prod(f0, f0);
-                    ag2.add_prod(f1, f1);
-                    ag2.add_prod(f2, f2);
+                    ag2 = fma(f0, f0, ag2);
+                    ag2 = fma(f1, f1, ag2);
+                    ag2 = fma(f2, f2, ag2);
                 }
             }
             __syncthreads();
@@ -568,7 +575,11 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
         S.bc->t[0] = T(r6) / T(6.0 * s[1]);                 // p_0 = x: gV.(x - p_0) = 0
     };
     {
-        Acc<T> a1[2] = {aV, ag2};
+        Acc<T> a1[2];
+        a1[0].zero();
+        a1[1].zero();
+        a1[0].add(aV);
+        a1[1].add(ag2);
         warp_partials_store<T, 2>(a1, S.red);
     }
     // 3. hinges (bending), chunked through the stash
@@ -680,9 +691,7 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                     gV[2 * nVp + v] = g[2] / T(6);
                 }
                 __syncthreads();
-                Acc<T> a2[2];
-                a2[0].zero();
-                a2[1].zero();
+                T qg2 = T(0), qd = T(0);
 #pragma unroll
                 for (int g4 = 0; g4 < EPT / 4; ++g4) {
                     const int e0 = 4 * (tid + g4 * B);
@@ -694,10 +703,15 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         if (v0 + i >= nV) continue;
-                        a2[0].add_prod(gv[i], gv[i]);
-                        a2[1].add_prod(gv[i], x[4 * g4 + i] - p[4 * g4 + i]);
+                        qg2 = fma(gv[i], gv[i], qg2);
+                        qd = fma(gv[i], x[4 * g4 + i] - p[4 * g4 + i], qd);
                     }
                 }
+                Acc<T> a2[2];
+                a2[0].zero();
+                a2[1].zero();
+                a2[0].add(qg2);
+                a2[1].add(qd);
                 block_reduce_t0<T, 2>(a2, S.red, [&](const double *s) {
                     S.bc->t[0] = T(tc.V0x6 - S.bc->d[0] - 6.0 * s[1]) / T(6.0 * s[0]);
                 });
@@ -722,7 +736,7 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
             __syncthreads();
             Acc<T> a3[1];
             a3[0].zero();
-            volume_pass(tc, pos, nVp, a3[0]);
+            a3[0].add(volume_pass(tc, pos, nVp));
             block_reduce_t0<T, 1>(a3, S.red, [&](const double *s) {
                 S.bc->d[0] = s[0];
                 S.bc->i[0] = fabs(tc.V0x6 - s[0]) <= tc.vtol6 || it == 7;
@@ -750,12 +764,14 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
             gr[j] = gs[i] + tc.kv * r;
         }
     }
-    Acc<T> fin[2];
+    Acc<T> fin[3];
     fin[0].zero();
     fin[1].zero();
+    fin[2].zero();
     fin[0].add(en);
     fin[1].add(al);
-    block_reduce_t0<T, 2>(fin, S.red, [&](const double *s) { done(s[0], 8.0 * Prec<T>::round_unit * s[1]); });
+    fin[2].add(extra);
+    block_reduce_t0<T, 3>(fin, S.red, [&](const double *s) { done(s[0], 8.0 * Prec<T>::round_unit * s[1], s[2]); });
 }
 
 }  // namespace npfem

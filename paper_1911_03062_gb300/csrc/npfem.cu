@@ -78,8 +78,9 @@ struct MeshTypeImpl {
     unsigned short *ell_col = nullptr;
     float *ell_val = nullptr;
     int ell_W = 0, ell_KR = 0, ell_nt = 0, ell_grid = 0;
-    // tensor-core GEMM configuration
+    // tensor-core GEMM configuration and the right-hand-side row count it was tuned for
     int n_tile = 0, stages = 0;
+    long long tuned_rows = 0;
     CUtensorMap mapP{}, mapPlo{}, mapM{}, mapMlo{};
     // cells
     int ncells = 0, cap = 0;
@@ -1189,17 +1190,23 @@ struct InvCopies {
 InvCopies invert_on_gpu(npfem_ctx *ctx, MeshTypeImpl *t, const std::vector<double> &P, bool want64, bool want_lo,
                         const char *what) {
     InvCopies out;
-    const int n = t->nV;
+    const int n = t->nV, nb = (n + GJB - 1) / GJB, npad = nb * GJB;
     std::vector<void *> tmp;
-    double *A = dalloc<double>(ctx, (size_t)n * n, &tmp);
-    double *rowk = dalloc<double>(ctx, n, &tmp), *colk = dalloc<double>(ctx, n, &tmp);
-    int *bad = dalloc<int>(ctx, 1, &tmp);
     try {
-        CK(cudaMemcpyAsync(A, P.data(), (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-        const int g1 = grid_for(n, 256), g2 = grid_for((long long)n * n, 256, 4 * ctx->nsm);
-        for (int k = 0; k < n; ++k) {
-            k_gj_prep<<<g1, 256, 0, ctx->stream>>>(n, k, A, rowk, colk, bad);
-            k_gj_update<<<g2, 256, 0, ctx->stream>>>(n, k, A, rowk, colk, bad);
+        // P padded to a multiple of the pivot block with the identity (its inverse is
+        // blockdiag(P^{-1}, I)), then blocked Gauss-Jordan: 2 launches per GJB pivots
+        std::vector<double> Ap((size_t)npad * npad, 0.0);
+        for (int i = 0; i < npad; ++i)
+            for (int j = 0; j < npad; ++j)
+                Ap[(size_t)i * npad + j] = (i < n && j < n) ? P[(size_t)i * n + j] : (i == j ? 1.0 : 0.0);
+        double *A = dalloc<double>(ctx, (size_t)npad * npad, &tmp);
+        double *D = dalloc<double>(ctx, GJB * GJB, &tmp);
+        double *C = dalloc<double>(ctx, (size_t)npad * GJB, &tmp), *DR = dalloc<double>(ctx, (size_t)npad * GJB, &tmp);
+        int *bad = dalloc<int>(ctx, 1, &tmp);
+        CK(cudaMemcpyAsync(A, Ap.data(), Ap.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        for (int kb = 0; kb < nb; ++kb) {
+            k_bgj_panel<<<nb, 256, 0, ctx->stream>>>(npad, kb, A, D, C, DR, bad);
+            k_bgj_update<<<dim3(nb, nb), 256, 0, ctx->stream>>>(npad, kb, A, D, C, DR, bad);
         }
         CK(cudaGetLastError());
         int hbad = 0;
@@ -1211,7 +1218,7 @@ InvCopies invert_on_gpu(npfem_ctx *ctx, MeshTypeImpl *t, const std::vector<doubl
         if (bf16(ctx)) out.i16 = dalloc<__nv_bfloat16>(ctx, (size_t)n * t->nVp, &t->owned);
         if (bf16(ctx) && want_lo) out.i16lo = dalloc<__nv_bfloat16>(ctx, (size_t)n * t->nVp, &t->owned);
         if (mixed(ctx) && !bf16(ctx) && want_lo) out.i32lo = dalloc<float>(ctx, (size_t)n * t->nVp, &t->owned);
-        k_convert_pinv<<<grid_for((long long)n * t->nVp, 256, 4096), 256, 0, ctx->stream>>>(n, t->nVp, A, out.i64,
+        k_convert_pinv<<<grid_for((long long)n * t->nVp, 256, 4096), 256, 0, ctx->stream>>>(n, npad, t->nVp, A, out.i64,
                                                                                           out.i32, out.i16,
                                                                                           out.i16lo, out.i32lo);
         CK(cudaGetLastError());
@@ -1224,27 +1231,42 @@ InvCopies invert_on_gpu(npfem_ctx *ctx, MeshTypeImpl *t, const std::vector<doubl
     return out;
 }
 
-// GEMM tile autotuner: for each (device, nV, operand type) time the grouped
-// tensor-core apply on 24576 right-hand-side rows for the N-tile widths that
-// cover nV with the fewest (and one more) tiles and 2..6 pipeline stages, and
-// keep the fastest.  Results are cached per process and, when
-// npfem_options.autotune_cache names a file, read from / appended to it
-// ("key n_tile stages microseconds" lines).
+// GEMM tile autotuner: for each (device, nV, operand type, right-hand-side row
+// bucket) time the grouped tensor-core apply for the N-tile widths that cover nV
+// with the fewest (and one more) tiles and 2..6 pipeline stages, on operands
+// filled with non-zero values, and keep the fastest.  The bucket is the type's
+// row count 3 x cells rounded up to a power of two (at least 3 x 1024); a type is
+// tuned at creation for 3 x 8192 rows and again, with its real row count, by the
+// first step after its cell count changed bucket (before that step's graph is
+// captured).  Timing runs on min(bucket, 3 x 32768) rows.  The grid is not a
+// search dimension: every block holds both 256-column TMEM accumulators (512
+// columns, the whole TMEM of an SM), so one block per SM, persistent over the
+// units, is the only shape that runs all SMs concurrently.  Results are cached
+// per process and, when npfem_options.autotune_cache names a file, read from /
+// appended to it ("key n_tile stages microseconds" lines).
 std::mutex g_tune_mu;
 std::map<std::string, std::pair<int, int>> g_tuned;
 
-std::string tune_key(npfem_ctx *ctx, int nV) {
+long long tune_bucket(long long rows) {
+    long long b = 3 * 1024;
+    while (b < rows) b <<= 1;
+    return b;
+}
+
+std::string tune_key(npfem_ctx *ctx, int nV, long long bucket) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) prop.name[0] = 0;
     std::string name(prop.name);
     for (char &c : name)
         if (c == ' ') c = '_';
-    return name + "|nV=" + std::to_string(nV) + "|" + (bf16(ctx) ? "bf16" : "tf32");
+    return name + "|nV=" + std::to_string(nV) + "|" + (bf16(ctx) ? "bf16" : "tf32") + "|rows=" + std::to_string(bucket);
 }
 
-void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
+void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t, long long want_rows) {
     const void *pb = bf16(ctx) ? (const void *)t->Pinv16 : (const void *)t->Pinv32;
-    const std::string key = tune_key(ctx, t->nV);
+    const long long bucket = tune_bucket(want_rows);
+    const std::string key = tune_key(ctx, t->nV, bucket);
+    t->tuned_rows = bucket;
     auto use = [&](int nt, int st) {
         t->n_tile = nt;
         t->stages = st;
@@ -1276,13 +1298,15 @@ void choose_tiles(npfem_ctx *ctx, MeshTypeImpl *t) {
             }
         }
     }
-    const int rows = 3 * 8192;
+    const int rows = (int)std::min<long long>(bucket, 3 * 32768);
     std::vector<void *> tmp;
     float best = 1e30f;
     int best_nt = 0, best_st = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     try {
-        void *Q = dalloc<unsigned char>(ctx, (size_t)rows * t->nVp * (bf16(ctx) ? 2 : 4), &tmp);
+        const size_t qbytes = (size_t)rows * t->nVp * (bf16(ctx) ? 2 : 4);
+        void *Q = dalloc<unsigned char>(ctx, qbytes, &tmp);
+        CK(cudaMemsetAsync(Q, 0x3C, qbytes, ctx->stream));   // every element ~1.1e-2 (BF16 and FP32)
         float *Z = dalloc<float>(ctx, (size_t)rows * t->nVp, &tmp);
         CUtensorMap mq = make_map(ctx, Q, bf16(ctx), t->nV, rows, t->nVp, tc::BM);
         CUtensorMap mz = make_map(ctx, Z, false, t->nV, rows, t->nVp, 32);
@@ -1695,17 +1719,19 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         const size_t es = esize(ctx);
         // stash: 9 values per triangle of a chunk; as large as the shared memory left
         // after the header and the three vectors allows (capped), and with the vectors
-        // at least the L-BFGS batch scratch ((2 m_max + 4) values per thread)
+        // at least the L-BFGS batch scratch ((2 m_max + 4) values per thread) plus, in
+        // the FP32 path, the history staging area (m vectors of EPT values per thread)
         const size_t fixed = smem_header_bytes() + 3 * SMEM_VECS * (size_t)t->nVp * es;
         const size_t cap = mixed(ctx) ? 16384 : 6144;
         size_t room = (size_t)ctx->smem_optin > fixed + 1024 ? ((size_t)ctx->smem_optin - fixed - 1024) / es : 0;
         size_t st = std::min<size_t>({9 * (size_t)nT, cap, room});
-        const size_t need = (size_t)(2 * NPFEM_MAX_HISTORY + 4) * t->block;
+        const size_t need = (size_t)(2 * NPFEM_MAX_HISTORY + 4) * t->block +
+                            (mixed(ctx) ? (size_t)std::max(1, ctx->opt.history) * t->ept * t->block : 0);
         if (st + 3 * SMEM_VECS * (size_t)t->nVp < need) st = need - 3 * SMEM_VECS * (size_t)t->nVp;
         if (st < 9) st = 9;
         t->stash_T = (int)st;
         t->smem_step = smem_header_bytes() + (3 * SMEM_VECS * (size_t)t->nVp + t->stash_T) * es;
-        if (mixed(ctx)) choose_tiles(ctx, t);
+        if (mixed(ctx)) choose_tiles(ctx, t, 3 * 8192);
         if (t->smem_step > (size_t)ctx->smem_optin || gemm_smem(t) + 2048 > (size_t)ctx->smem_optin)
             fail(ctx, NPFEM_EINVAL, "mesh type needs more shared memory than the device offers");
         set_prefetch_distance(ctx, t);
@@ -1814,6 +1840,14 @@ int npfem_step(npfem_ctx *ctx, const double *f_ext, int f_ext_on_device) {
             CK(cudaMemcpyAsync(ctx->d_f, f_ext, ctx->ndofs * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
             fd = ctx->d_f;
         }
+        // tile choices for the real right-hand-side counts (outside any capture; a changed
+        // choice rebuilds the graph)
+        if (mixed(ctx))
+            for (auto *t : ctx->types)
+                if (t->ncells && tune_bucket(3ll * t->ncells) != t->tuned_rows) {
+                    choose_tiles(ctx, t, 3ll * t->ncells);
+                    invalidate_graph(ctx);
+                }
         k_set_ptr<<<1, 1, 0, ctx->stream>>>(ctx->d_fslot, fd);
         CK(cudaGetLastError());
         ctx->prof_next = 0;

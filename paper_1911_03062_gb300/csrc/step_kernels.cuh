@@ -137,6 +137,40 @@ __device__ __forceinline__ void prefetch_l2(const void *p, size_t n) {
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p)), "r"(b) : "memory");
 }
 
+// Per-thread asynchronous staging of history vectors in shared memory (FP32 path):
+// each thread copies its own granules of vector l into slot l of the staging area
+// (cp.async, 16 bytes each, L1 bypassed) and later reads back only what it copied,
+// so no barrier is involved -- a pass over cnt vectors waits for one latency
+// instead of cnt, and the next pass's copies fly while the block reduces.
+// Layout: granule g of slot l of thread t at ((l * G + g) * B + t) * 4 values.
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int EPT>
+__device__ __forceinline__ void stage_issue(float *stage, int l, const float *__restrict__ src, int n3) {
+#pragma unroll
+    for (int g = 0; g < EPT / 4; ++g) {
+        const int e0 = 4 * (threadIdx.x + g * blockDim.x);
+        if (e0 < n3) cp_async16(stage + (((size_t)l * (EPT / 4) + g) * blockDim.x + threadIdx.x) * 4, src + e0);
+    }
+}
+
+template <int EPT>
+__device__ __forceinline__ void stage_read(const float *stage, int l, float (&r)[EPT], int n3) {
+#pragma unroll
+    for (int g = 0; g < EPT / 4; ++g) {
+        const int e0 = 4 * (threadIdx.x + g * blockDim.x);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e0 < n3) v = *reinterpret_cast<const float4 *>(stage + (((size_t)l * (EPT / 4) + g) * blockDim.x + threadIdx.x) * 4);
+        r[4 * g] = v.x; r[4 * g + 1] = v.y; r[4 * g + 2] = v.z; r[4 * g + 3] = v.w;
+    }
+}
+
 // Sums over the block of n per-thread partials at once (the dot products of
 // one L-BFGS pass): partials are written transposed to shared memory, warp w
 // reduces values w, w + nwarps, ... in float-float (FP64 in the FP64 path)
@@ -263,7 +297,7 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         store_vec<T, EPT>(a.delta + base, dl, n3);
         __syncthreads();
         const Contact<T> ct{a.kcol ? a.kcol + (long long)cell * nVp : nullptr, a.ccol ? a.ccol + base : nullptr};
-        local_eval<T, EPT>(a.tc, a.yrel + base, ct, dl, gr, S, a.stash_T, [&](double g, double allow) {
+        local_eval<T, EPT>(a.tc, a.yrel + base, ct, dl, gr, S, a.stash_T, T(0), [&](double g, double allow, double) {
             a.g[cell] = g;
             a.allow[cell] = allow;
             a.hcount[cell] = 0;
@@ -303,6 +337,10 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
     const int nVp = a.tc.nVp, n3 = 3 * nVp, m = a.m;
     const int nitems = list ? *list_count : a.ncells;
     double *out = S.red;                       // batched sums (up to 2 MH + 4)
+    // FP32 path: the history passes go through a staging area in shared memory after
+    // the batched-sum scratch ((2 MH + 4) B values); free outside the local steps
+    constexpr bool STAGED = sizeof(T) == 4;
+    float *stage = reinterpret_cast<float *>(S.pos + (2 * MH + 4) * blockDim.x);
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int cell = list ? list[item] : item;
         const long long base = (long long)cell * n3;
@@ -312,6 +350,14 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         double *Mc = a.M + (long long)cell * m * m;
         const int cnt = a.hcount[cell], head = a.hhead[cell];
         auto slot = [&](int l) { return (head - cnt + l + 2 * m) % m; };   // l = 0 oldest
+        // the cell's vectors read later in this iteration, requested into L2 now: the
+        // gradient, the iterate, y (local steps) and the s history (second loop)
+        if ((int)threadIdx.x < 3 + (STAGED ? cnt : 2 * cnt)) {
+            const int i = threadIdx.x;
+            const T *src = i == 0 ? a.grad + base : i == 1 ? a.delta + base : i == 2 ? a.yrel + base
+                         : (i - 3) < cnt ? Sh + (long long)slot(i - 3) * n3 : Yh + (long long)slot(i - 3 - cnt) * n3;
+            prefetch_l2(src, (size_t)n3 * sizeof(T));
+        }
         // the cell's scalars that thread 0 uses between barriers, fetched up front into
         // shared memory (red[RED_SCALARS ..), above every reduction's scratch): M, rho, alpha, g, allow
         double *sM = S.red + RED_SCALARS, *srho = sM + MH * MH, *salp = srho + MH;
@@ -324,21 +370,38 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         if (threadIdx.x == 0) {
             S.bc->d[5] = a.g[cell];
             S.bc->d[6] = a.allow[cell];
+            S.bc->d[2] = 1.0;                        // alpha
+            S.bc->i[2] = 0;                          // halvings
+            S.bc->i[1] = 0;                          // not a descent direction
+        }
+        if constexpr (STAGED) {
+#pragma unroll
+            for (int l = 0; l < MH; ++l)
+                if (l < cnt) stage_issue<EPT>(stage, l, Yh + (long long)slot(l) * n3, n3);
+            cp_async_commit();
         }
         T r[EPT], d[EPT], gr[EPT], dl[EPT];
         load_vec<T, EPT>(a.z + base, r, n3);
         if (cnt > 0) {
             // second loop, pass A: y_i . z for all pairs
+            if constexpr (STAGED) cp_async_wait_all();
             T pa[MH];
 #pragma unroll
             for (int l = 0; l < MH; ++l) {
                 pa[l] = T(0);
                 if (l < cnt) {
                     T yi[EPT];
-                    load_vec<T, EPT>(Yh + (long long)slot(l) * n3, yi, n3);
+                    if constexpr (STAGED) stage_read<EPT>(stage, l, yi, n3);
+                    else load_vec<T, EPT>(Yh + (long long)slot(l) * n3, yi, n3);
 #pragma unroll
                     for (int j = 0; j < EPT; ++j) pa[l] += yi[j] * r[j];
                 }
+            }
+            if constexpr (STAGED) {                  // this thread's y granules are read: s next
+#pragma unroll
+                for (int l = 0; l < MH; ++l)
+                    if (l < cnt) stage_issue<EPT>(stage, l, Sh + (long long)slot(l) * n3, n3);
+                cp_async_commit();
             }
             block_sum_many<T, MH>(pa, cnt, MH, S.pos, out);
             if (threadIdx.x == 0) {
@@ -353,11 +416,13 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             }
             __syncthreads();
             // pass B: r = z + sum_l coef_l s_l
+            if constexpr (STAGED) cp_async_wait_all();
 #pragma unroll
             for (int l = 0; l < MH; ++l) {
                 if (l < cnt) {
                     T si[EPT];
-                    load_vec<T, EPT>(Sh + (long long)slot(l) * n3, si, n3);
+                    if constexpr (STAGED) stage_read<EPT>(stage, l, si, n3);
+                    else load_vec<T, EPT>(Sh + (long long)slot(l) * n3, si, n3);
                     const T cf = S.bc->t[l];
 #pragma unroll
                     for (int j = 0; j < EPT; ++j) r[j] += cf * si[j];
@@ -366,29 +431,12 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         }
 #pragma unroll
         for (int j = 0; j < EPT; ++j) d[j] = -r[j];
-        load_vec<T, EPT>(a.grad + base, gr, n3);
+        // grad . d: this thread's partial, reduced with the first trial's energy
+        T gdp = T(0);
         {
-            Acc<T> ac[1];
-            ac[0].zero();
+            load_vec<T, EPT>(a.grad + base, gr, n3);
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) ac[0].add_prod(gr[j], d[j]);
-            block_reduce_t0<T, 1>(ac, S.red, [&](const double *s) {
-                S.bc->d[1] = s[0];                       // grad . d
-                S.bc->d[2] = 1.0;                        // alpha
-                S.bc->i[2] = 0;                          // halvings
-                S.bc->i[1] = (s[0] >= 0.0 && cnt > 0);   // not a descent direction
-                if (S.bc->i[1]) {
-                    a.hcount[cell] = 0;
-                    a.hhead[cell] = 0;
-                    a.fb_list[atomicAdd(a.fb_count, 1)] = cell;
-                    atomicAdd(&a.st->fallbacks, 1ull);
-                }
-            });
-        }
-        if (S.bc->i[1]) {
-            store_vec<T, EPT>(a.q + base, gr, n3);
-            __syncthreads();
-            continue;
+            for (int j = 0; j < EPT; ++j) gdp = fma(gr[j], d[j], gdp);
         }
         load_vec<T, EPT>(a.delta + base, dl, n3);
         T dt[EPT], gt[EPT];
@@ -397,7 +445,20 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
 #pragma unroll
             for (int j = 0; j < EPT; ++j) dt[j] = dl[j] + alpha * d[j];
             const Contact<T> ct{a.kcol ? a.kcol + (long long)cell * nVp : nullptr, a.ccol ? a.ccol + base : nullptr};
-            local_eval<T, EPT>(a.tc, a.yrel + base, ct, dt, gt, S, a.stash_T, [&](double g, double allow) {
+            local_eval<T, EPT>(a.tc, a.yrel + base, ct, dt, gt, S, a.stash_T, gdp,
+                               [&](double g, double allow, double gds) {
+                if (S.bc->i[2] == 0) {                   // first trial: grad . d arrives here
+                    S.bc->d[1] = gds;
+                    if (gds >= 0.0 && cnt > 0) {         // not a descent direction: clear the
+                        S.bc->i[1] = 1;                  // history, queue the cell for
+                        S.bc->i[3] = 1;                  // d = -P^{-1} grad, end the search
+                        a.hcount[cell] = 0;
+                        a.hhead[cell] = 0;
+                        a.fb_list[atomicAdd(a.fb_count, 1)] = cell;
+                        atomicAdd(&a.st->fallbacks, 1ull);
+                        return;
+                    }
+                }
                 const double al = S.bc->d[2], gd = S.bc->d[1];
                 const double slack = a.use_allow ? (S.bc->d[6] + allow) : 0.0;
                 S.bc->d[3] = g;
@@ -416,8 +477,14 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             });
             if (S.bc->i[3]) break;
             alpha = S.bc->t[2];
+            gdp = T(0);
         }
         load_vec<T, EPT>(a.grad + base, gr, n3);      // old gradient (dead during the search)
+        if (S.bc->i[1]) {                              // fallback: the apply's RHS is grad g
+            store_vec<T, EPT>(a.q + base, gr, n3);
+            __syncthreads();
+            continue;
+        }
         store_vec<T, EPT>(a.delta + base, dt, n3);
         store_vec<T, EPT>(a.grad + base, gt, n3);
         if (a.last) {
@@ -449,6 +516,12 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         }
         // history pair and the first loop's dots (pass C): for every old pair
         // s_l . grad_new and s_l . y_new; for the new pair s.y, s.s, y.y, s.grad_new
+        if constexpr (STAGED) {
+#pragma unroll
+            for (int l = 0; l < MH; ++l)
+                if (l < cnt) stage_issue<EPT>(stage, l, Sh + (long long)slot(l) * n3, n3);
+            cp_async_commit();
+        }
         T sv[EPT], yv[EPT];
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
@@ -456,19 +529,27 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             yv[j] = gt[j] - gr[j];
         }
         T pc[2 * MH + 4];
+        if constexpr (STAGED) cp_async_wait_all();
 #pragma unroll
         for (int l = 0; l < MH; ++l) {
             pc[2 * l] = T(0);
             pc[2 * l + 1] = T(0);
             if (l < cnt) {
                 T si[EPT];
-                load_vec<T, EPT>(Sh + (long long)slot(l) * n3, si, n3);
+                if constexpr (STAGED) stage_read<EPT>(stage, l, si, n3);
+                else load_vec<T, EPT>(Sh + (long long)slot(l) * n3, si, n3);
 #pragma unroll
                 for (int j = 0; j < EPT; ++j) {
                     pc[2 * l] += si[j] * gt[j];
                     pc[2 * l + 1] += si[j] * yv[j];
                 }
             }
+        }
+        if constexpr (STAGED) {                      // this thread's s granules are read: y next
+#pragma unroll
+            for (int l = 0; l < MH; ++l)
+                if (l < cnt) stage_issue<EPT>(stage, l, Yh + (long long)slot(l) * n3, n3);
+            cp_async_commit();
         }
         T nsy = T(0), nss = T(0), nyy = T(0), nsg = T(0);
 #pragma unroll
@@ -546,11 +627,13 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         T qv[EPT];
 #pragma unroll
         for (int j = 0; j < EPT; ++j) qv[j] = gt[j];
+        if constexpr (STAGED) cp_async_wait_all();
 #pragma unroll
         for (int l = 0; l < MH; ++l) {
             if (l >= first_old && l < cnt) {
                 T yi[EPT];
-                load_vec<T, EPT>(Yh + (long long)slot(l) * n3, yi, n3);
+                if constexpr (STAGED) stage_read<EPT>(stage, l, yi, n3);
+                else load_vec<T, EPT>(Yh + (long long)slot(l) * n3, yi, n3);
                 const T ca = S.bc->t[l - first_old];
 #pragma unroll
                 for (int j = 0; j < EPT; ++j) qv[j] -= ca * yi[j];

@@ -132,6 +132,24 @@ def test_apply_pinv_fp64():
     assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("level", [1, 2, 4])
+def test_blocked_inverse_matches_library_inverse(level):
+    # the set-up's blocked Gauss-Jordan inverse (32-pivot blocks; nV = 42, 162, 2562 pad to
+    # 64, 192, 2592) read back through the FP64 apply of identity columns, against numpy
+    import torch
+    from oracle import oracle as O
+    from paper_1911_03062_gb300.npfem import Solver
+    u, t = I.icosphere(level)
+    mt = I.MeshType(f"L{level}", I.rbc_shape(u), t, I.Material(1.0, 5.0, 0.05, 10.0, 5e-4), I.RBC_R0)
+    s = Solver(precision="fp64")
+    tid = s.create_type(mt)
+    inv = np.linalg.inv(O.OracleType.from_mesh_type(mt).P_dense())
+    eye = torch.eye(mt.nV, dtype=torch.float64, device="cuda")
+    z = s.apply_pinv(tid, eye, torch.empty_like(eye)).cpu().numpy()
+    assert np.abs(z - inv).max() <= 1e-12 * np.abs(inv).max()
+    s.close()
+
+
 def test_errors():
     from paper_1911_03062_gb300.npfem import ENONFINITE, EINVAL, ESTATE, NpfemError, Solver
     s = Solver(precision="fp64")

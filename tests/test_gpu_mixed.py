@@ -189,3 +189,42 @@ def test_sampled_cells_hetero20k_full_bf16():
     xo, _ = run_oracle(groups, 1, sample=[[0, g.n_cells - 1] for g in groups])
     assert rel_pos_err(xg, xo, groups) <= TOL_MIXED
     assert st["max_refine_residual"] <= 1e-6
+
+
+_TUNE_SCRIPT = r"""
+import sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_1911_03062_gb300 import inputs as I
+from paper_1911_03062_gb300.npfem import Solver
+g = I.materialise(I.Group(I.rbc_type(), 40, seed=9, amp=0.3))
+s = Solver(precision="bf16", autotune_cache=sys.argv[2])
+s.add_cells(s.create_type(g.mtype), g.x0, g.v0)
+for _ in range(2):
+    s.step(g.f_ext.ravel())
+np.save(sys.argv[3], s.positions())
+s.close()
+"""
+
+
+def test_autotune_cache_file_round_trip(tmp_path):
+    # a context that tunes writes its choices (one line per (mesh, operand type, row
+    # bucket): the creation bucket and the bucket of its 40 cells); a second context in a
+    # fresh process (empty in-process cache) reads them back, tunes nothing, and steps
+    # bitwise like the first
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tiles.txt"
+    outs = [tmp_path / "x1.npy", tmp_path / "x2.npy"]
+    lines = []
+    for out in outs:
+        subprocess.run([sys.executable, "-c", _TUNE_SCRIPT, root, str(cache), str(out)], check=True, timeout=600)
+        lines.append(cache.read_text().splitlines())
+    assert len(lines[0]) == 2 and lines[1] == lines[0]
+    assert any("|rows=3072" in ln for ln in lines[0]) and any("|rows=24576" in ln for ln in lines[0])
+    for ln in lines[0]:
+        key, nt, st, us = ln.split()
+        assert int(nt) % 32 == 0 and 2 <= int(st) <= 6 and float(us) > 0
+    assert np.array_equal(np.load(outs[0]), np.load(outs[1]))
