@@ -65,6 +65,7 @@ template <> struct Acc<double> {
     __device__ __forceinline__ void store(double *p) const { *p = v; }
     __device__ __forceinline__ void load(const double *p) { v = *p; }
     __device__ __forceinline__ double get() const { return v; }
+    __device__ __forceinline__ double nearest() const { return v; }
 };
 
 template <> struct Acc<float> {
@@ -88,6 +89,8 @@ template <> struct Acc<float> {
         v.lo = f.y;
     }
     __device__ __forceinline__ double get() const { return (double)v.hi + (double)v.lo; }
+    // the sum rounded to FP32: the high part of the normalised pair (no FP64 arithmetic)
+    __device__ __forceinline__ float nearest() const { return v.hi; }
 };
 
 // Block-wide sums of N accumulators: each warp reduces by shuffles, warp 0

@@ -1719,14 +1719,12 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         const size_t es = esize(ctx);
         // stash: 9 values per triangle of a chunk; as large as the shared memory left
         // after the header and the three vectors allows (capped), and with the vectors
-        // at least the L-BFGS batch scratch ((2 m_max + 4) values per thread) plus, in
-        // the FP32 path, the history staging area (m vectors of EPT values per thread)
+        // at least the L-BFGS batch scratch ((2 m_max + 4) values per thread)
         const size_t fixed = smem_header_bytes() + 3 * SMEM_VECS * (size_t)t->nVp * es;
         const size_t cap = mixed(ctx) ? 16384 : 6144;
         size_t room = (size_t)ctx->smem_optin > fixed + 1024 ? ((size_t)ctx->smem_optin - fixed - 1024) / es : 0;
         size_t st = std::min<size_t>({9 * (size_t)nT, cap, room});
-        const size_t need = (size_t)(2 * NPFEM_MAX_HISTORY + 4) * t->block +
-                            (mixed(ctx) ? (size_t)std::max(1, ctx->opt.history) * t->ept * t->block : 0);
+        const size_t need = (size_t)(2 * NPFEM_MAX_HISTORY + 4) * t->block;
         if (st + 3 * SMEM_VECS * (size_t)t->nVp < need) st = need - 3 * SMEM_VECS * (size_t)t->nVp;
         if (st < 9) st = 9;
         t->stash_T = (int)st;

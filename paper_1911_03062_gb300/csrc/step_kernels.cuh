@@ -137,48 +137,14 @@ __device__ __forceinline__ void prefetch_l2(const void *p, size_t n) {
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p)), "r"(b) : "memory");
 }
 
-// Per-thread asynchronous staging of history vectors in shared memory (FP32 path):
-// each thread copies its own granules of vector l into slot l of the staging area
-// (cp.async, 16 bytes each, L1 bypassed) and later reads back only what it copied,
-// so no barrier is involved -- a pass over cnt vectors waits for one latency
-// instead of cnt, and the next pass's copies fly while the block reduces.
-// Layout: granule g of slot l of thread t at ((l * G + g) * B + t) * 4 values.
-__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
-                 "l"(gsrc)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-template <int EPT>
-__device__ __forceinline__ void stage_issue(float *stage, int l, const float *__restrict__ src, int n3) {
-#pragma unroll
-    for (int g = 0; g < EPT / 4; ++g) {
-        const int e0 = 4 * (threadIdx.x + g * blockDim.x);
-        if (e0 < n3) cp_async16(stage + (((size_t)l * (EPT / 4) + g) * blockDim.x + threadIdx.x) * 4, src + e0);
-    }
-}
-
-template <int EPT>
-__device__ __forceinline__ void stage_read(const float *stage, int l, float (&r)[EPT], int n3) {
-#pragma unroll
-    for (int g = 0; g < EPT / 4; ++g) {
-        const int e0 = 4 * (threadIdx.x + g * blockDim.x);
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (e0 < n3) v = *reinterpret_cast<const float4 *>(stage + (((size_t)l * (EPT / 4) + g) * blockDim.x + threadIdx.x) * 4);
-        r[4 * g] = v.x; r[4 * g + 1] = v.y; r[4 * g + 2] = v.z; r[4 * g + 3] = v.w;
-    }
-}
-
 // Sums over the block of n per-thread partials at once (the dot products of
 // one L-BFGS pass): partials are written transposed to shared memory, warp w
 // reduces values w, w + nwarps, ... in float-float (FP64 in the FP64 path)
-// in a fixed order, and out[i] (FP64, shared memory) holds the totals for
-// every thread on return.  scratch: NMAX * blockDim.x values of T (the
-// per-cell kernels use their local-step buffers, idle outside local_eval).
+// in a fixed order, and out[i] (shared memory) holds the totals, rounded once
+// to T, for every thread on return.  scratch: NMAX * blockDim.x values of T
+// (the per-cell kernels use their local-step buffers, idle outside local_eval).
 template <typename T, int NMAX>
-__device__ __forceinline__ void block_sum_many(const T (&part)[NMAX], int n1, int n2, T *scratch, double *out) {
+__device__ __forceinline__ void block_sum_many(const T (&part)[NMAX], int n1, int n2, T *scratch, T *out) {
     // values [0, n1) and [n2, NMAX) are summed; the others are skipped
     const int B = blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (B + 31) >> 5;
 #pragma unroll
@@ -192,7 +158,7 @@ __device__ __forceinline__ void block_sum_many(const T (&part)[NMAX], int n1, in
         for (int k = lane; k < B; k += 32) acc.add(scratch[i * B + k]);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) acc.merge_shfl(0xffffffffu, off);
-        if (lane == 0) out[i] = acc.get();
+        if (lane == 0) out[i] = (T)acc.nearest();
     }
     __syncthreads();
 }
@@ -336,23 +302,25 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
     const Smem<T> S = smem_layout<T>(a.tc.nVp);
     const int nVp = a.tc.nVp, n3 = 3 * nVp, m = a.m;
     const int nitems = list ? *list_count : a.ncells;
-    double *out = S.red;                       // batched sums (up to 2 MH + 4)
-    // FP32 path: the history passes go through a staging area in shared memory after
-    // the batched-sum scratch ((2 MH + 4) B values); free outside the local steps
-    constexpr bool STAGED = sizeof(T) == 4;
-    float *stage = reinterpret_cast<float *>(S.pos + (2 * MH + 4) * blockDim.x);
+    // batched sums (up to 2 MH + 4) and the cell's L-BFGS scalars in the arithmetic of T:
+    // the dots are summed in float-float and rounded once to FP32 in the FP32 path, whose
+    // coefficients then act on FP32 vectors (FP64 throughout in the FP64 path)
+    T *out = reinterpret_cast<T *>(S.red);
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int cell = list ? list[item] : item;
         const long long base = (long long)cell * n3;
         T *Sh = a.S + (long long)cell * m * n3;
         T *Yh = a.Y + (long long)cell * m * n3;
-        double *rho = a.rho + (long long)cell * m, *alp = a.alpha + (long long)cell * m;
-        double *Mc = a.M + (long long)cell * m * m;
+        T *rho = reinterpret_cast<T *>(a.rho) + (long long)cell * m, *alp = reinterpret_cast<T *>(a.alpha) + (long long)cell * m;
+        T *Mc = reinterpret_cast<T *>(a.M) + (long long)cell * m * m;
         const int cnt = a.hcount[cell], head = a.hhead[cell];
-        auto slot = [&](int l) { return (head - cnt + l + 2 * m) % m; };   // l = 0 oldest
+        // ring slot of history position l (0 = oldest): (head - cnt + l) mod m by a compare
+        // and subtract (an integer division has a 74-cycle latency on this GPU)
+        const int s0 = head - cnt < 0 ? head - cnt + m : head - cnt;
+        auto slot = [&](int l) { const int v = s0 + l; return v >= m ? v - m : v; };
         // the cell's vectors read later in this iteration, requested into L2 now: the
-        // gradient, the iterate, y (local steps) and the s history (second loop)
-        if ((int)threadIdx.x < 3 + (STAGED ? cnt : 2 * cnt)) {
+        // gradient, the iterate, y (local steps) and the history pairs
+        if ((int)threadIdx.x < 3 + 2 * cnt) {
             const int i = threadIdx.x;
             const T *src = i == 0 ? a.grad + base : i == 1 ? a.delta + base : i == 2 ? a.yrel + base
                          : (i - 3) < cnt ? Sh + (long long)slot(i - 3) * n3 : Yh + (long long)slot(i - 3 - cnt) * n3;
@@ -360,7 +328,7 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         }
         // the cell's scalars that thread 0 uses between barriers, fetched up front into
         // shared memory (red[RED_SCALARS ..), above every reduction's scratch): M, rho, alpha, g, allow
-        double *sM = S.red + RED_SCALARS, *srho = sM + MH * MH, *salp = srho + MH;
+        T *sM = reinterpret_cast<T *>(S.red + RED_SCALARS), *srho = sM + MH * MH, *salp = srho + MH;
         static_assert(RED_SCALARS + MH * MH + 2 * MH <= RED_DOUBLES, "L-BFGS scalars exceed the reduction area");
         for (int i = threadIdx.x; i < m * m + 2 * m; i += blockDim.x) {
             if (i < m * m) sM[i] = Mc[i];
@@ -374,55 +342,38 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             S.bc->i[2] = 0;                          // halvings
             S.bc->i[1] = 0;                          // not a descent direction
         }
-        if constexpr (STAGED) {
-#pragma unroll
-            for (int l = 0; l < MH; ++l)
-                if (l < cnt) stage_issue<EPT>(stage, l, Yh + (long long)slot(l) * n3, n3);
-            cp_async_commit();
-        }
         T r[EPT], d[EPT], gr[EPT], dl[EPT];
         load_vec<T, EPT>(a.z + base, r, n3);
         if (cnt > 0) {
             // second loop, pass A: y_i . z for all pairs
-            if constexpr (STAGED) cp_async_wait_all();
             T pa[MH];
 #pragma unroll
             for (int l = 0; l < MH; ++l) {
                 pa[l] = T(0);
                 if (l < cnt) {
                     T yi[EPT];
-                    if constexpr (STAGED) stage_read<EPT>(stage, l, yi, n3);
-                    else load_vec<T, EPT>(Yh + (long long)slot(l) * n3, yi, n3);
+                    load_vec<T, EPT>(Yh + (long long)slot(l) * n3, yi, n3);
 #pragma unroll
                     for (int j = 0; j < EPT; ++j) pa[l] += yi[j] * r[j];
                 }
             }
-            if constexpr (STAGED) {                  // this thread's y granules are read: s next
-#pragma unroll
-                for (int l = 0; l < MH; ++l)
-                    if (l < cnt) stage_issue<EPT>(stage, l, Sh + (long long)slot(l) * n3, n3);
-                cp_async_commit();
-            }
             block_sum_many<T, MH>(pa, cnt, MH, S.pos, out);
-            if (threadIdx.x == 0) {
-                double coef[MH];
+            if (threadIdx.x == 0) {                     // coefficients kept in S.bc->t
+                T *coef = S.bc->t;
                 for (int l = 0; l < cnt; ++l) {
                     const int i = slot(l);
-                    double dot = out[l];
+                    T dot = out[l];
                     for (int k = 0; k < l; ++k) dot += coef[k] * sM[slot(k) * m + i];
                     coef[l] = salp[i] - srho[i] * dot;
-                    S.bc->t[l] = T(coef[l]);
                 }
             }
             __syncthreads();
             // pass B: r = z + sum_l coef_l s_l
-            if constexpr (STAGED) cp_async_wait_all();
 #pragma unroll
             for (int l = 0; l < MH; ++l) {
                 if (l < cnt) {
                     T si[EPT];
-                    if constexpr (STAGED) stage_read<EPT>(stage, l, si, n3);
-                    else load_vec<T, EPT>(Sh + (long long)slot(l) * n3, si, n3);
+                    load_vec<T, EPT>(Sh + (long long)slot(l) * n3, si, n3);
                     const T cf = S.bc->t[l];
 #pragma unroll
                     for (int j = 0; j < EPT; ++j) r[j] += cf * si[j];
@@ -441,9 +392,14 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         load_vec<T, EPT>(a.delta + base, dl, n3);
         T dt[EPT], gt[EPT];
         T alpha = T(1);
-        for (;;) {
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) dt[j] = dl[j] + alpha * d[j];
+        for (int j = 0; j < EPT; ++j) dt[j] = dl[j] + alpha * d[j];
+        // d waits in the q buffer (dead until this iteration writes the next q) and the
+        // iterate in delta, so neither they nor the trial point hold registers through
+        // the local steps: a backtracking trial, and the end of the search, re-form the
+        // trial point from them (the same expression, so the same bits)
+        store_vec<T, EPT>(a.q + base, d, n3);
+        for (;;) {
             const Contact<T> ct{a.kcol ? a.kcol + (long long)cell * nVp : nullptr, a.ccol ? a.ccol + base : nullptr};
             local_eval<T, EPT>(a.tc, a.yrel + base, ct, dt, gt, S, a.stash_T, gdp,
                                [&](double g, double allow, double gds) {
@@ -478,8 +434,16 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             if (S.bc->i[3]) break;
             alpha = S.bc->t[2];
             gdp = T(0);
+            load_vec<T, EPT>(a.delta + base, dl, n3);
+            load_vec<T, EPT>(a.q + base, d, n3);
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) dt[j] = dl[j] + alpha * d[j];
         }
-        load_vec<T, EPT>(a.grad + base, gr, n3);      // old gradient (dead during the search)
+        load_vec<T, EPT>(a.grad + base, gr, n3);      // old gradient and iterate (dead during the search)
+        load_vec<T, EPT>(a.delta + base, dl, n3);
+        load_vec<T, EPT>(a.q + base, d, n3);
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) dt[j] = dl[j] + alpha * d[j];
         if (S.bc->i[1]) {                              // fallback: the apply's RHS is grad g
             store_vec<T, EPT>(a.q + base, gr, n3);
             __syncthreads();
@@ -516,12 +480,6 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         }
         // history pair and the first loop's dots (pass C): for every old pair
         // s_l . grad_new and s_l . y_new; for the new pair s.y, s.s, y.y, s.grad_new
-        if constexpr (STAGED) {
-#pragma unroll
-            for (int l = 0; l < MH; ++l)
-                if (l < cnt) stage_issue<EPT>(stage, l, Sh + (long long)slot(l) * n3, n3);
-            cp_async_commit();
-        }
         T sv[EPT], yv[EPT];
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
@@ -529,27 +487,19 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             yv[j] = gt[j] - gr[j];
         }
         T pc[2 * MH + 4];
-        if constexpr (STAGED) cp_async_wait_all();
 #pragma unroll
         for (int l = 0; l < MH; ++l) {
             pc[2 * l] = T(0);
             pc[2 * l + 1] = T(0);
             if (l < cnt) {
                 T si[EPT];
-                if constexpr (STAGED) stage_read<EPT>(stage, l, si, n3);
-                else load_vec<T, EPT>(Sh + (long long)slot(l) * n3, si, n3);
+                load_vec<T, EPT>(Sh + (long long)slot(l) * n3, si, n3);
 #pragma unroll
                 for (int j = 0; j < EPT; ++j) {
                     pc[2 * l] += si[j] * gt[j];
                     pc[2 * l + 1] += si[j] * yv[j];
                 }
             }
-        }
-        if constexpr (STAGED) {                      // this thread's s granules are read: y next
-#pragma unroll
-            for (int l = 0; l < MH; ++l)
-                if (l < cnt) stage_issue<EPT>(stage, l, Yh + (long long)slot(l) * n3, n3);
-            cp_async_commit();
         }
         T nsy = T(0), nss = T(0), nyy = T(0), nsg = T(0);
 #pragma unroll
@@ -565,12 +515,13 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         pc[2 * MH + 3] = nsg;
         block_sum_many<T, 2 * MH + 4>(pc, 2 * cnt, 2 * MH, S.pos, out);
         if (threadIdx.x == 0) {
-            const double sy = out[2 * MH], ss = out[2 * MH + 1], yy = out[2 * MH + 2], sg = out[2 * MH + 3];
-            // curvature test sy > tol |s| |y|, squared (no FP64 square roots): for tol >= 0 it
+            const T sy = out[2 * MH], ss = out[2 * MH + 1], yy = out[2 * MH + 2], sg = out[2 * MH + 3];
+            // curvature test sy > tol |s| |y|, squared (no square roots): for tol >= 0 it
             // needs sy > 0 and sy^2 > tol^2 |s|^2 |y|^2; for tol < 0 a pair with sy <= 0 passes
             // when sy^2 < tol^2 |s|^2 |y|^2 (tol = -inf: any pair with s, y != 0)
-            const int keep = m > 0 && (a.curv_tol >= 0.0 ? (sy > 0.0 && sy * sy > a.curv_tol2 * ss * yy)
-                                                         : (sy > 0.0 || sy * sy < a.curv_tol2 * ss * yy));
+            const T tol2 = (T)a.curv_tol2;
+            const int keep = m > 0 && (a.curv_tol >= 0.0 ? (sy > T(0) && sy * sy > tol2 * ss * yy)
+                                                         : (sy > T(0) || sy * sy < tol2 * ss * yy));
             const double gtv = S.bc->d[3];
             a.g[cell] = gtv;
             a.allow[cell] = S.bc->d[4];
@@ -579,17 +530,11 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
             // the history after this iteration, oldest first: old pairs (minus the
             // evicted oldest when full) then the new one
             int first_old = 0, ncnt = cnt;
+            T rr = T(0);
             if (keep) {
                 if (cnt == m) first_old = 1; else ncnt = cnt + 1;
                 const int ns = head;                         // the new pair's slot
-                double rr;
-                if (sizeof(T) == 4 && sy > 1e-30 && sy < 1e30) {
-                    // FP32 reciprocal + one Newton step in FP64: ~1e-14 relative
-                    const double r0 = (double)(1.0f / (float)sy);
-                    rr = r0 * (2.0 - sy * r0);
-                } else {
-                    rr = 1.0 / sy;
-                }
+                rr = T(1) / sy;
                 rho[ns] = rr;
                 srho[ns] = rr;
                 for (int l = first_old; l < cnt; ++l) {
@@ -597,25 +542,22 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
                     sM[slot(l) * m + ns] = out[2 * l + 1];
                 }
             }
-            // alpha_i = rho_i (s_i . grad - sum_{j newer} alpha_j s_i . y_j), newest first
-            double al[MH + 1];
+            // alpha_i = rho_i (s_i . grad - sum_{j newer} alpha_j s_i . y_j), newest first:
+            // the new pair's (p = nold), then the kept old ones (p = l - first_old), kept
+            // in S.bc->t[p] (the coefficients pass D applies)
             const int nold = cnt - first_old;
-            if (keep) al[nold] = srho[head] * sg;
+            T *al = S.bc->t;
+            const T aln = keep ? rr * sg : T(0);
+            if (keep) al[nold] = aln;
             for (int l = cnt - 1; l >= first_old; --l) {
                 const int i = slot(l), p = l - first_old;
-                double dot = out[2 * l];
+                T dot = out[2 * l];
                 for (int k = p + 1; k < nold; ++k) dot -= al[k] * sM[i * m + slot(k + first_old)];
-                if (keep) dot -= al[nold] * out[2 * l + 1];
+                if (keep) dot -= aln * out[2 * l + 1];
                 al[p] = srho[i] * dot;
+                alp[i] = al[p];
             }
-            for (int p = 0; p < nold; ++p) {
-                alp[slot(p + first_old)] = al[p];
-                S.bc->t[p] = T(al[p]);
-            }
-            if (keep) {
-                alp[head] = al[nold];
-                S.bc->t[nold] = T(al[nold]);
-            }
+            if (keep) alp[head] = aln;
             S.bc->i[4] = keep;
             S.bc->i[5] = first_old;
             a.hcount[cell] = ncnt;
@@ -627,13 +569,11 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
         T qv[EPT];
 #pragma unroll
         for (int j = 0; j < EPT; ++j) qv[j] = gt[j];
-        if constexpr (STAGED) cp_async_wait_all();
 #pragma unroll
         for (int l = 0; l < MH; ++l) {
             if (l >= first_old && l < cnt) {
                 T yi[EPT];
-                if constexpr (STAGED) stage_read<EPT>(stage, l, yi, n3);
-                else load_vec<T, EPT>(Yh + (long long)slot(l) * n3, yi, n3);
+                load_vec<T, EPT>(Yh + (long long)slot(l) * n3, yi, n3);
                 const T ca = S.bc->t[l - first_old];
 #pragma unroll
                 for (int j = 0; j < EPT; ++j) qv[j] -= ca * yi[j];
