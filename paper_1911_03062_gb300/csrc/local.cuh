@@ -487,22 +487,11 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
         const int ct = stash_T / 9;
         for (int t0 = 0; t0 < tc.nT; t0 += ct) {
             const int t1 = min(tc.nT, t0 + ct);
-            // software-pipelined: the next triangle's constants load while this one is evaluated
-            int4 tv_n = make_int4(0, 0, 0, 0);
-            T Di_n[4] = {T(0), T(0), T(0), T(0)}, w_n[2] = {T(0), T(0)};
-            if (t0 + tid < t1) {
-                tv_n = __ldg(tc.tri + t0 + tid);
-                ld4(tc.dinv + 4 * (t0 + tid), Di_n);
-                ld2(tc.wtri + 2 * (t0 + tid), w_n);
-            }
             for (int t = t0 + tid; t < t1; t += B) {
-                const int4 tv = tv_n;
-                const T Di[4] = {Di_n[0], Di_n[1], Di_n[2], Di_n[3]}, w[2] = {w_n[0], w_n[1]};
-                if (t + B < t1) {
-                    tv_n = __ldg(tc.tri + t + B);
-                    ld4(tc.dinv + 4 * (t + B), Di_n);
-                    ld2(tc.wtri + 2 * (t + B), w_n);
-                }
+                const int4 tv = __ldg(tc.tri + t);
+                T Di[4], w[2];
+                ld4(tc.dinv + 4 * t, Di);
+                ld2(tc.wtri + 2 * t, w);
                 T R[6], N[3];
                 aV += tri_local(pos, yrel, nVp, tv, Di, w[0], w[1], tc.cd, o, R, N, en, al);
                 T *st = stash + 9 * (t - t0);
@@ -512,25 +501,28 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
             }
             __syncthreads();
             if (sizeof(T) == 4 && tc.pad_t && t0 == 0 && t1 == tc.nT) {
-                // whole mesh in one chunk: all slots of a vertex requested at once (coalesced;
-                // one L2 round trip per vertex)
+                // whole mesh in one chunk: all slots of a vertex loaded at once (coalesced)
                 for (int v = tid; v < nV; v += B) {
                     T g0 = T(0), g1 = T(0), g2 = T(0), n0 = T(0), n1 = T(0), n2 = T(0);
-                    int4 inc[PAD_T];
 #pragma unroll
-                    for (int q = 0; q < PAD_T; ++q)
-                        inc[q] = q < tc.pad_t ? __ldg(tc.vt_pad + q * nV + v) : make_int4(0, 0, 0, 0);
+                    for (int q0 = 0; q0 < PAD_T; q0 += 4) {
+                        if (q0 >= tc.pad_t) break;
+                        int4 inc[4];
 #pragma unroll
-                    for (int q = 0; q < PAD_T; ++q) {
-                        const T *st = stash + 9 * inc[q].x;
-                        const T G0 = __int_as_float(inc[q].y), G1 = __int_as_float(inc[q].z);
-                        const T wn = __int_as_float(inc[q].w);
-                        g0 += st[0] * G0 + st[1] * G1;
-                        g1 += st[2] * G0 + st[3] * G1;
-                        g2 += st[4] * G0 + st[5] * G1;
-                        n0 += wn * st[6];
-                        n1 += wn * st[7];
-                        n2 += wn * st[8];
+                        for (int q = 0; q < 4; ++q)
+                            inc[q] = q0 + q < tc.pad_t ? __ldg(tc.vt_pad + (q0 + q) * nV + v) : make_int4(0, 0, 0, 0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const T *st = stash + 9 * inc[q].x;
+                            const T G0 = __int_as_float(inc[q].y), G1 = __int_as_float(inc[q].z);
+                            const T wn = __int_as_float(inc[q].w);
+                            g0 += st[0] * G0 + st[1] * G1;
+                            g1 += st[2] * G0 + st[3] * G1;
+                            g2 += st[4] * G0 + st[5] * G1;
+                            n0 += wn * st[6];
+                            n1 += wn * st[7];
+                            n2 += wn * st[8];
+                        }
                     }
                     gsh[v] += g0;
                     gsh[nVp + v] += g1;
@@ -619,17 +611,21 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
             if (sizeof(T) == 4 && tc.pad_h && h0 == 0 && h1 == tc.nH) {
                 for (int v = tid; v < nV; v += B) {
                     T g0 = T(0), g1 = T(0), g2 = T(0);
-                    int2 inc[PAD_H];                    // all slots of the vertex requested at once
 #pragma unroll
-                    for (int q = 0; q < PAD_H; ++q)
-                        inc[q] = q < tc.pad_h ? __ldg(tc.vh_pad + q * nV + v) : make_int2(0, 0);
+                    for (int q0 = 0; q0 < PAD_H; q0 += 4) {
+                        if (q0 >= tc.pad_h) break;
+                        int2 inc[4];
 #pragma unroll
-                    for (int q = 0; q < PAD_H; ++q) {
-                        const T *st = stash + 3 * inc[q].x;
-                        const T c = __int_as_float(inc[q].y);
-                        g0 += c * st[0];
-                        g1 += c * st[1];
-                        g2 += c * st[2];
+                        for (int q = 0; q < 4; ++q)
+                            inc[q] = q0 + q < tc.pad_h ? __ldg(tc.vh_pad + (q0 + q) * nV + v) : make_int2(0, 0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const T *st = stash + 3 * inc[q].x;
+                            const T c = __int_as_float(inc[q].y);
+                            g0 += c * st[0];
+                            g1 += c * st[1];
+                            g2 += c * st[2];
+                        }
                     }
                     gsh[v] += g0;
                     gsh[nVp + v] += g1;
