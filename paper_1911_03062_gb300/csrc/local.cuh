@@ -52,6 +52,8 @@ struct TypeConst {
     // slot-major padded copies of the incidence lists (slot q of vertex v at
     // [q * nV + v]; unused slots carry zero weights), for one-round gathers:
     int pad_t, pad_h;       // slots per vertex (0 = not available)
+    int2 tri_vrange[4];     // triangle chunk c < 4 (of stash_T / 9 triangles): first and last vertex
+                            // its triangles touch (x > y: none)
     const int4 *vt_pad;     // (t, G0, G1, 1) as bits; padding (0, 0, 0, 0)
     const int2 *vh_pad;     // (h, c) as bits; padding (0, 0)
 };
@@ -322,7 +324,7 @@ __device__ __forceinline__ T tri_local(const T *pos, const T *__restrict__ yr, i
             }
     }
     en += T(0.5) * ws * ns + T(0.5) * wa * na;
-    al += (ws * sqrt(ns) + wa * sqrt(na)) * sqrt(nf);
+    al += ws * sqrt(ns * nf) + wa * sqrt(na * nf);
     if (cd != T(0)) {
         const Damp<T> dm = tri_damp(pos, yr, nVp, tv, Di[0], Di[1], Di[2], Di[3], cd * (ws + wa), sqrt(nf));
 #pragma unroll
@@ -378,7 +380,7 @@ __device__ __forceinline__ void hinge_local(const T *pos, const T *__restrict__ 
         R[c] = kb * r;
     }
     en += T(0.5) * kb * n2;
-    al += kb * sqrt(n2) * nb;
+    al += kb * fabs(nb - nb * sc) * nb;              // |b - p| = |b| |1 - sc| (no square root)
     if (cd != T(0)) {
         const Damp<T> dm = hinge_damp(pos, yr, nVp, hv, hc[0], hc[1], hc[2], hc[3], cd * kb, nb);
         R[0] += dm.r[0];
@@ -500,9 +502,14 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                 st[6] = N[0]; st[7] = N[1]; st[8] = N[2];
             }
             __syncthreads();
-            if (sizeof(T) == 4 && tc.pad_t && t0 == 0 && t1 == tc.nT) {
-                // whole mesh in one chunk: all slots of a vertex loaded at once (coalesced)
-                for (int v = tid; v < nV; v += B) {
+            if (sizeof(T) == 4 && tc.pad_t) {
+                // all slots of a vertex loaded at once (coalesced); a slot whose triangle lies
+                // outside this chunk adds nothing (padding slots: triangle 0, zero weights);
+                // only the vertices this chunk's triangles touch are visited (a contiguous
+                // range: vertices in RCM order, triangles sorted by their smallest vertex)
+                const int nct = t1 - t0, chunk = t0 / ct;
+                const int2 rg = chunk < 4 ? tc.tri_vrange[chunk] : make_int2(0, nV - 1);
+                for (int v = rg.x + tid; v <= rg.y; v += B) {
                     T g0 = T(0), g1 = T(0), g2 = T(0), n0 = T(0), n1 = T(0), n2 = T(0);
 #pragma unroll
                     for (int q0 = 0; q0 < PAD_T; q0 += 4) {
@@ -513,7 +520,9 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                             inc[q] = q0 + q < tc.pad_t ? __ldg(tc.vt_pad + (q0 + q) * nV + v) : make_int4(0, 0, 0, 0);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            const T *st = stash + 9 * inc[q].x;
+                            const int tt = inc[q].x - t0;
+                            if ((unsigned)tt >= (unsigned)nct) continue;
+                            const T *st = stash + 9 * tt;
                             const T G0 = __int_as_float(inc[q].y), G1 = __int_as_float(inc[q].z);
                             const T wn = __int_as_float(inc[q].w);
                             g0 += st[0] * G0 + st[1] * G1;
@@ -527,12 +536,9 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                     gsh[v] += g0;
                     gsh[nVp + v] += g1;
                     gsh[2 * nVp + v] += g2;
-                    gva[v] = n0;                        // single chunk: the complete gradient
-                    gva[nVp + v] = n1;
-                    gva[2 * nVp + v] = n2;
-                    ag2 = fma(n0, n0, ag2);
-                    ag2 = fma(n1, n1, ag2);
-                    ag2 = fma(n2, n2, ag2);
+                    gva[v] += n0;                       // area-vector sums (zeroed with the positions)
+                    gva[nVp + v] += n1;
+                    gva[2 * nVp + v] += n2;
                 }
                 __syncthreads();
                 continue;
@@ -563,6 +569,18 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                 }
             }
             __syncthreads();
+        }
+    }
+    if (sizeof(T) == 4 && tc.pad_t) {
+        // |gV(x)|^2 over this thread's elements of the complete volume gradient
+#pragma unroll
+        for (int g4 = 0; g4 < EPT / 4; ++g4) {
+            const int e0 = 4 * (tid + g4 * B);
+            if (e0 >= n3) continue;
+            T gv[4];
+            ld4(gva + e0, gv);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ag2 = fma(gv[i], gv[i], ag2);
         }
     }
     // First volume reduction {6 V(x), |gV(x)|^2} on the hinge phase's barriers:

@@ -1724,11 +1724,39 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         const size_t cap = mixed(ctx) ? 16384 : 6144;
         size_t room = (size_t)ctx->smem_optin > fixed + 1024 ? ((size_t)ctx->smem_optin - fixed - 1024) / es : 0;
         size_t st = std::min<size_t>({9 * (size_t)nT, cap, room});
+        if (mixed(ctx) && t->block <= 256) {
+            // FP32 path, blocks of <= 256 threads (64 registers): size the stash so that four
+            // blocks share an SM -- triangles in equal chunks of what fits, the hinges in one
+            // chunk where that fits too (the padded gathers take chunks; a fourth resident
+            // block measured faster than one stash for the whole mesh)
+            int per_sm = 0, resv = 0;
+            CK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+            CK(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device));
+            const size_t budget = (size_t)per_sm / 4 > (size_t)resv + fixed ? ((size_t)per_sm / 4 - resv - fixed) / es : 0;
+            if (budget >= 9 * 32) {
+                const size_t chunks = (9 * (size_t)nT + budget - 1) / budget;
+                const size_t ct = ((size_t)nT + chunks - 1) / chunks;
+                st = std::min(st, std::max<size_t>(9 * ct, 3 * (size_t)t->nH <= budget ? 3 * (size_t)t->nH : 0));
+            }
+        }
         const size_t need = (size_t)(2 * NPFEM_MAX_HISTORY + 4) * t->block;
         if (st + 3 * SMEM_VECS * (size_t)t->nVp < need) st = need - 3 * SMEM_VECS * (size_t)t->nVp;
         if (st < 9) st = 9;
         t->stash_T = (int)st;
         t->smem_step = smem_header_bytes() + (3 * SMEM_VECS * (size_t)t->nVp + t->stash_T) * es;
+        if (mixed(ctx)) {
+            // vertex range of each triangle chunk (the padded gather visits only those)
+            const int ct = std::max(1, t->stash_T / 9);
+            for (int c = 0; c < 4; ++c) {
+                int lo = nV, hi = -1;
+                for (int k = c * ct; k < std::min(nT, (c + 1) * ct); ++k)
+                    for (int j = 0; j < 3; ++j) {
+                        lo = std::min(lo, tris_i[3 * k + j]);
+                        hi = std::max(hi, tris_i[3 * k + j]);
+                    }
+                t->tc32.tri_vrange[c] = make_int2(lo, hi);
+            }
+        }
         if (mixed(ctx)) choose_tiles(ctx, t, 3 * 8192);
         if (t->smem_step > (size_t)ctx->smem_optin || gemm_smem(t) + 2048 > (size_t)ctx->smem_optin)
             fail(ctx, NPFEM_EINVAL, "mesh type needs more shared memory than the device offers");

@@ -200,7 +200,7 @@ __global__ void k_damp_rhs(int ncells, int nV, int nVp, const double *__restrict
 }
 
 template <typename T, int EPT, int MAXB>
-__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) : 1) k_predict(IterArgs<T> a) {
+__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 4) : 1) k_predict(IterArgs<T> a) {
     const Smem<T> S = smem_layout<T>(a.tc.nVp);
     const int nVp = a.tc.nVp, n3 = 3 * nVp;
     for (int cell = blockIdx.x; cell < a.ncells; cell += gridDim.x) {
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) :
 constexpr int MH = NPFEM_MAX_HISTORY;
 
 template <typename T, int EPT, int MAXB>
-__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 3) : 1) k_iterate(IterArgs<T> a, const int *list,
+__global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 4) : 1) k_iterate(IterArgs<T> a, const int *list,
                                                                       const int *list_count) {
     const Smem<T> S = smem_layout<T>(a.tc.nVp);
     const int nVp = a.tc.nVp, n3 = 3 * nVp, m = a.m;
