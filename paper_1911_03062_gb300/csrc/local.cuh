@@ -54,7 +54,7 @@ struct TypeConst {
     int pad_t, pad_h;       // slots per vertex (0 = not available)
     int2 tri_vrange[4];     // triangle chunk c < 4 (of stash_T / 9 triangles): first and last vertex
                             // its triangles touch (x > y: none)
-    const int4 *vt_pad;     // (t, G0, G1, 1) as bits; padding (0, 0, 0, 0)
+    const int *vt_pad;      // (t << 2) | corner; padding -1
     const int2 *vh_pad;     // (h, c) as bits; padding (0, 0)
 };
 
@@ -260,16 +260,18 @@ __device__ __noinline__ Damp<T> tri_damp(const T *pos, const T *__restrict__ yr,
     return o;
 }
 
-// Strain + area projection of one triangle.  Returns R = w_s (F - T_s) +
-// w_a (F - T_a) (the vertex gradient is sum_c R[:, c] G[corner][c]), N =
-// (e1 x e2) / 6 (each corner's share of the volume gradient) and the
+// Strain + area projection of one triangle, written to its 9 stash values:
+// R = w_s (F - T_s) + w_a (F - T_a) (the vertex gradient is sum_c R[:, c]
+// G[corner][c]) in st[0..5], or (corners) the gradients of corners 1 and 2,
+// R G[1] and R G[2], in st[0..2] and st[3..5]; N = (e1 x e2) / 6 (each
+// corner's share of the volume gradient) in st[6..8].  Returns the
 // signed-volume term (x0 - o).(e1 x e2) of the triangle.
 // Rayleigh damping (cd = beta/h != 0): the triangle's part of
 // beta/(2h) (x - y)^T L (x - y), i.e. cd (w_s + w_a)/2 |F(x - y)|^2, adds
 // cd (w_s + w_a) F(x - y) to R; yr holds y (same frame as pos).
 template <typename T>
 __device__ __forceinline__ T tri_local(const T *pos, const T *__restrict__ yr, int nVp, int4 tv, const T (&Di)[4], T ws,
-                                       T wa, T cd, const T o[3], T R[6], T N[3], T &en, T &al) {
+                                       T wa, T cd, const T o[3], bool corners, T *st, T &en, T &al) {
     T F[6], E1[3], E2[3], A0[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -281,6 +283,10 @@ __device__ __forceinline__ T tri_local(const T *pos, const T *__restrict__ yr, i
         F[2 * c] = E1[c] * Di[0] + E2[c] * Di[2];
         F[2 * c + 1] = E1[c] * Di[1] + E2[c] * Di[3];
     }
+    // volume part first (the edge vectors are then dead)
+    const T C0 = E1[1] * E2[2] - E1[2] * E2[1], C1 = E1[2] * E2[0] - E1[0] * E2[2], C2 = E1[0] * E2[1] - E1[1] * E2[0];
+    const T vol = A0[0] * C0 + A0[1] * C1 + A0[2] * C2;
+    T R[6];
     // S = F^T F = V diag(s^2) V^T.  For a triangle that has not collapsed,
     // R = ws (F - U V^T) + wa (F - U diag(d) V^T) = F G with the 2x2
     // G = V diag((ws + wa) - (ws + wa d_i) / s_i) V^T (U = F V diag(1/s)),
@@ -332,11 +338,22 @@ __device__ __forceinline__ T tri_local(const T *pos, const T *__restrict__ yr, i
         en += dm.e;
         al += dm.a;
     }
-    T C0 = E1[1] * E2[2] - E1[2] * E2[1], C1 = E1[2] * E2[0] - E1[0] * E2[2], C2 = E1[0] * E2[1] - E1[1] * E2[0];
-    N[0] = C0 / T(6);
-    N[1] = C1 / T(6);
-    N[2] = C2 / T(6);
-    return A0[0] * C0 + A0[1] * C1 + A0[2] * C2;
+    if (corners) {
+        // the gradients of corners 1 and 2 (corner 0's is minus their sum: the three
+        // G rows sum to zero), so that the gather's incidence entries carry no coefficients
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            st[r] = R[2 * r] * Di[0] + R[2 * r + 1] * Di[1];
+            st[3 + r] = R[2 * r] * Di[2] + R[2 * r + 1] * Di[3];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) st[i] = R[i];
+    }
+    st[6] = C0 / T(6);
+    st[7] = C1 / T(6);
+    st[8] = C2 / T(6);
+    return vol;
 }
 
 // Rayleigh damping part of one hinge (out of line, as tri_damp; r[0..2] used).
@@ -395,17 +412,21 @@ __device__ __forceinline__ void hinge_local(const T *pos, const T *__restrict__ 
 // thread's partial sum over its triangles (plain arithmetic of T; the block combines
 // the partials in float-float / FP64).
 template <typename T>
-__device__ __forceinline__ T volume_pass(const TypeConst<T> &tc, const T *pos, int nVp) {
+__device__ __forceinline__ T volume_pass(const TypeConst<T> &tc, const T *pos, int nVp, T *nst) {
     T aV = T(0);
     const T o0 = pos[0], o1 = pos[nVp], o2 = pos[2 * nVp];
-    int4 tv_n = threadIdx.x < tc.nT ? __ldg(tc.tri + threadIdx.x) : make_int4(0, 0, 0, 0);
     for (int t = threadIdx.x; t < tc.nT; t += blockDim.x) {
-        const int4 tv = tv_n;
-        if (t + (int)blockDim.x < tc.nT) tv_n = __ldg(tc.tri + t + blockDim.x);
+        const int4 tv = __ldg(tc.tri + t);
         T ax = pos[tv.x] - o0, ay = pos[nVp + tv.x] - o1, az = pos[2 * nVp + tv.x] - o2;
         T e1x = pos[tv.y] - pos[tv.x], e1y = pos[nVp + tv.y] - pos[nVp + tv.x], e1z = pos[2 * nVp + tv.y] - pos[2 * nVp + tv.x];
         T e2x = pos[tv.z] - pos[tv.x], e2y = pos[nVp + tv.z] - pos[nVp + tv.x], e2z = pos[2 * nVp + tv.z] - pos[2 * nVp + tv.x];
-        aV += ax * (e1y * e2z - e1z * e2y) + ay * (e1z * e2x - e1x * e2z) + az * (e1x * e2y - e1y * e2x);
+        const T cx = e1y * e2z - e1z * e2y, cy = e1z * e2x - e1x * e2z, cz = e1x * e2y - e1y * e2x;
+        aV += ax * cx + ay * cy + az * cz;
+        if (nst) {                                   // the triangle's share of the volume gradient
+            nst[3 * t] = cx / T(6);
+            nst[3 * t + 1] = cy / T(6);
+            nst[3 * t + 2] = cz / T(6);
+        }
     }
     return aV;
 }
@@ -494,17 +515,13 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                 T Di[4], w[2];
                 ld4(tc.dinv + 4 * t, Di);
                 ld2(tc.wtri + 2 * t, w);
-                T R[6], N[3];
-                aV += tri_local(pos, yrel, nVp, tv, Di, w[0], w[1], tc.cd, o, R, N, en, al);
-                T *st = stash + 9 * (t - t0);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) st[i] = R[i];
-                st[6] = N[0]; st[7] = N[1]; st[8] = N[2];
+                aV += tri_local(pos, yrel, nVp, tv, Di, w[0], w[1], tc.cd, o, sizeof(T) == 4 && tc.pad_t != 0,
+                                stash + 9 * (t - t0), en, al);
             }
             __syncthreads();
             if (sizeof(T) == 4 && tc.pad_t) {
                 // all slots of a vertex loaded at once (coalesced); a slot whose triangle lies
-                // outside this chunk adds nothing (padding slots: triangle 0, zero weights);
+                // outside this chunk, or a padding slot (-1), adds nothing;
                 // only the vertices this chunk's triangles touch are visited (a contiguous
                 // range: vertices in RCM order, triangles sorted by their smallest vertex)
                 const int nct = t1 - t0, chunk = t0 / ct;
@@ -514,23 +531,23 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
 #pragma unroll
                     for (int q0 = 0; q0 < PAD_T; q0 += 4) {
                         if (q0 >= tc.pad_t) break;
-                        int4 inc[4];
+                        int inc[4];
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
-                            inc[q] = q0 + q < tc.pad_t ? __ldg(tc.vt_pad + (q0 + q) * nV + v) : make_int4(0, 0, 0, 0);
+                            inc[q] = q0 + q < tc.pad_t ? __ldg(tc.vt_pad + (q0 + q) * nV + v) : -1;
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            const int tt = inc[q].x - t0;
+                            const int tt = (inc[q] >> 2) - t0;
                             if ((unsigned)tt >= (unsigned)nct) continue;
                             const T *st = stash + 9 * tt;
-                            const T G0 = __int_as_float(inc[q].y), G1 = __int_as_float(inc[q].z);
-                            const T wn = __int_as_float(inc[q].w);
-                            g0 += st[0] * G0 + st[1] * G1;
-                            g1 += st[2] * G0 + st[3] * G1;
-                            g2 += st[4] * G0 + st[5] * G1;
-                            n0 += wn * st[6];
-                            n1 += wn * st[7];
-                            n2 += wn * st[8];
+                            const int k = inc[q] & 3;
+                            const T a0 = st[0], a1 = st[1], a2 = st[2], b0 = st[3], b1 = st[4], b2 = st[5];
+                            g0 += k == 1 ? a0 : k == 2 ? b0 : -(a0 + b0);
+                            g1 += k == 1 ? a1 : k == 2 ? b1 : -(a1 + b1);
+                            g2 += k == 1 ? a2 : k == 2 ? b2 : -(a2 + b2);
+                            n0 += st[6];
+                            n1 += st[7];
+                            n2 += st[8];
                         }
                     }
                     gsh[v] += g0;
@@ -681,15 +698,41 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
     //    lambda_j = (V0 - V(p_j) - gV(p_j).(x - p_j)) / |gV(p_j)|^2,
     //    stopped once |V(p_j) - V0| <= tol V0 or after 8 updates.  gV(x) was
     //    gathered with the triangles (gva) and lambda_0 formed during the hinge
-    //    phase; later gradients come from the one-ring cross products (into gva).
-    //    pos holds p.
-    T p[EPT];
-#pragma unroll
-    for (int j = 0; j < EPT; ++j) p[j] = x[j];
+    //    phase; later gradients come from the triangles' (e1 x e2)/6 of the last
+    //    volume pass (FP32 path) or the one-ring cross products (into gva).
+    //    pos holds p (x until the first update); each thread reads back its own
+    //    elements, so p needs no registers.
     {
         T *gV = gva;
+        // FP32 path with the padded incidence table: each volume pass also leaves every
+        // triangle's (e1 x e2)/6 in the stash, and the next gradient is their sum over the
+        // vertex's triangles (the same sum as the triangle phase's)
+        const bool nsum = sizeof(T) == 4 && tc.pad_t && stash_T >= 3 * tc.nT;
         for (int it = 0; !S.bc->i[0]; ++it) {
-            if (it > 0) {
+            if (it > 0 && nsum) {
+                for (int v = tid; v < nV; v += B) {
+                    T g0 = T(0), g1 = T(0), g2 = T(0);
+#pragma unroll
+                    for (int q0 = 0; q0 < PAD_T; q0 += 4) {
+                        if (q0 >= tc.pad_t) break;
+                        int inc[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            inc[q] = q0 + q < tc.pad_t ? __ldg(tc.vt_pad + (q0 + q) * nV + v) : -1;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (inc[q] < 0) continue;
+                            const T *nq = stash + 3 * (inc[q] >> 2);
+                            g0 += nq[0];
+                            g1 += nq[1];
+                            g2 += nq[2];
+                        }
+                    }
+                    gV[v] = g0;
+                    gV[nVp + v] = g1;
+                    gV[2 * nVp + v] = g2;
+                }
+            } else if (it > 0) {
                 const T q0 = pos[0], q1 = pos[nVp], q2 = pos[2 * nVp];
                 for (int v = tid; v < nV; v += B) {
                     T g[3] = {T(0), T(0), T(0)};
@@ -707,6 +750,8 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                     gV[nVp + v] = g[1] / T(6);
                     gV[2 * nVp + v] = g[2] / T(6);
                 }
+            }
+            if (it > 0) {
                 __syncthreads();
                 T qg2 = T(0), qd = T(0);
 #pragma unroll
@@ -715,13 +760,14 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                     if (e0 >= n3) continue;
                     int v0;
                     elem_cv(e0, nVp, v0);
-                    T gv[4];
+                    T gv[4], pv[4];
                     ld4(gV + e0, gv);
+                    ld4(pos + e0, pv);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         if (v0 + i >= nV) continue;
                         qg2 = fma(gv[i], gv[i], qg2);
-                        qd = fma(gv[i], x[4 * g4 + i] - p[4 * g4 + i], qd);
+                        qd = fma(gv[i], x[4 * g4 + i] - pv[i], qd);
                     }
                 }
                 Acc<T> a2[2];
@@ -745,15 +791,14 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int j = 4 * g4 + i;
-                    if (v0 + i < nV) p[j] = x[j] + lam * gv[i];
-                    pv[i] = p[j];
+                    pv[i] = v0 + i < nV ? x[j] + lam * gv[i] : x[j];
                 }
                 st4(pos + e0, pv);
             }
             __syncthreads();
             Acc<T> a3[1];
             a3[0].zero();
-            a3[0].add(volume_pass(tc, pos, nVp));
+            a3[0].add(volume_pass(tc, pos, nVp, nsum ? stash : nullptr));
             block_reduce_t0<T, 1>(a3, S.red, [&](const double *s) {
                 S.bc->d[0] = s[0];
                 S.bc->i[0] = fabs(tc.V0x6 - s[0]) <= tc.vtol6 || it == 7;
@@ -769,13 +814,14 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
         if (e0 >= n3) continue;
         int v0;
         elem_cv(e0, nVp, v0);
-        T gs[4];
+        T gs[4], pv[4];
         ld4(gsh + e0, gs);
+        ld4(pos + e0, pv);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             if (v0 + i >= nV) continue;
             const int j = 4 * g4 + i;
-            T r = x[j] - p[j];
+            T r = x[j] - pv[i];
             en += T(0.5) * tc.kv * r * r;
             al += tc.kv * fabs(r) * fabs(x[j]);
             gr[j] = gs[i] + tc.kv * r;

@@ -1138,17 +1138,10 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
     c.pad_t = (sizeof(T) == 4 && maxt <= PAD_T) ? maxt : 0;
     c.pad_h = (sizeof(T) == 4 && maxh <= PAD_H) ? maxh : 0;
     if (c.pad_t) {
-        std::vector<int4> vp((size_t)c.pad_t * t->nV, make_int4(0, 0, 0, 0));
+        std::vector<int> vp((size_t)c.pad_t * t->nV, -1);
         for (int v = 0; v < t->nV; ++v)
-            for (int k = H.vt_ptr[v], q = 0; k < H.vt_ptr[v + 1]; ++k, ++q) {
-                float g0 = (float)H.vt_g[2 * k], g1 = (float)H.vt_g[2 * k + 1], one = 1.0f;
-                int4 e;
-                e.x = H.vt_inc[k] >> 2;
-                std::memcpy(&e.y, &g0, 4);
-                std::memcpy(&e.z, &g1, 4);
-                std::memcpy(&e.w, &one, 4);
-                vp[(size_t)q * t->nV + v] = e;
-            }
+            for (int k = H.vt_ptr[v], q = 0; k < H.vt_ptr[v + 1]; ++k, ++q)
+                vp[(size_t)q * t->nV + v] = H.vt_inc[k];          // (t << 2) | corner
         c.vt_pad = upload(ctx, vp, t->owned);
     }
     if (c.pad_h) {

@@ -10,6 +10,7 @@ Branches (Supp. Sec. 2.1, the quasi-Newton update after Eq.
   - collapsed triangles (sigma_2 <= tol sigma_1: the polar factor's tie-break), whose
     branch is decided by rounding, so its bar is the oracle's own sensitivity;
   - flat hinges (|b_rest| = 0) and a hinge flattened exactly (|b| ~ 0: p = b);
+  - the volume projection taking several Gauss-Newton updates (squeezed cells);
   - the literal FP64 refinement residual (residual_fp64 = 1).
 Each run asserts from stats() that its branch ran.  All calls go through
 libnpfem.so."""
@@ -178,6 +179,49 @@ def test_flat_and_flattened_hinges_fp64():
     xg, _, _ = run_gpu(groups, 2)
     xo, _ = run_oracle(groups, 2)
     assert rel_pos_err(xg, xo, groups) <= TOL["fp64"]
+
+
+def squeezed_cells(n=4, seed=7):
+    """Full RBCs (642 vertices) squeezed to about 95 % of their rest volume by a random
+    diagonal scaling (0.97-0.99 per axis), at rest: the volume projection of the first
+    local steps needs several Gauss-Newton updates, each with the volume gradient
+    recomputed at the new point."""
+    mt = I.rbc_type()
+    rng = np.random.default_rng(seed)
+    c = mt.rest.mean(axis=0)
+    x = np.stack([(mt.rest - c) @ np.diag(rng.uniform(0.97, 0.99, 3)) + c for _ in range(n)])
+    return mt, x, np.zeros_like(x), np.zeros_like(x)
+
+
+def gn_updates(T, x, tol):
+    """Updates the volume projection of the local step takes from x when it stops at
+    |V - V0| <= tol |V0| (the same iteration as the oracle's, in numpy on its V and gV)."""
+    V0, p = T.volume(T.rest), x.copy()
+    for j in range(9):
+        V = T.volume(p)
+        if abs(V - V0) <= tol * abs(V0) or j == 8:
+            return j
+        g = T.volume_grad(p)
+        p = x + (V0 - V - np.sum(g * (x - p))) / np.sum(g * g) * g
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_volume_projection_with_several_updates(prec):
+    # The FP64 path stops the projection at 1e-14 |V0| (here after 6-7 updates), the FP32
+    # local step at 2e-6 |V0| after 2-3 updates; both recompute gV at every new point.
+    # (The FP32 stop alone moves this step by 4.3e-7 R: the oracle built to stop at
+    # 2e-6 |V0| lands there.  At larger volume deficits it moves it further: 3.6e-6 R
+    # for cells squeezed to ~85 %.)
+    from oracle import oracle as O
+    mt, xn, vn, f = squeezed_cells()
+    T = O.OracleType.from_mesh_type(mt)
+    tol = 1e-14 if prec == "fp64" else 2e-6
+    upd = [gn_updates(T, x, tol) for x in xn]
+    assert min(upd) >= 2 and max(upd) >= 3, upd
+    x1, _ = T.step_cells(xn, vn, f)
+    xg, _, _ = run_gpu([group_of(mt, xn, vn, f)], 1, prec)
+    err = float(np.linalg.norm(xg[0] - x1, axis=2).max()) / mt.radius
+    assert err <= TOL[prec], err
 
 
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
