@@ -203,8 +203,12 @@ size_t npfem_num_dofs(const npfem_ctx *ctx);
  * (e.g. the same stream, or an event the stream waits on), and it must stay
  * valid and unchanged until the step has run (npfem_sync, or an event recorded
  * on the stream after the call).  Otherwise it is host memory, copied to the
- * device in the call; for page-locked memory that copy runs asynchronously on
- * the stream, so keep the buffer unchanged until the next synchronising call.
+ * device in the call; for page-locked memory that copy runs asynchronously, so
+ * keep the buffer unchanged until the next synchronising call.  Unless a force
+ * filter, the collision search or a damped type reads the forces first, the
+ * copy goes in four pieces on a second stream of the library's while the
+ * predictor starts on the cells whose forces are in (the step's results are
+ * the same bits as with device forces).
  * The call enqueues the work and returns; device errors are reported by the
  * next call that synchronises (get_*, stats, npfem_sync).
  * Errors: EINVAL, ESTATE (no cells), ECUDA. */

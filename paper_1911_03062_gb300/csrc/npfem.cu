@@ -102,6 +102,8 @@ struct MeshTypeImpl {
     int pf_iter = 0, pf_pred = 0;                // L2 prefetch distance: resident blocks of the kernel
 };
 
+constexpr int F_CHUNKS = 4;   // pieces of the host force copy (see npfem_step)
+
 struct npfem_ctx {
     npfem_options opt{};
     int device = 0, nsm = 0;
@@ -110,6 +112,11 @@ struct npfem_ctx {
     std::vector<MeshTypeImpl *> types;
     long long ndofs = 0;
     double *d_f = nullptr;               // device copy of host forces (public layout)
+    // host forces arrive in F_CHUNKS pieces on the copy stream (ev_chunk[i]: piece i is in),
+    // each type's predictor launched per piece; ev_done: the last step has read d_f
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev_chunk[F_CHUNKS] = {};
+    cudaEvent_t ev_done = nullptr;
     double **d_fslot = nullptr;          // device slot: base of the forces read by the step
     double *d_stage = nullptr;           // staging for get/set (public layout)
     double *d_ffilt = nullptr;           // median-filtered forces (public layout), force_median only
@@ -130,6 +137,7 @@ struct npfem_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool graph_valid = false;
+    bool graph_early = false;            // the graph was captured without the predictor
     bool stepped = false;
     int smem_optin = 0;
     // launch accounting and optional per-kernel CUDA-event timing
@@ -237,6 +245,15 @@ int grid_for(long long n, int block, int cap = 1 << 20) {
 // Every kernel launch of a step goes through prof_begin / prof_end: counts
 // the launch and, when profiling, brackets it with a pair of CUDA events on
 // the context stream (captured into the graph as event nodes).
+// an event record on the context stream: an external record node when the
+// stream is being captured (so that the graph records it at each replay)
+void prof_record(npfem_ctx *ctx, cudaEvent_t e) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs == cudaStreamCaptureStatusActive) CK(cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal));
+    else CK(cudaEventRecord(e, ctx->stream));
+}
+
 void prof_begin(npfem_ctx *ctx, int cls) {
     ctx->launch_counter++;
     if (!ctx->prof_on) return;
@@ -249,12 +266,12 @@ void prof_begin(npfem_ctx *ctx, int cls) {
         ctx->prof_cls.resize(ctx->prof_ev.size() / 2);
     }
     ctx->prof_cls[ctx->prof_next / 2] = cls;
-    CK(cudaEventRecordWithFlags(ctx->prof_ev[ctx->prof_next], ctx->stream, cudaEventRecordExternal));
+    prof_record(ctx, ctx->prof_ev[ctx->prof_next]);
 }
 
 void prof_end(npfem_ctx *ctx) {
     if (!ctx->prof_on) return;
-    CK(cudaEventRecordWithFlags(ctx->prof_ev[ctx->prof_next + 1], ctx->stream, cudaEventRecordExternal));
+    prof_record(ctx, ctx->prof_ev[ctx->prof_next + 1]);
     ctx->prof_next += 2;
 }
 
@@ -333,11 +350,13 @@ void prefetch_distance_t(npfem_ctx *ctx, MeshTypeImpl *t) {
 }
 
 template <typename T, int EPT, int MAXB>
-void run_predict_t(npfem_ctx *ctx, MeshTypeImpl *t) {
+void run_predict_t(npfem_ctx *ctx, MeshTypeImpl *t, int c0, int c1) {
     IterArgs<T> a = make_args<T>(ctx, t);
     a.pf_dist = t->pf_pred;
+    a.cell0 = c0;
+    a.ncells = c1;
     prof_begin(ctx, NPFEM_K_PREDICT);
-    k_predict<T, EPT, MAXB><<<t->ncells, t->block, t->smem_step, ctx->stream>>>(a);
+    k_predict<T, EPT, MAXB><<<c1 - c0, t->block, t->smem_step, ctx->stream>>>(a);
     CK(cudaGetLastError());
     prof_end(ctx);
 }
@@ -364,9 +383,9 @@ void run_iterate_t(npfem_ctx *ctx, MeshTypeImpl *t, int last, bool fallback) {
         else FN<T, 16, 512>(__VA_ARGS__);                                \
     } while (0)
 
-void run_predict(npfem_ctx *ctx, MeshTypeImpl *t) {
-    if (mixed(ctx)) DISPATCH_EPT(float, run_predict_t, ctx, t);
-    else DISPATCH_EPT(double, run_predict_t, ctx, t);
+void run_predict(npfem_ctx *ctx, MeshTypeImpl *t, int c0, int c1) {
+    if (mixed(ctx)) DISPATCH_EPT(float, run_predict_t, ctx, t, c0, c1);
+    else DISPATCH_EPT(double, run_predict_t, ctx, t, c0, c1);
 }
 
 void run_iterate(npfem_ctx *ctx, MeshTypeImpl *t, int last, bool fallback) {
@@ -779,7 +798,7 @@ void damped_predictor_rhs(npfem_ctx *ctx) {
     if (!items.empty()) gemm_group(ctx, items, 0, true);
 }
 
-void enqueue_step(npfem_ctx *ctx) {
+void enqueue_step(npfem_ctx *ctx, bool with_predict) {
     // counters only: a pending error word survives until a synchronising call reads it
     CK(cudaMemsetAsync(reinterpret_cast<char *>(ctx->d_st) + sizeof(unsigned long long), 0,
                        sizeof(DevStatus) - sizeof(unsigned long long), ctx->stream));
@@ -801,8 +820,9 @@ void enqueue_step(npfem_ctx *ctx) {
     }
     if (ctx->opt.pik_radius > 0) pik_search(ctx);
     damped_predictor_rhs(ctx);
-    for (auto *t : ctx->types)
-        if (t->ncells) run_predict(ctx, t);
+    if (with_predict)
+        for (auto *t : ctx->types)
+            if (t->ncells) run_predict(ctx, t, 0, t->ncells);
     const int K = ctx->opt.iters;
     for (int k = 0; k < K; ++k) {
         const int last = (k == K - 1);
@@ -1536,6 +1556,13 @@ void npfem_destroy(npfem_ctx *ctx) {
         if (p) cudaFree(p);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    if (ctx->copy) {
+        cudaStreamSynchronize(ctx->copy);
+        cudaStreamDestroy(ctx->copy);
+    }
+    for (cudaEvent_t e : ctx->ev_chunk)
+        if (e) cudaEventDestroy(e);
+    if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -1849,14 +1876,49 @@ int npfem_add_cells(npfem_ctx *ctx, int type_id, int n_cells, const double *x0, 
     });
 }
 
+namespace {
+// first value of piece i of the n-value public force array
+long long force_chunk_lo(long long n, int i) { return n * i / F_CHUNKS; }
+
+// the piece that holds the last force value of cell c of type t
+int force_chunk_of_cell(const npfem_ctx *ctx, const MeshTypeImpl *t, int c) {
+    const long long last = t->pub_off_h[c] + 3ll * t->nV - 1;
+    int k = 0;
+    while (k + 1 < F_CHUNKS && force_chunk_lo(ctx->ndofs, k + 1) <= last) ++k;
+    return k;
+}
+}  // namespace
+
 int npfem_step(npfem_ctx *ctx, const double *f_ext, int f_ext_on_device) {
     if (!ctx) return NPFEM_EINVAL;
     return guard(ctx, [&] {
         if (ctx->ndofs == 0) fail(ctx, NPFEM_ESTATE, "no cells");
         if (!f_ext) fail(ctx, NPFEM_EINVAL, "f_ext is null");
+        // With nothing ahead of the predictor that reads the forces (no force filter,
+        // collision search or damped predictor), the predictor runs outside the graph, per
+        // type in pieces that follow the public force array's F_CHUNKS pieces: host forces
+        // are copied piece by piece on a second stream while the predictor works on the
+        // pieces already in.
+        const bool early = !ctx->opt.force_median && !(ctx->opt.pik_radius > 0) &&
+                           std::none_of(ctx->types.begin(), ctx->types.end(), [](const MeshTypeImpl *t) { return t->damped; });
         const double *fd = f_ext;
         if (!f_ext_on_device) {
-            CK(cudaMemcpyAsync(ctx->d_f, f_ext, ctx->ndofs * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+            if (early) {
+                if (!ctx->copy) {
+                    CK(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+                    for (cudaEvent_t &e : ctx->ev_chunk) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                    CK(cudaEventCreateWithFlags(&ctx->ev_done, cudaEventDisableTiming));
+                }
+                CK(cudaStreamWaitEvent(ctx->copy, ctx->ev_done, 0));      // the last step read d_f
+                for (int i = 0; i < F_CHUNKS; ++i) {
+                    const long long lo = force_chunk_lo(ctx->ndofs, i), hi = force_chunk_lo(ctx->ndofs, i + 1);
+                    CK(cudaMemcpyAsync(ctx->d_f + lo, f_ext + lo, (hi - lo) * sizeof(double), cudaMemcpyHostToDevice,
+                                       ctx->copy));
+                    CK(cudaEventRecord(ctx->ev_chunk[i], ctx->copy));
+                }
+            } else {
+                CK(cudaMemcpyAsync(ctx->d_f, f_ext, ctx->ndofs * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+            }
             fd = ctx->d_f;
         }
         // tile choices for the real right-hand-side counts (outside any capture; a changed
@@ -1870,13 +1932,32 @@ int npfem_step(npfem_ctx *ctx, const double *f_ext, int f_ext_on_device) {
         k_set_ptr<<<1, 1, 0, ctx->stream>>>(ctx->d_fslot, fd);
         CK(cudaGetLastError());
         ctx->prof_next = 0;
+        ctx->launch_counter = 0;
+        if (early) {
+            for (auto *t : ctx->types) {
+                if (!t->ncells) continue;
+                for (int c0 = 0; c0 < t->ncells;) {
+                    // the cells whose forces end in piece k: a run (the pieces grow with the cell)
+                    const int k = force_chunk_of_cell(ctx, t, c0);
+                    int c1 = c0 + 1, hi = t->ncells;
+                    while (c1 < hi) {
+                        const int mid = c1 + (hi - c1) / 2;
+                        if (force_chunk_of_cell(ctx, t, mid) > k) hi = mid;
+                        else c1 = mid + 1;
+                    }
+                    if (!f_ext_on_device) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_chunk[k], 0));
+                    run_predict(ctx, t, c0, c1);
+                    c0 = c1;
+                }
+            }
+        }
         if (ctx->opt.use_graph) {
-            if (!ctx->graph_valid) {
+            if (!ctx->graph_valid || ctx->graph_early != early) {
                 invalidate_graph(ctx);
-                ctx->launch_counter = 0;
+                ctx->graph_early = early;
                 CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
                 try {
-                    enqueue_step(ctx);
+                    enqueue_step(ctx, !early);
                     ctx->launches_per_step = ctx->launch_counter + 1;   // + the force-pointer kernel
                 } catch (...) {
                     cudaGraph_t g = nullptr;
@@ -1891,10 +1972,10 @@ int npfem_step(npfem_ctx *ctx, const double *f_ext, int f_ext_on_device) {
             }
             CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
         } else {
-            ctx->launch_counter = 0;
-            enqueue_step(ctx);
+            enqueue_step(ctx, !early);
             ctx->launches_per_step = ctx->launch_counter + 1;
         }
+        if (early && !f_ext_on_device) CK(cudaEventRecord(ctx->ev_done, ctx->stream));
         if (ctx->prof_on) prof_harvest(ctx, ctx->opt.use_graph ? ctx->graph_prof_pairs : ctx->prof_next / 2);
         ctx->stepped = true;
     });

@@ -19,6 +19,7 @@ template <typename T>
 struct IterArgs {
     TypeConst<T> tc;
     int ncells, m, max_bt, last, use_allow, stash_T;
+    int cell0;                    // k_predict: first cell of the launch (it steps cells cell0 .. ncells - 1)
     int pf_dist;                  // k_predict: L2 prefetch of cell + pf_dist (one resident wave ahead), 0: off
     double h, inv_h, c1;
     double curv_tol, curv_tol2;   // history admits a pair if s.y > curv_tol |s||y| (and its square)
@@ -203,7 +204,7 @@ template <typename T, int EPT, int MAXB>
 __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 4) : 1) k_predict(IterArgs<T> a) {
     const Smem<T> S = smem_layout<T>(a.tc.nVp);
     const int nVp = a.tc.nVp, n3 = 3 * nVp;
-    for (int cell = blockIdx.x; cell < a.ncells; cell += gridDim.x) {
+    for (int cell = a.cell0 + blockIdx.x; cell < a.ncells; cell += gridDim.x) {
         const long long base = (long long)cell * n3;
         if (a.pf_dist && threadIdx.x < 3) {
             const int fut = cell + a.pf_dist;        // one resident wave ahead

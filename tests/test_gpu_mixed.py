@@ -228,3 +228,63 @@ def test_autotune_cache_file_round_trip(tmp_path):
         key, nt, st, us = ln.split()
         assert int(nt) % 32 == 0 and 2 <= int(st) <= 6 and float(us) > 0
     assert np.array_equal(np.load(outs[0]), np.load(outs[1]))
+
+
+@pytest.mark.parametrize("prec,graph", [("bf16", True), ("fp64", False)])
+def test_host_forces_in_pieces_match_device_forces(prec, graph):
+    # Host forces are copied in four pieces on a second stream and each type's predictor is
+    # launched per piece as the pieces arrive; a device force array is read in place.  Two
+    # types whose cells come in two batches each, so the public array interleaves them and
+    # the pieces split both types' cell runs.  The steps must agree bit for bit.
+    import torch
+    from paper_1911_03062_gb300.npfem import Solver
+    g = make_groups([(I.rbc_type(), 6, 0.3), (I.plt_type(), 5, 0.3)])
+    order = [(0, slice(0, 3)), (1, slice(0, 2)), (0, slice(3, 6)), (1, slice(2, 5))]
+    f_pub = np.concatenate([g[gi].f_ext[sl].ravel() for gi, sl in order])
+
+    def run(on_device):
+        s = Solver(precision=prec, use_graph=graph)
+        ids = [s.create_type(gr.mtype) for gr in g]
+        for gi, sl in order:
+            s.add_cells(ids[gi], g[gi].x0[sl], g[gi].v0[sl])
+        f = torch.from_numpy(f_pub).to("cuda") if on_device else f_pub
+        for _ in range(3):
+            s.step(f)
+        x, v = s.positions(), s.velocities()
+        s.close()
+        return x, v
+
+    xh, vh = run(False)
+    xd, vd = run(True)
+    assert np.all(np.isfinite(xh))
+    assert np.array_equal(xh, xd) and np.array_equal(vh, vd)
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_kernel_timing_mode(graph):
+    # Per-kernel CUDA-event times (npfem_profile) with the step's graph and without it, host
+    # forces (the predictor launched outside the graph, per force piece) and device forces:
+    # every launch of the step is timed and the positions are the same bits as untimed.
+    import torch
+    from paper_1911_03062_gb300.npfem import Solver
+    g = make_groups([(I.rbc_type(), 8, 0.3), (I.plt_type(), 4, 0.3)])
+    f = public(g, "f_ext")
+
+    def run(prof):
+        s = Solver(precision="bf16", use_graph=graph)
+        for gr in g:
+            s.add_cells(s.create_type(gr.mtype), gr.x0, gr.v0)
+        s.profile(prof)
+        s.step(f)
+        s.step(torch.from_numpy(f).to("cuda"))
+        times = s.profile_read() if prof else {}
+        x, n = s.positions(), s.stats()["launches_per_step"]
+        s.close()
+        return x, times, n
+
+    x0, _, _ = run(False)
+    x1, times, n = run(True)
+    assert np.array_equal(x0, x1)
+    assert sum(c for _, c in times.values()) == 2 * n - 2      # all but the force-pointer kernel
+    assert times["predict"][1] >= 2 * 2 and times["iterate"][1] == 2 * 2 * 10
+    assert all(ms > 0 for ms, _ in times.values())
