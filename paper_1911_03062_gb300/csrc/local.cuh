@@ -34,10 +34,10 @@ template <typename T> struct alignas(2 * sizeof(T)) HingeInc { int h; T c; };
 template <typename T>
 struct TypeConst {
     int nV, nVp, nT, nH;
-    const int4 *tri;        // nT: (i0, i1, i2, 0), outward CCW
+    const uint2 *tri;       // nT: i0 | i1 << 16, i2 (16-bit vertex indices), outward CCW
     const T *dinv;          // nT x 4: inverse rest edge matrix D_m^{-1}, row major
     const T *wtri;          // nT x 2: (k_strain, k_area) x rest area
-    const int4 *hv;         // nH: hinge (x0, x1, x2, x3)
+    const uint2 *hv;        // nH: hinge x0 | x1 << 16, x2 | x3 << 16 (16-bit vertex indices)
     const T *hc;            // nH x 4: cotangent stencil
     const T *hrest;         // nH: |b| at rest
     const int *vt_ptr;      // nV + 1: vertex -> triangle incidences (sorted by triangle)
@@ -91,6 +91,10 @@ __device__ __forceinline__ void st4(double *p, const double (&r)[4]) {
     reinterpret_cast<double2 *>(p)[0] = make_double2(r[0], r[1]);
     reinterpret_cast<double2 *>(p)[1] = make_double2(r[2], r[3]);
 }
+
+// 16-bit packed vertex indices of a triangle / hinge
+__device__ __forceinline__ int4 tri_idx(uint2 p) { return make_int4(p.x & 0xffffu, p.x >> 16, p.y & 0xffffu, 0); }
+__device__ __forceinline__ int4 hinge_idx(uint2 p) { return make_int4(p.x & 0xffffu, p.x >> 16, p.y & 0xffffu, p.y >> 16); }
 
 __device__ __forceinline__ int elem_cv(int e, int nVp, int &v) {
     int c = (e >= nVp) + (e >= 2 * nVp);
@@ -416,7 +420,7 @@ __device__ __forceinline__ T volume_pass(const TypeConst<T> &tc, const T *pos, i
     T aV = T(0);
     const T o0 = pos[0], o1 = pos[nVp], o2 = pos[2 * nVp];
     for (int t = threadIdx.x; t < tc.nT; t += blockDim.x) {
-        const int4 tv = __ldg(tc.tri + t);
+        const int4 tv = tri_idx(__ldg(tc.tri + t));
         T ax = pos[tv.x] - o0, ay = pos[nVp + tv.x] - o1, az = pos[2 * nVp + tv.x] - o2;
         T e1x = pos[tv.y] - pos[tv.x], e1y = pos[nVp + tv.y] - pos[nVp + tv.x], e1z = pos[2 * nVp + tv.y] - pos[2 * nVp + tv.x];
         T e2x = pos[tv.z] - pos[tv.x], e2y = pos[nVp + tv.z] - pos[nVp + tv.x], e2z = pos[2 * nVp + tv.z] - pos[2 * nVp + tv.x];
@@ -511,7 +515,7 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
         for (int t0 = 0; t0 < tc.nT; t0 += ct) {
             const int t1 = min(tc.nT, t0 + ct);
             for (int t = t0 + tid; t < t1; t += B) {
-                const int4 tv = __ldg(tc.tri + t);
+                const int4 tv = tri_idx(__ldg(tc.tri + t));
                 T Di[4], w[2];
                 ld4(tc.dinv + 4 * t, Di);
                 ld2(tc.wtri + 2 * t, w);
@@ -621,7 +625,7 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
         const int ch = stash_T / 3;
         for (int h0 = 0; h0 < tc.nH; h0 += ch) {
             const int h1 = min(tc.nH, h0 + ch);
-            int4 hv_n = make_int4(0, 0, 0, 0);
+            uint2 hv_n = make_uint2(0, 0);
             T hc_n[4] = {T(0), T(0), T(0), T(0)}, rest_n = T(0);
             if (h0 + tid < h1) {
                 hv_n = __ldg(tc.hv + h0 + tid);
@@ -629,7 +633,7 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
                 rest_n = tc.hrest[h0 + tid];
             }
             for (int h = h0 + tid; h < h1; h += B) {
-                const int4 hv = hv_n;
+                const int4 hv = hinge_idx(hv_n);
                 const T hc[4] = {hc_n[0], hc_n[1], hc_n[2], hc_n[3]}, rest = rest_n;
                 if (h + B < h1) {
                     hv_n = __ldg(tc.hv + h + B);

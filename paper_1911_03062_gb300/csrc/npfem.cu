@@ -1113,9 +1113,12 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
     c.nVp = t->nVp;
     c.nT = t->nT;
     c.nH = t->nH;
-    std::vector<int4> tri(t->nT), hv(t->nH);
-    for (int i = 0; i < t->nT; ++i) tri[i] = make_int4(H.tri[3 * i], H.tri[3 * i + 1], H.tri[3 * i + 2], 0);
-    for (int i = 0; i < t->nH; ++i) hv[i] = make_int4(H.hv[4 * i], H.hv[4 * i + 1], H.hv[4 * i + 2], H.hv[4 * i + 3]);
+    std::vector<uint2> tri(t->nT), hv(t->nH);
+    auto u16 = [](int v) { return (unsigned)v & 0xffffu; };
+    for (int i = 0; i < t->nT; ++i)
+        tri[i] = make_uint2(u16(H.tri[3 * i]) | u16(H.tri[3 * i + 1]) << 16, u16(H.tri[3 * i + 2]));
+    for (int i = 0; i < t->nH; ++i)
+        hv[i] = make_uint2(u16(H.hv[4 * i]) | u16(H.hv[4 * i + 1]) << 16, u16(H.hv[4 * i + 2]) | u16(H.hv[4 * i + 3]) << 16);
     std::vector<double> wtri(2 * t->nT), mh2(t->nVp, 0.0);   // mh2 zero-padded for 4-wide loads
     for (int i = 0; i < t->nT; ++i) {
         wtri[2 * i] = t->ks * H.area[i];
