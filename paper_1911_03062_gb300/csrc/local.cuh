@@ -35,8 +35,10 @@ template <typename T>
 struct TypeConst {
     int nV, nVp, nT, nH;
     const uint2 *tri;       // nT: i0 | i1 << 16, i2 (16-bit vertex indices), outward CCW
-    const T *dinv;          // nT x 4: inverse rest edge matrix D_m^{-1}, row major
-    const T *wtri;          // nT x 2: (k_strain, k_area) x rest area
+    const T *dinv;          // nT x 4: D_m^{-1}[0][0], D_m^{-1}[0][1], D_m^{-1}[1][1] (the rest frame's
+                            // first axis is edge 0->1, so D_m and its inverse are upper triangular),
+                            // rest area
+    T ks, ka;               // strain and area stiffness (weights k x rest area)
     const uint2 *hv;        // nH: hinge x0 | x1 << 16, x2 | x3 << 16 (16-bit vertex indices)
     const T *hc;            // nH x 4: cotangent stencil
     const T *hrest;         // nH: |b| at rest
@@ -274,8 +276,9 @@ __device__ __noinline__ Damp<T> tri_damp(const T *pos, const T *__restrict__ yr,
 // beta/(2h) (x - y)^T L (x - y), i.e. cd (w_s + w_a)/2 |F(x - y)|^2, adds
 // cd (w_s + w_a) F(x - y) to R; yr holds y (same frame as pos).
 template <typename T>
-__device__ __forceinline__ T tri_local(const T *pos, const T *__restrict__ yr, int nVp, int4 tv, const T (&Di)[4], T ws,
+__device__ __forceinline__ T tri_local(const T *pos, const T *__restrict__ yr, int nVp, int4 tv, const T (&Di)[3], T ws,
                                        T wa, T cd, const T o[3], bool corners, T *st, T &en, T &al) {
+    // F = [e1 e2] D_m^{-1} with D_m^{-1} = [[Di0, Di1], [0, Di2]]
     T F[6], E1[3], E2[3], A0[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -284,8 +287,8 @@ __device__ __forceinline__ T tri_local(const T *pos, const T *__restrict__ yr, i
         E1[c] = pc[tv.y] - x0;
         E2[c] = pc[tv.z] - x0;
         A0[c] = x0 - o[c];
-        F[2 * c] = E1[c] * Di[0] + E2[c] * Di[2];
-        F[2 * c + 1] = E1[c] * Di[1] + E2[c] * Di[3];
+        F[2 * c] = E1[c] * Di[0];
+        F[2 * c + 1] = E1[c] * Di[1] + E2[c] * Di[2];
     }
     // volume part first (the edge vectors are then dead)
     const T C0 = E1[1] * E2[2] - E1[2] * E2[1], C1 = E1[2] * E2[0] - E1[0] * E2[2], C2 = E1[0] * E2[1] - E1[1] * E2[0];
@@ -336,7 +339,7 @@ __device__ __forceinline__ T tri_local(const T *pos, const T *__restrict__ yr, i
     en += T(0.5) * ws * ns + T(0.5) * wa * na;
     al += ws * sqrt(ns * nf) + wa * sqrt(na * nf);
     if (cd != T(0)) {
-        const Damp<T> dm = tri_damp(pos, yr, nVp, tv, Di[0], Di[1], Di[2], Di[3], cd * (ws + wa), sqrt(nf));
+        const Damp<T> dm = tri_damp(pos, yr, nVp, tv, Di[0], Di[1], T(0), Di[2], cd * (ws + wa), sqrt(nf));
 #pragma unroll
         for (int i = 0; i < 6; ++i) R[i] += dm.r[i];
         en += dm.e;
@@ -348,7 +351,7 @@ __device__ __forceinline__ T tri_local(const T *pos, const T *__restrict__ yr, i
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             st[r] = R[2 * r] * Di[0] + R[2 * r + 1] * Di[1];
-            st[3 + r] = R[2 * r] * Di[2] + R[2 * r + 1] * Di[3];
+            st[3 + r] = R[2 * r + 1] * Di[2];
         }
     } else {
 #pragma unroll
@@ -516,9 +519,9 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
             const int t1 = min(tc.nT, t0 + ct);
             for (int t = t0 + tid; t < t1; t += B) {
                 const int4 tv = tri_idx(__ldg(tc.tri + t));
-                T Di[4], w[2];
-                ld4(tc.dinv + 4 * t, Di);
-                ld2(tc.wtri + 2 * t, w);
+                T dq[4];
+                ld4(tc.dinv + 4 * t, dq);
+                const T Di[3] = {dq[0], dq[1], dq[2]}, w[2] = {tc.ks * dq[3], tc.ka * dq[3]};
                 aV += tri_local(pos, yrel, nVp, tv, Di, w[0], w[1], tc.cd, o, sizeof(T) == 4 && tc.pad_t != 0,
                                 stash + 9 * (t - t0), en, al);
             }

@@ -1119,10 +1119,12 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
         tri[i] = make_uint2(u16(H.tri[3 * i]) | u16(H.tri[3 * i + 1]) << 16, u16(H.tri[3 * i + 2]));
     for (int i = 0; i < t->nH; ++i)
         hv[i] = make_uint2(u16(H.hv[4 * i]) | u16(H.hv[4 * i + 1]) << 16, u16(H.hv[4 * i + 2]) | u16(H.hv[4 * i + 3]) << 16);
-    std::vector<double> wtri(2 * t->nT), mh2(t->nVp, 0.0);   // mh2 zero-padded for 4-wide loads
+    std::vector<double> dq(4 * t->nT), mh2(t->nVp, 0.0);   // mh2 zero-padded for 4-wide loads
     for (int i = 0; i < t->nT; ++i) {
-        wtri[2 * i] = t->ks * H.area[i];
-        wtri[2 * i + 1] = t->ka * H.area[i];
+        dq[4 * i] = H.dinv[4 * i];
+        dq[4 * i + 1] = H.dinv[4 * i + 1];
+        dq[4 * i + 2] = H.dinv[4 * i + 3];
+        dq[4 * i + 3] = H.area[i];
     }
     // inertia diagonal of the local step: m/h^2, damped (1 + h alpha) m/h^2 + (beta/h) k_vol
     // (Mt's mass part and the volume part of its beta L; the element parts of beta L are
@@ -1131,8 +1133,9 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
         mh2[v] = t->damped ? (1.0 + t->h * t->ra) * mass[v] / (t->h * t->h) + t->rb / t->h * t->kv
                            : mass[v] / (t->h * t->h);
     c.tri = upload(ctx, tri, t->owned);
-    c.dinv = upload(ctx, cvt<T>(H.dinv), t->owned);
-    c.wtri = upload(ctx, cvt<T>(wtri), t->owned);
+    c.dinv = upload(ctx, cvt<T>(dq), t->owned);
+    c.ks = (T)t->ks;
+    c.ka = (T)t->ka;
     c.hv = upload(ctx, hv, t->owned);
     c.hc = upload(ctx, cvt<T>(H.hc), t->owned);
     c.hrest = upload(ctx, cvt<T>(H.hrest), t->owned);
