@@ -47,6 +47,7 @@ struct TypeConst {
     const int *vh_ptr;      // nV + 1: vertex -> hinge incidences (sorted by hinge)
     const HingeInc<T> *vh;
     const T *mh2;           // nV: m_v / h^2 (damped: (1 + h alpha) m_v / h^2 + (beta / h) k_vol)
+    int ova, ovb;           // two vertices far apart at rest: the midpoint of their y is the origin
     double V0;              // rest volume
     double V0x6, vtol6;     // 6 V0 and 6 tol |V0| (the volume sums give 6 V)
     T kb, kv;               // bending and volume weights

@@ -1663,6 +1663,23 @@ int npfem_create_mesh_type(npfem_ctx *ctx, int nV, const double *rest_xyz, int n
         t->V0 = H.V0;
         if (mixed(ctx)) t->tc32 = upload_consts<float>(ctx, t, H, mass);
         else t->tc64 = upload_consts<double>(ctx, t, H, mass);
+        {
+            // the origin's two vertices: the one farthest from vertex 0 at rest, and the one
+            // farthest from it
+            auto far_from = [&](int a) {
+                int best = 0;
+                double bd = -1.0;
+                for (int v = 0; v < nV; ++v) {
+                    double d = 0.0;
+                    for (int c = 0; c < 3; ++c) d += (rest_i[3 * v + c] - rest_i[3 * a + c]) * (rest_i[3 * v + c] - rest_i[3 * a + c]);
+                    if (d > bd) { bd = d; best = v; }
+                }
+                return best;
+            };
+            const int va = far_from(0), vb = far_from(va);
+            t->tc32.ova = t->tc64.ova = va;
+            t->tc32.ovb = t->tc64.ovb = vb;
+        }
         std::vector<double> minv(nV), diag(nV);
         std::vector<int> op(nV + 1, 0);
         std::vector<int2> oe;

@@ -164,7 +164,7 @@ __device__ __forceinline__ void block_sum_many(const T (&part)[NMAX], int n1, in
     __syncthreads();
 }
 
-// Start of a step: y, origin (centroid of y), y_rel, delta = 0, history
+// Start of a step: y, origin (midpoint of y at two far-apart vertices), y_rel, delta = 0, history
 // cleared, g and grad g at x^0 = y, and q = grad g (the first apply's RHS).
 // Right-hand side of the damped predictor, b = M v_n + h F_ext (SoA rows of nVp,
 // zero padding), as the apply's operand: q in the form's type and split into a
@@ -229,26 +229,26 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 4) :
                 a.ccol[base + e] = T((double)a.ccol[base + e] - (y[j] - xo[j]));
             }
         }
-        // centroid of y, per component
-        Acc<double> s[3];
-        s[0].zero(); s[1].zero(); s[2].zero();
+        // origin of the FP32 offsets: the midpoint of y at two vertices that are far apart
+        // at rest, near the middle of the cell (any fixed point serves; it is stored and y
+        // is re-formed in FP64 at the end): no block reduction in FP64, whose rate is 1/62
+        // of FP32's on this GPU
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
             int e = elem_of(j), v;
             if (e >= n3) continue;
             int c = elem_cv(e, nVp, v);
-            if (v >= a.tc.nV) continue;
-            s[c].add(y[j]);
+            if (v == a.tc.ova) S.bc->d[c] = y[j];
+            if (v == a.tc.ovb) S.bc->d[3 + c] = y[j];
         }
-        block_reduce_t0<double, 3>(s, S.red, [&](const double *o) {
-            // origin of the FP32 offsets: the centroid up to ~1e-7 relative (any fixed
-            // point serves; it is stored and y is re-formed in FP64 at the end)
-            const double inv_n = (double)(1.0f / (float)a.tc.nV);
-            for (int c = 0; c < 3; ++c) {
-                S.bc->d[c] = o[c] * inv_n;
-                a.origin[3 * cell + c] = S.bc->d[c];
-            }
-        });
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            const int c = threadIdx.x;
+            const double o = 0.5 * (S.bc->d[c] + S.bc->d[3 + c]);
+            a.origin[3 * cell + c] = o;
+            S.bc->d[c] = o;                  // thread c alone reads d[c] and d[3 + c] here
+        }
+        __syncthreads();
         T yr[EPT], dl[EPT], gr[EPT];
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
