@@ -94,7 +94,7 @@ struct MeshTypeImpl {
     int *ring_bc = nullptr;                      // vertex -> triangle incidences: the other two vertices
     __nv_bfloat16 *rlo_lo = nullptr;             // split corrections: BF16 low part of r
     __nv_bfloat16 *q16 = nullptr;
-    double *origin = nullptr, *rho = nullptr, *alpha = nullptr, *M = nullptr, *g = nullptr, *allow = nullptr;
+    double *y64 = nullptr, *origin = nullptr, *rho = nullptr, *alpha = nullptr, *M = nullptr, *g = nullptr, *allow = nullptr;
     int *hcount = nullptr, *hhead = nullptr, *conv = nullptr, *fb_list = nullptr, *fb_count = nullptr;
     CUtensorMap mapQ{}, mapR{}, mapRlo{}, mapZ{}, mapZp{};
     int ept = 8, block = 256, stash_T = 0;
@@ -315,6 +315,7 @@ IterArgs<T> make_args(npfem_ctx *ctx, MeshTypeImpl *t) {
     a.vpub = t->vpub;
     a.minv = t->minv;
     a.yrel = (T *)t->yrel;
+    a.y64 = t->y64;
     a.origin = t->origin;
     a.delta = (T *)t->delta;
     a.grad = (T *)t->grad;
@@ -1374,7 +1375,7 @@ void fill_cells(npfem_ctx *ctx, MeshTypeImpl *t, const MeshTypeImpl *old_t, int 
 
 void free_cells(MeshTypeImpl *t) {
     void **bufs[] = {(void **)&t->pub_off, (void **)&t->xn, (void **)&t->vn, &t->yrel, &t->delta, &t->grad, &t->q,
-                     &t->z, &t->zp, &t->kcol, &t->ccol, &t->S, &t->Y, &t->rlo, (void **)&t->rlo_lo, (void **)&t->q16, (void **)&t->origin, (void **)&t->rho,
+                     &t->z, &t->zp, &t->kcol, &t->ccol, &t->S, &t->Y, &t->rlo, (void **)&t->rlo_lo, (void **)&t->q16, (void **)&t->y64, (void **)&t->origin, (void **)&t->rho,
                      (void **)&t->alpha, (void **)&t->M, (void **)&t->g, (void **)&t->allow, (void **)&t->hcount,
                      (void **)&t->hhead, (void **)&t->conv, (void **)&t->fb_list, (void **)&t->fb_count};
     for (void **b : bufs) dfree(*b);
@@ -1387,7 +1388,7 @@ void alloc_cells(npfem_ctx *ctx, MeshTypeImpl *cur, int cap) {
     MeshTypeImpl nt = *cur;
     void **cell_ptrs[] = {(void **)&nt.pub_off, (void **)&nt.xn, (void **)&nt.vn, &nt.yrel, &nt.delta, &nt.grad,
                           &nt.q, &nt.z, &nt.zp, &nt.kcol, &nt.ccol, &nt.S, &nt.Y, &nt.rlo, (void **)&nt.rlo_lo,
-                          (void **)&nt.q16, (void **)&nt.origin, (void **)&nt.rho, (void **)&nt.alpha,
+                          (void **)&nt.q16, (void **)&nt.y64, (void **)&nt.origin, (void **)&nt.rho, (void **)&nt.alpha,
                           (void **)&nt.M, (void **)&nt.g, (void **)&nt.allow, (void **)&nt.hcount,
                           (void **)&nt.hhead, (void **)&nt.conv, (void **)&nt.fb_list, (void **)&nt.fb_count};
     for (void **b : cell_ptrs) *b = nullptr;
@@ -1425,6 +1426,7 @@ void fill_cells(npfem_ctx *ctx, MeshTypeImpl *t, const MeshTypeImpl *old_t, int 
     t->q16 = bf16(ctx) ? dalloc<__nv_bfloat16>(ctx, cap * n3) : nullptr;
     t->rlo = mixed(ctx) ? dalloc<unsigned char>(ctx, cap * n3 * (bf16(ctx) ? 2 : 4)) : nullptr;
     t->rlo_lo = (split(ctx) || (bf16(ctx) && t->damped)) ? dalloc<__nv_bfloat16>(ctx, cap * n3) : nullptr;
+    t->y64 = dalloc<double>(ctx, cap * n3);
     t->origin = dalloc<double>(ctx, 3 * (size_t)cap);
     t->rho = dalloc<double>(ctx, m * cap);
     t->alpha = dalloc<double>(ctx, m * cap);

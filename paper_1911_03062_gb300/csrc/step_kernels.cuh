@@ -32,6 +32,7 @@ struct IterArgs {
     const T *kcol;                // PIK collisions: [cell][nVp] stiffness (0: no contact), else null
     T *ccol;                      // PIK: [cell][3][nVp] push p - x_n, turned into p - y by k_predict
     T *yrel;                      // y - origin
+    double *y64;                  // [cell][3][nVp] y in FP64 (k_predict writes it, the last iteration reads it)
     double *origin;               // [cell][3]
     T *delta, *grad, *q, *z;
     __nv_bfloat16 *q_bf16;        // GEMM operand copy of q (BF16 form), or null
@@ -87,6 +88,8 @@ __device__ __forceinline__ void store_vec_bf16(__nv_bfloat16 *__restrict__ p, co
 
 // y = x_n + h v_n + h^2 M^{-1} F_ext in FP64 for this thread's elements; with
 // Rayleigh damping y = x_n + h Mt^{-1}(M v_n + h F_ext), the solve done before.
+// y is also stored (a.y64) for the step's last iteration, which forms
+// x_{n+1} = y + delta from it.
 template <typename T, int EPT>
 __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, double (&y)[EPT], double (&xo)[EPT]) {
     const int nVp = a.tc.nVp, nV = a.tc.nV, n3 = 3 * nVp;
@@ -114,6 +117,8 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
                 xo[4 * g + i] = xv[i];
                 y[4 * g + i] = xv[i] + a.h * (double)zv[i];
             }
+            const double yv[4] = {y[4 * g], y[4 * g + 1], y[4 * g + 2], y[4 * g + 3]};
+            st4(a.y64 + base + e0, yv);
             continue;
         }
         ld4(a.vn + base + e0, vv);
@@ -127,6 +132,9 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
             const double fv = kc4[i] != T(0) ? 0.0 : f[3 * a.vpub[v] + c];
             y[4 * g + i] = xv[i] + a.h * vv[i] + a.h * a.h * a.minv[v] * fv;
         }
+        // kept for the last iteration's x_{n+1} = y + delta
+        const double yv[4] = {y[4 * g], y[4 * g + 1], y[4 * g + 2], y[4 * g + 3]};
+        st4(a.y64 + base + e0, yv);
     }
 }
 
@@ -461,7 +469,8 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 4) :
                 atomicAdd(&a.st->energy_sum, gtv);
             }
             double y[EPT], xo[EPT];
-            predictor64<T, EPT>(a, cell, y, xo);
+            load_vec<double, EPT>(a.y64 + base, y, n3);       // y as the predictor formed it
+            load_vec<double, EPT>(a.xn + base, xo, n3);
 #pragma unroll
             for (int g = 0; g < EPT / 4; ++g) {
                 const int e0 = 4 * (threadIdx.x + g * blockDim.x);
