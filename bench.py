@@ -41,7 +41,7 @@ sys.path.insert(0, ROOT)
 # 40 k_iterate launches of one step, averaged over the 20 launches that process all
 # cells (the fallback-list launches, ~0.1 MB each, excluded like their times).
 # Set to None whenever k_iterate changes until it is captured again.
-ITERATE_TRAFFIC = 4.017e9
+ITERATE_TRAFFIC = 4.012e9
 PARITY_CELLS = 16        # cells per mesh type compared with the oracle (evenly spaced)
 METRIC = "cell-iterations/sec at 50k cells, mixed vs FP64 GPU at ≤1e-6 rel pos error"
 UNIT = "cell-iterations/s"

@@ -39,9 +39,9 @@ struct TypeConst {
                             // first axis is edge 0->1, so D_m and its inverse are upper triangular),
                             // rest area
     T ks, ka;               // strain and area stiffness (weights k x rest area)
-    const uint2 *hv;        // nH: hinge x0 | x1 << 16, x2 | x3 << 16 (16-bit vertex indices)
+    const uint4 *hv;        // nH: hinge x0 | x1 << 16, x2 | x3 << 16 (16-bit vertex indices), then |b| at
+                            // rest (FP32 form: its bits in .z; FP64 form: low word .z, high word .w)
     const T *hc;            // nH x 4: cotangent stencil
-    const T *hrest;         // nH: |b| at rest
     const int *vt_ptr;      // nV + 1: vertex -> triangle incidences (sorted by triangle)
     const TriInc<T> *vt;
     const int *vh_ptr;      // nV + 1: vertex -> hinge incidences (sorted by hinge)
@@ -97,7 +97,9 @@ __device__ __forceinline__ void st4(double *p, const double (&r)[4]) {
 
 // 16-bit packed vertex indices of a triangle / hinge
 __device__ __forceinline__ int4 tri_idx(uint2 p) { return make_int4(p.x & 0xffffu, p.x >> 16, p.y & 0xffffu, 0); }
-__device__ __forceinline__ int4 hinge_idx(uint2 p) { return make_int4(p.x & 0xffffu, p.x >> 16, p.y & 0xffffu, p.y >> 16); }
+__device__ __forceinline__ int4 hinge_idx(uint4 p) { return make_int4(p.x & 0xffffu, p.x >> 16, p.y & 0xffffu, p.y >> 16); }
+__device__ __forceinline__ void hinge_rest(uint4 p, float &r) { r = __uint_as_float(p.z); }
+__device__ __forceinline__ void hinge_rest(uint4 p, double &r) { r = __hiloint2double((int)p.w, (int)p.z); }
 
 __device__ __forceinline__ int elem_cv(int e, int nVp, int &v) {
     int c = (e >= nVp) + (e >= 2 * nVp);
@@ -629,20 +631,20 @@ __device__ void local_eval(const TypeConst<T> &tc, const T *__restrict__ yrel, c
         const int ch = stash_T / 3;
         for (int h0 = 0; h0 < tc.nH; h0 += ch) {
             const int h1 = min(tc.nH, h0 + ch);
-            uint2 hv_n = make_uint2(0, 0);
-            T hc_n[4] = {T(0), T(0), T(0), T(0)}, rest_n = T(0);
+            uint4 hv_n = make_uint4(0, 0, 0, 0);
+            T hc_n[4] = {T(0), T(0), T(0), T(0)};
             if (h0 + tid < h1) {
                 hv_n = __ldg(tc.hv + h0 + tid);
                 ld4(tc.hc + 4 * (h0 + tid), hc_n);
-                rest_n = tc.hrest[h0 + tid];
             }
             for (int h = h0 + tid; h < h1; h += B) {
                 const int4 hv = hinge_idx(hv_n);
-                const T hc[4] = {hc_n[0], hc_n[1], hc_n[2], hc_n[3]}, rest = rest_n;
+                T rest;
+                hinge_rest(hv_n, rest);
+                const T hc[4] = {hc_n[0], hc_n[1], hc_n[2], hc_n[3]};
                 if (h + B < h1) {
                     hv_n = __ldg(tc.hv + h + B);
                     ld4(tc.hc + 4 * (h + B), hc_n);
-                    rest_n = tc.hrest[h + B];
                 }
                 T R[3];
                 hinge_local(pos, yrel, nVp, hv, hc, rest, tc.kb, tc.cd, R, en, al);

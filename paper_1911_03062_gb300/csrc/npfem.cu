@@ -1114,12 +1114,25 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
     c.nVp = t->nVp;
     c.nT = t->nT;
     c.nH = t->nH;
-    std::vector<uint2> tri(t->nT), hv(t->nH);
+    std::vector<uint2> tri(t->nT);
+    std::vector<uint4> hv(t->nH);
     auto u16 = [](int v) { return (unsigned)v & 0xffffu; };
     for (int i = 0; i < t->nT; ++i)
         tri[i] = make_uint2(u16(H.tri[3 * i]) | u16(H.tri[3 * i + 1]) << 16, u16(H.tri[3 * i + 2]));
-    for (int i = 0; i < t->nH; ++i)
-        hv[i] = make_uint2(u16(H.hv[4 * i]) | u16(H.hv[4 * i + 1]) << 16, u16(H.hv[4 * i + 2]) | u16(H.hv[4 * i + 3]) << 16);
+    for (int i = 0; i < t->nH; ++i) {
+        uint4 r = make_uint4(u16(H.hv[4 * i]) | u16(H.hv[4 * i + 1]) << 16, u16(H.hv[4 * i + 2]) | u16(H.hv[4 * i + 3]) << 16, 0, 0);
+        if (sizeof(T) == 4) {
+            const float rf = (float)H.hrest[i];
+            std::memcpy(&r.z, &rf, 4);
+        } else {
+            const double rd = H.hrest[i];
+            uint64_t b;
+            std::memcpy(&b, &rd, 8);
+            r.z = (unsigned)(b & 0xffffffffu);
+            r.w = (unsigned)(b >> 32);
+        }
+        hv[i] = r;
+    }
     std::vector<double> dq(4 * t->nT), mh2(t->nVp, 0.0);   // mh2 zero-padded for 4-wide loads
     for (int i = 0; i < t->nT; ++i) {
         dq[4 * i] = H.dinv[4 * i];
@@ -1139,7 +1152,6 @@ TypeConst<T> upload_consts(npfem_ctx *ctx, MeshTypeImpl *t, const HostType &H, c
     c.ka = (T)t->ka;
     c.hv = upload(ctx, hv, t->owned);
     c.hc = upload(ctx, cvt<T>(H.hc), t->owned);
-    c.hrest = upload(ctx, cvt<T>(H.hrest), t->owned);
     std::vector<TriInc<T>> vt(H.vt_inc.size());
     std::vector<int> ring(H.vt_inc.size());
     for (size_t k = 0; k < vt.size(); ++k) {

@@ -91,7 +91,7 @@ __device__ __forceinline__ void store_vec_bf16(__nv_bfloat16 *__restrict__ p, co
 // y is also stored (a.y64) for the step's last iteration, which forms
 // x_{n+1} = y + delta from it.
 template <typename T, int EPT>
-__device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, double (&y)[EPT], double (&xo)[EPT]) {
+__device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, double (&y)[EPT]) {
     const int nVp = a.tc.nVp, nV = a.tc.nV, n3 = 3 * nVp;
     const double *f = *a.fptr + a.pub_off[cell];
     const long long base = (long long)cell * n3;
@@ -99,10 +99,7 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
     for (int g = 0; g < EPT / 4; ++g) {
         const int e0 = 4 * (threadIdx.x + g * blockDim.x);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            y[4 * g + i] = 0.0;
-            xo[4 * g + i] = 0.0;
-        }
+        for (int i = 0; i < 4; ++i) y[4 * g + i] = 0.0;
         if (e0 >= n3) continue;
         int v0;
         const int c = elem_cv(e0, nVp, v0);
@@ -114,7 +111,6 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (v0 + i >= nV) continue;
-                xo[4 * g + i] = xv[i];
                 y[4 * g + i] = xv[i] + a.h * (double)zv[i];
             }
             const double yv[4] = {y[4 * g], y[4 * g + 1], y[4 * g + 2], y[4 * g + 3]};
@@ -128,7 +124,6 @@ __device__ __forceinline__ void predictor64(const IterArgs<T> &a, int cell, doub
         for (int i = 0; i < 4; ++i) {
             const int v = v0 + i;
             if (v >= nV) continue;
-            xo[4 * g + i] = xv[i];
             const double fv = kc4[i] != T(0) ? 0.0 : f[3 * a.vpub[v] + c];
             y[4 * g + i] = xv[i] + a.h * vv[i] + a.h * a.h * a.minv[v] * fv;
         }
@@ -223,8 +218,8 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 4) :
                 else prefetch_l2(*a.fptr + a.pub_off[fut], (size_t)3 * a.tc.nV * sizeof(double));
             }
         }
-        double y[EPT], xo[EPT];
-        predictor64<T, EPT>(a, cell, y, xo);
+        double y[EPT];
+        predictor64<T, EPT>(a, cell, y);
         if (a.ccol) {
             // collision targets relative to y: p - y = (p - x_n) - (y - x_n)
 #pragma unroll
@@ -234,7 +229,7 @@ __global__ void __launch_bounds__(MAXB, MAXB <= 256 ? (sizeof(T) == 8 ? 2 : 4) :
                 if (e >= n3) continue;
                 elem_cv(e, nVp, v);
                 if (v >= a.tc.nV) continue;
-                a.ccol[base + e] = T((double)a.ccol[base + e] - (y[j] - xo[j]));
+                a.ccol[base + e] = T((double)a.ccol[base + e] - (y[j] - a.xn[base + e]));
             }
         }
         // origin of the FP32 offsets: the midpoint of y at two vertices that are far apart
